@@ -1,0 +1,351 @@
+"""Seeded synthetic scenes for the SPH coupling substep.
+
+This module only lays out inputs: fluid lattices with jitter, static wall shells,
+lattice-sampled rigid and soft bodies, and the grabbed body's prescribed path.  It
+holds none of the method's arithmetic (no kernel, density, force, hashing or
+integration), so both the CUDA path and the CPU oracle can consume its arrays.
+
+Scene recipes (all lengths in metres, z is up, gravity -9.81 along z):
+
+* ``dam_break``      16^3 fluid block at spacing 0.02 in the corner of a 0.5 m box
+                     with a two-layer static wall shell (open top) and one free
+                     0.1 m rigid cube of density 500 sampled at half spacing.
+* ``stirring_tank``  125 x 125 x 16 fluid at spacing 0.008 in a 1 x 1 x 0.5 m tank,
+                     a 0.02 x 0.2 x 0.3 m paddle sampled at 0.004, grabbed and driven
+                     on a horizontal circle (radius 0.2 m, 1 Hz, seeded phase).
+* ``coupled``        1,000,000 fluid at spacing 0.01 in a 2 x 1 x 0.6 m tank, a solid
+                     sphere probe (r 0.0964 m at 0.005, about 30k particles) on a
+                     seeded random-walk grab path, and a 24^3 soft cube at 0.01.
+* ``batched``        64 stirring scenes with fluid counts log-uniform in [8k, 256k].
+
+Smoothing length h equals the fluid spacing, so the kernel support 2h is twice the
+spacing; the pressure constant is k = c^2 with c = 0.4 h / dt (an acoustic CFL of 0.4);
+kinematic viscosity 1e-3 m^2/s.  The grid cell edge is the support radius enlarged by
+0.1 % so that FP32 rounding of cell coordinates can never separate two particles
+closer than the support radius by more than one cell.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+KIND_STATIC = 1
+KIND_RIGID = 2
+KIND_SOFT = 3
+
+FLAG_CLAMP_PRESSURE = 1 << 0   # negative pressures are clamped to zero
+FLAG_RECORD = 1 << 1           # keep per-particle acceleration and neighbour counts
+
+
+@dataclass
+class Body:
+    kind: int
+    xyz: np.ndarray                 # static: world positions; rigid: body-frame offsets
+                                    # about the centre of mass; soft: world positions
+    spacing: float                  # sampling spacing (SPH mass = rho0 * spacing^3)
+    mass: float = 0.0               # inertial mass of a rigid body
+    inertia: np.ndarray = field(default_factory=lambda: np.zeros((3, 3), np.float32))
+    pose: np.ndarray = field(default_factory=lambda: np.array([0, 0, 0, 1, 0, 0, 0], np.float32))
+    vel: np.ndarray = field(default_factory=lambda: np.zeros(6, np.float32))
+    springs: Optional[np.ndarray] = None   # (ns, 2) local index pairs (soft)
+    young: float = 0.0
+    poisson: float = 0.0
+    grab_local: np.ndarray = field(default_factory=lambda: np.zeros(3, np.float32))
+
+    @property
+    def n(self) -> int:
+        return int(self.xyz.shape[0])
+
+
+@dataclass
+class Scene:
+    name: str
+    params: dict
+    fluid_x: np.ndarray             # (nf, 3) float32
+    fluid_v: np.ndarray             # (nf, 3) float32
+    fluid_spacing: float
+    bodies: List[Body]
+    grab_body: int = -1             # index into bodies, -1 = nothing grabbed
+    trajectory: Optional[np.ndarray] = None   # (T, 13) float32 x,q(wxyz),v,w per substep
+    n_substeps: int = 100
+
+    @property
+    def n_fluid(self) -> int:
+        return int(self.fluid_x.shape[0])
+
+    @property
+    def n_total(self) -> int:
+        return self.n_fluid + sum(b.n for b in self.bodies)
+
+
+def make_params(spacing, dt, lo, hi, *, rho0=1000.0, nu=1e-3, flags=FLAG_CLAMP_PRESSURE,
+                cfl=0.4, smooth_window=20):
+    h = float(spacing)
+    c = cfl * h / dt
+    return dict(h=h, rho0=float(rho0), k=float(c * c), nu=float(nu),
+                g=(0.0, 0.0, -9.81), dt=float(dt),
+                lo=tuple(float(a) for a in lo), hi=tuple(float(a) for a in hi),
+                cell=float(np.float32(2.0 * h * 1.001)), flags=int(flags),
+                visc_eps=0.01, spring_zeta=0.1, smooth_window=int(smooth_window))
+
+
+def _lattice(n, spacing, origin):
+    """Cell-centred lattice points origin + (i + 0.5) * spacing, i < n per axis, x fastest."""
+    nx, ny, nz = n
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pts = np.stack([i, j, k], axis=-1).reshape(-1, 3).astype(np.float64)
+    return (pts + 0.5) * spacing + np.asarray(origin, np.float64)
+
+
+def _jitter(rng, pts, spacing, frac=0.01):
+    return pts + rng.uniform(-frac * spacing, frac * spacing, size=pts.shape)
+
+
+def wall_shell(box_lo, box_hi, spacing, layers=2):
+    """Static walls: `layers` lattice layers outside the box on the sides and bottom (open top)."""
+    box_lo = np.asarray(box_lo, np.float64)
+    box_hi = np.asarray(box_hi, np.float64)
+    n = np.rint((box_hi - box_lo) / spacing).astype(int)
+    ii = np.arange(-layers, n[0] + layers)
+    jj = np.arange(-layers, n[1] + layers)
+    kk = np.arange(-layers, n[2])
+    K, J, I = np.meshgrid(kk, jj, ii, indexing="ij")
+    I, J, K = I.ravel(), J.ravel(), K.ravel()
+    outside = (I < 0) | (I >= n[0]) | (J < 0) | (J >= n[1]) | (K < 0)
+    pts = np.stack([I[outside], J[outside], K[outside]], -1).astype(np.float64)
+    return ((pts + 0.5) * spacing + box_lo).astype(np.float32)
+
+
+def solid_box(size, spacing):
+    """Body-frame lattice of a solid box centred on the origin."""
+    n = np.maximum(np.rint(np.asarray(size) / spacing).astype(int), 1)
+    return (_lattice(n, spacing, -0.5 * n * spacing)).astype(np.float32), n
+
+
+def solid_sphere(radius, spacing):
+    m = int(np.ceil(radius / spacing)) + 1
+    pts = _lattice((2 * m, 2 * m, 2 * m), spacing, (-m * spacing,) * 3)
+    keep = np.sum(pts * pts, axis=1) <= radius * radius
+    return pts[keep].astype(np.float32)
+
+
+def lattice_springs(n):
+    """18-neighbour lattice springs (6 axis + 12 face diagonals) of an n[0] x n[1] x n[2] block."""
+    nx, ny, nz = n
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    offs = [(1, 0, 0), (0, 1, 0), (0, 0, 1),
+            (1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1)]
+    pairs = []
+    for dx, dy, dz in offs:
+        z0, z1 = max(0, -dz), nz - max(0, dz)
+        y0, y1 = max(0, -dy), ny - max(0, dy)
+        x0, x1 = max(0, -dx), nx - max(0, dx)
+        a = idx[z0:z1, y0:y1, x0:x1]
+        b = idx[z0 + dz:z1 + dz, y0 + dy:y1 + dy, x0 + dx:x1 + dx]
+        pairs.append(np.stack([a.ravel(), b.ravel()], -1))
+    return np.concatenate(pairs).astype(np.int32)
+
+
+def _box_inertia(mass, size):
+    a, b, c = size
+    return (mass / 12.0) * np.diag([b * b + c * c, a * a + c * c, a * a + b * b]).astype(np.float32)
+
+
+def _fill_fluid(rng, cols, spacing, origin, count, carve):
+    """Fill columns bottom-up with a lattice, skip points that `carve` rejects, keep `count`."""
+    nx, ny = cols
+    nz = int(np.ceil(count / (nx * ny))) + 8
+    pts = _lattice((nx, ny, nz), spacing, origin)
+    if carve is not None:
+        pts = pts[~carve(pts)]
+    if pts.shape[0] < count:
+        raise ValueError("fluid lattice too small for the requested count")
+    pts = pts[:count]
+    return _jitter(rng, pts, spacing).astype(np.float32)
+
+
+def circle_trajectory(rng, n_sub, dt, centre, radius=0.2, freq=1.0, z=0.0):
+    phase = rng.uniform(0.0, 2.0 * np.pi)
+    t = np.arange(n_sub) * dt
+    ang = 2.0 * np.pi * freq * t + phase
+    traj = np.zeros((n_sub, 13), np.float64)
+    traj[:, 0] = centre[0] + radius * np.cos(ang)
+    traj[:, 1] = centre[1] + radius * np.sin(ang)
+    traj[:, 2] = z
+    traj[:, 3] = 1.0
+    w = 2.0 * np.pi * freq
+    traj[:, 7] = -radius * w * np.sin(ang)
+    traj[:, 8] = radius * w * np.cos(ang)
+    return traj.astype(np.float32)
+
+
+def random_walk_trajectory(rng, n_sub, dt, start, lo, hi, sigma=0.05, vmax=0.5):
+    """Velocity random walk v += N(0, sigma^2) per substep, |v| <= vmax, reflected at lo/hi."""
+    traj = np.zeros((n_sub, 13), np.float64)
+    x = np.asarray(start, np.float64).copy()
+    v = np.zeros(3)
+    for s in range(n_sub):
+        traj[s, 0:3] = x
+        traj[s, 3] = 1.0
+        traj[s, 7:10] = v
+        v = v + rng.normal(0.0, sigma, 3)
+        sp = np.linalg.norm(v)
+        if sp > vmax:
+            v *= vmax / sp
+        x = x + v * dt
+        for a in range(3):
+            if x[a] < lo[a]:
+                x[a] = 2 * lo[a] - x[a]
+                v[a] = -v[a]
+            if x[a] > hi[a]:
+                x[a] = 2 * hi[a] - x[a]
+                v[a] = -v[a]
+    return traj.astype(np.float32)
+
+
+def dam_break(seed=0, n_side=16, n_substeps=100, grab=False, cube_pos=(0.4, 0.25, 0.12)):
+    """3D dam break: n_side^3 fluid at 0.02 m, 0.5 m static box, one free 0.1 m cube (density 500)."""
+    rng = np.random.default_rng(seed)
+    s = 0.02
+    box = 0.5
+    dt = 1e-3
+    fluid = _jitter(rng, _lattice((n_side,) * 3, s, (0.0, 0.0, 0.0)), s).astype(np.float32)
+    walls = Body(KIND_STATIC, wall_shell((0, 0, 0), (box, box, box), s), s)
+    cube_local, _ = solid_box((0.1, 0.1, 0.1), s / 2)
+    cube_mass = 500.0 * 0.1 ** 3
+    cube = Body(KIND_RIGID, cube_local, s / 2, mass=cube_mass,
+                inertia=_box_inertia(cube_mass, (0.1, 0.1, 0.1)),
+                pose=np.array([*cube_pos, 1, 0, 0, 0], np.float32))
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s), (box + 3 * s, box + 3 * s, 1.5 * box))
+    sc = Scene("dam_break", params, fluid, np.zeros_like(fluid), s, [walls, cube],
+               n_substeps=n_substeps)
+    if grab:
+        sc.grab_body = 1
+        sc.trajectory = random_walk_trajectory(rng, n_substeps, dt, cube_pos,
+                                               (0.08, 0.08, 0.08), (0.42, 0.42, 0.35),
+                                               sigma=0.02, vmax=0.4)
+    return sc
+
+
+def stirring_tank(seed=0, n_fluid=250_000, cols=(125, 125), tank=(1.0, 1.0, 0.5),
+                  n_substeps=2000, spacing=0.008, paddle=(0.02, 0.2, 0.3)):
+    """Stirring tank: fluid at 0.008 m, grabbed paddle on a 0.2 m / 1 Hz circle."""
+    rng = np.random.default_rng(seed)
+    s = spacing
+    dt = 5e-4
+    tx, ty, tz = tank
+    centre = np.array([tx / 2, ty / 2])
+    p_local, _ = solid_box(paddle, s / 2)
+    pz = 0.02 + paddle[2] / 2
+    radius = min(0.2, 0.5 * min(tx, ty) - paddle[1])
+    traj = circle_trajectory(rng, n_substeps, dt, centre, radius=radius, z=pz)
+    p0 = traj[0, :3].astype(np.float64)
+    half = np.asarray(paddle) / 2 + 0.5 * s
+
+    def carve(pts):
+        return np.all(np.abs(pts - p0) <= half, axis=1)
+
+    fluid = _fill_fluid(rng, cols, s, (0.0, 0.0, 0.0), n_fluid, carve)
+    walls = Body(KIND_STATIC, wall_shell((0, 0, 0), tank, s), s)
+    pmass = 500.0 * float(np.prod(paddle))
+    pad = Body(KIND_RIGID, p_local, s / 2, mass=pmass, inertia=_box_inertia(pmass, paddle),
+               pose=traj[0, :7].copy(), vel=traj[0, 7:].copy())
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s), (tx + 3 * s, ty + 3 * s, 1.2 * tz))
+    return Scene("stirring_tank", params, fluid, np.zeros_like(fluid), s, [walls, pad],
+                 grab_body=1, trajectory=traj, n_substeps=n_substeps)
+
+
+def coupled(seed=0, n_fluid=1_000_000, cols=(200, 100), tank=(2.0, 1.0, 0.6), n_substeps=1000,
+            spacing=0.01, probe_r=0.0964, soft_n=24, young=5e4, poisson=0.45):
+    """Coupled scene: fluid at 0.01 m, random-walk sphere probe, free soft cube."""
+    rng = np.random.default_rng(seed)
+    s = spacing
+    dt = 5e-4
+    tx, ty, tz = tank
+    depth = n_fluid / (cols[0] * cols[1]) * s
+    probe_c = np.array([0.3 * tx, 0.5 * ty, 0.5 * depth])
+    probe_local = solid_sphere(probe_r, s / 2)
+    soft_local, soft_dims = solid_box((soft_n * s,) * 3, s)
+    soft_c = np.array([0.7 * tx, 0.5 * ty, depth - 0.5 * soft_n * s + 0.25 * soft_n * s])
+    soft_xyz = (soft_local.astype(np.float64) + soft_c).astype(np.float32)
+    soft_half = 0.5 * soft_n * s + 0.5 * s
+
+    def carve(pts):
+        in_probe = np.sum((pts - probe_c) ** 2, axis=1) <= (probe_r + 0.5 * s) ** 2
+        in_soft = np.all(np.abs(pts - soft_c) <= soft_half, axis=1)
+        return in_probe | in_soft
+
+    fluid = _fill_fluid(rng, cols, s, (0.0, 0.0, 0.0), n_fluid, carve)
+    walls = Body(KIND_STATIC, wall_shell((0, 0, 0), tank, s), s)
+    pmass = 1000.0 * probe_local.shape[0] * (s / 2) ** 3
+    inertia = np.eye(3, dtype=np.float32) * np.float32(0.4 * pmass * probe_r ** 2)
+    m = probe_r + 0.02
+    traj = random_walk_trajectory(rng, n_substeps, dt, probe_c, (m, m, m),
+                                  (tx - m, ty - m, tz - m))
+    probe = Body(KIND_RIGID, probe_local, s / 2, mass=pmass, inertia=inertia,
+                 pose=traj[0, :7].copy(), vel=traj[0, 7:].copy())
+    soft = Body(KIND_SOFT, soft_xyz, s, springs=lattice_springs(soft_dims), young=young,
+                poisson=poisson)
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s), (tx + 3 * s, ty + 3 * s, 1.4 * tz))
+    return Scene("coupled", params, fluid, np.zeros_like(fluid), s, [walls, probe, soft],
+                 grab_body=1, trajectory=traj, n_substeps=n_substeps)
+
+
+def batched_counts(seed=0, n_scenes=64, lo=8_000, hi=256_000):
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), n_scenes)).astype(np.int64)
+
+
+def batched(seed=0, n_scenes=64, n_substeps=200, lo=8_000, hi=256_000):
+    """Independent stirring scenes with log-uniform fluid counts (depth 16 layers at 0.008 m)."""
+    counts = batched_counts(seed, n_scenes, lo, hi)
+    scenes = []
+    for i, c in enumerate(counts):
+        side = int(np.ceil(np.sqrt(c / 16.0)))
+        side = max(side, 40)
+        tank = (side * 0.008, side * 0.008, 0.5)
+        paddle = (0.02, min(0.2, 0.25 * side * 0.008), 0.3)
+        scenes.append(stirring_tank(seed=1000 + i, n_fluid=int(c), cols=(side, side), tank=tank,
+                                    n_substeps=n_substeps, paddle=paddle))
+    return scenes
+
+
+def tiny(seed=0, n=(4, 4, 4), spacing=0.02, dt=1e-3, with_bodies=True):
+    """A few hundred particles: fluid block, small wall patch, one rigid and one soft body."""
+    rng = np.random.default_rng(seed)
+    s = spacing
+    fluid = _jitter(rng, _lattice(n, s, (0.0, 0.0, 0.0)), s).astype(np.float32)
+    v = rng.uniform(-0.1, 0.1, fluid.shape).astype(np.float32)
+    bodies = []
+    if with_bodies:
+        floor = _lattice((n[0] + 2, n[1] + 2, 1), s, (-s, -s, -1.2 * s)).astype(np.float32)
+        bodies.append(Body(KIND_STATIC, floor, s))
+        loc, _ = solid_box((2 * s, 2 * s, 2 * s), s / 2)
+        bodies.append(Body(KIND_RIGID, loc, s / 2, mass=0.004,
+                           inertia=_box_inertia(0.004, (2 * s,) * 3),
+                           pose=np.array([n[0] * s + 0.6 * s, 0.5 * n[1] * s, 1.1 * s,
+                                          0.9659258, 0.0, 0.258819, 0.0], np.float32),
+                           vel=np.array([-0.05, 0.02, 0.0, 0.3, -0.2, 0.5], np.float32)))
+        sl, sd = solid_box((2 * s, 2 * s, 2 * s), s)
+        sxyz = (sl.astype(np.float64) + np.array([0.5 * n[0] * s, n[1] * s + 0.9 * s,
+                                                   0.8 * s])).astype(np.float32)
+        sxyz = _jitter(rng, sxyz, s, 0.05).astype(np.float32)
+        bodies.append(Body(KIND_SOFT, sxyz, s, springs=lattice_springs(sd), young=5e3,
+                           poisson=0.45))
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s),
+                         ((n[0] + 4) * s, (n[1] + 4) * s, (n[2] + 4) * s))
+    return Scene("tiny", params, fluid, v, s, bodies, grab_body=-1, n_substeps=10)
+
+
+def column(seed=0, n=(6, 6, 20), spacing=0.02, dt=1e-3):
+    """Hydrostatic column: fluid in a closed-bottom shaft of static walls."""
+    rng = np.random.default_rng(seed)
+    s = spacing
+    fluid = _jitter(rng, _lattice(n, s, (0.0, 0.0, 0.0)), s).astype(np.float32)
+    box_hi = (n[0] * s, n[1] * s, (n[2] + 4) * s)
+    walls = Body(KIND_STATIC, wall_shell((0, 0, 0), box_hi, s), s)
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s),
+                         (box_hi[0] + 3 * s, box_hi[1] + 3 * s, box_hi[2] + 3 * s))
+    return Scene("column", params, fluid, np.zeros_like(fluid), s, [walls], n_substeps=2000)

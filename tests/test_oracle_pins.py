@@ -1,0 +1,403 @@
+"""Pins of the FP64 oracle against the paper and against mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: the paper's printed
+kernel polynomial (golden fixture), closed forms, invariants (normalisation, momentum,
+angular momentum, Newton's third law), library routines (stable argsort, k-d tree,
+scipy rotations, quadrature) and brute force.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.spatial import cKDTree
+from scipy.spatial.transform import Rotation
+
+import oracle
+from paper_2511_15908_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _params(h=0.02, dt=1e-3, lo=(-0.1,) * 3, hi=(0.5,) * 3, **kw):
+    p = scenes.make_params(h, dt, lo, hi)
+    p.update(kw)
+    return p
+
+
+# ----------------------------------------------------------------- kernel (Eq. kernel)
+
+def test_kernel_matches_printed_polynomial_golden():
+    rows = []
+    with open(os.path.join(GOLDEN, "kernel_values.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            q, frac = line.split()
+            rows.append((float(q), float(Fraction(frac))))
+    for h in (0.01, 0.02, 0.37):
+        a = oracle.alpha(h)
+        for q, w in rows:
+            assert oracle.W(q * h, h) == pytest.approx(a * w, rel=1e-14, abs=1e-300)
+
+
+@pytest.mark.parametrize("h", [0.008, 0.01, 0.02, 1.0])
+def test_kernel_unit_integral(h):
+    # integral of W over R^3 must be 1: this fixes alpha_3 = 3 / (2 pi h^3)
+    val, err = integrate.quad(lambda r: 4 * np.pi * r * r * oracle.W(r, h), 0.0, 2 * h,
+                              points=[h], epsabs=0, epsrel=1e-12)
+    assert val == pytest.approx(1.0, rel=1e-10)
+    assert oracle.alpha(h) == pytest.approx(3.0 / (2.0 * np.pi * h ** 3), rel=1e-15)
+
+
+def test_kernel_continuity_and_support():
+    h = 0.02
+    eps = 1e-12
+    for q in (1.0, 2.0):
+        assert oracle.W((q - eps) * h, h) == pytest.approx(oracle.W((q + eps) * h, h),
+                                                           abs=1e-6 * oracle.alpha(h))
+    assert oracle.W(2.0 * h, h) == 0.0
+    assert oracle.W(3.0 * h, h) == 0.0
+    assert oracle.gradW_coef(2.0 * h, h) == 0.0
+
+
+def test_kernel_gradient_matches_finite_difference():
+    h = 0.02
+    for q in np.linspace(0.05, 1.95, 39):
+        r = q * h
+        d = 1e-6 * h
+        fd = (oracle.W(r + d, h) - oracle.W(r - d, h)) / (2 * d)
+        # grad_i W = coef * x_ij, so dW/dr = coef * r
+        assert oracle.gradW_coef(r, h) * r == pytest.approx(fd, rel=1e-7, abs=1e-9 * oracle.alpha(h) / h)
+    # finite at r = 0 (central force coefficient stays bounded)
+    assert np.isfinite(oracle.gradW_coef(0.0, h))
+
+
+def test_kernel_lattice_sum_reproduces_rest_density():
+    # A perfect cubic lattice with spacing s = h: sum_j s^3 W(|x_j|) is a Riemann sum of the
+    # unit integral, so the interior density equals rho0 to well under 0.1 %.
+    h = s = 0.02
+    n = np.arange(-3, 4)
+    I, J, K = np.meshgrid(n, n, n, indexing="ij")
+    r = s * np.sqrt(I ** 2 + J ** 2 + K ** 2).ravel()
+    total = sum(s ** 3 * oracle.W(x, h) for x in r)
+    assert total == pytest.approx(1.0, abs=1e-3)
+
+
+# --------------------------------------------------------------- grid hash (Alg. 2)
+
+def test_hash_keys_bound_each_particle():
+    rng = np.random.default_rng(1)
+    p = _params()
+    x = rng.uniform(-0.09, 0.49, (5000, 3)).astype(np.float32)
+    keys, bad = oracle.hash_keys(p, x)
+    assert bad == 0
+    dims = oracle.grid_dims(p)
+    cx = keys % dims[0]
+    cy = (keys // dims[0]) % dims[1]
+    cz = keys // (dims[0] * dims[1])
+    c = np.stack([cx, cy, cz], 1).astype(np.float64)
+    o = np.asarray(p["lo"], np.float64) - p["cell"]
+    # the cell box contains the point (FP32 rounding of (x-o)/cell is far below 1e-4 cell)
+    lo = o + c * p["cell"]
+    assert np.all(x >= lo - 1e-4 * p["cell"])
+    assert np.all(x < lo + p["cell"] * (1 + 1e-4))
+    assert keys.max() < np.prod(dims)
+
+
+def test_hash_clamps_outside_and_nonfinite():
+    p = _params()
+    x = np.array([[10.0, 0.1, 0.1], [-5.0, 0.1, 0.1], [np.nan, 0.1, 0.1], [0.1, 0.1, 0.1]],
+                 np.float32)
+    keys, bad = oracle.hash_keys(p, x)
+    assert bad == 3
+    assert keys.max() < np.prod(oracle.grid_dims(p))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_counting_sort_is_stable_argsort(seed):
+    rng = np.random.default_rng(seed)
+    ncell = 97
+    keys = rng.integers(0, ncell, 3001).astype(np.uint32)
+    cs, src = oracle.counting_sort(keys, ncell)
+    np.testing.assert_array_equal(src, np.argsort(keys, kind="stable"))
+    np.testing.assert_array_equal(cs, np.searchsorted(np.sort(keys), np.arange(ncell + 1)))
+
+
+def test_counting_sort_empty_and_single_cell():
+    cs, src = oracle.counting_sort(np.zeros(0, np.uint32), 5)
+    assert src.size == 0 and np.all(cs == 0)
+    cs, src = oracle.counting_sort(np.full(7, 3, np.uint32), 5)
+    np.testing.assert_array_equal(src, np.arange(7))
+    np.testing.assert_array_equal(cs, [0, 0, 0, 0, 7, 7])
+
+
+def test_neighbour_counts_match_kdtree():
+    rng = np.random.default_rng(3)
+    p = _params()
+    x = rng.uniform(0.0, 0.3, (3000, 3)).astype(np.float32)
+    R = 2 * p["h"]
+    got = oracle.nnbr_brute(p, x)
+    tree = cKDTree(x.astype(np.float64))
+    lo = np.array([len(a) - 1 for a in tree.query_ball_point(x, R * (1 - 1e-6))])
+    hi = np.array([len(a) - 1 for a in tree.query_ball_point(x, R * (1 + 1e-6))])
+    assert np.all(got >= lo) and np.all(got <= hi)
+    assert np.mean(lo == hi) > 0.99
+
+
+def test_grid_neighbours_equal_brute_force_on_dam_break():
+    sc = scenes.dam_break(seed=4)
+    a = oracle.System(sc, mode=0).substep()
+    b = oracle.System(sc, mode=1).substep()
+    np.testing.assert_array_equal(a["nnbr"], b["nnbr"])
+    np.testing.assert_array_equal(a["key"], b["key"])
+    np.testing.assert_array_equal(a["src"], b["src"])
+    np.testing.assert_allclose(a["rho"], b["rho"], rtol=1e-13)
+    np.testing.assert_allclose(a["acc"], b["acc"], rtol=1e-10, atol=1e-10)
+
+
+# ---------------------------------------------------- forces, invariants (Alg. 1)
+
+def _random_scene(seed=5):
+    sc = scenes.tiny(seed=seed, n=(6, 6, 6))
+    rng = np.random.default_rng(seed)
+    sc.fluid_v = rng.normal(0, 0.3, sc.fluid_x.shape).astype(np.float32)
+    return sc
+
+
+def _pair_forces(sc, out, sysm):
+    """Pair force on every particle (sorted order): m (acc - g for integrated) - spring."""
+    m = sysm.m  # already advanced to the sorted order
+    ids = out["id"]
+    kinds = np.zeros(len(ids), int)
+    first = sc.n_fluid
+    for b in sc.bodies:
+        kinds[(ids >= first) & (ids < first + b.n)] = b.kind
+        first += b.n
+    g = np.asarray(sc.params["g"])
+    f = m[:, None].astype(np.float64) * out["acc"]
+    integ = (kinds == 0) | (kinds == scenes.KIND_SOFT)
+    f[integ] -= m[integ, None] * g
+    return f, kinds
+
+
+def test_pair_forces_cancel_linear_and_angular_momentum():
+    sc = _random_scene()
+    s = oracle.System(sc, mode=0)
+    out = s.substep()
+    diag = out["diag"]
+    assert np.linalg.norm(diag[0:3]) <= 1e-12 * diag[3]
+    # angular momentum: pair and spring forces are central, so sum x_i x F_i vanishes
+    f, kinds = _pair_forces(sc, out, s)
+    # include springs (they are central too): add them back for soft particles
+    # (acc of soft particles already contains spring/m, so f above holds pair + spring)
+    x = np.empty_like(f)
+    x[:] = out["x_new"]  # boundary x unchanged; integrated x moved, so rebuild positions:
+    # positions fed to the substep: boundary x_new == x_in; fluid/soft x_in = x_new - v_new dt
+    integ = (kinds == 0) | (kinds == scenes.KIND_SOFT)
+    x[integ] = out["x_new"][integ] - out["v_new"][integ] * sc.params["dt"]
+    torque = np.cross(x, f).sum(0)
+    scale = np.sum(np.linalg.norm(x, axis=1) * np.linalg.norm(f, axis=1))
+    assert np.linalg.norm(torque) <= 1e-9 * scale
+
+
+def test_newton_third_law_fluid_body():
+    # fluid plus one rigid body, no walls: force on the body = - force on the fluid
+    sc = scenes.tiny(seed=6, n=(5, 5, 5))
+    sc.bodies = [sc.bodies[1]]
+    sc.bodies[0].pose[:3] = [0.05, 0.05, 0.05]   # inside the fluid block
+    s = oracle.System(sc, mode=0)
+    out = s.substep()
+    f, kinds = _pair_forces(sc, out, s)
+    on_fluid = f[kinds == 0].sum(0)
+    F = out["wrench"][0, :3]
+    assert np.linalg.norm(F) > 1e-4
+    np.testing.assert_allclose(F, -on_fluid, rtol=1e-10, atol=1e-12 * np.abs(f).sum())
+
+
+def _lattice_scene(n=11, s=0.02, vel=None, nu=1e-3, h=None):
+    idx = np.arange(n)
+    K, J, I = np.meshgrid(idx, idx, idx, indexing="ij")
+    x = (np.stack([I, J, K], -1).reshape(-1, 3) * s).astype(np.float32)
+    v = np.zeros_like(x) if vel is None else vel(x.astype(np.float64)).astype(np.float32)
+    p = _params(h=s if h is None else h, lo=(-0.1,) * 3, hi=(n * s + 0.1,) * 3, nu=nu)
+    return scenes.Scene("lattice", p, x, v, s, []), x
+
+
+def test_viscosity_vanishes_for_rigid_motion():
+    w = np.array([0.3, -0.7, 1.1])
+    sc, x = _lattice_scene(n=7, vel=lambda x: np.cross(w, x) + np.array([0.2, 0.1, -0.4]))
+    sc.params["flags"] = scenes.FLAG_CLAMP_PRESSURE
+    out = oracle.System(sc, mode=0).substep()
+    # perfect lattice: density below rho0 everywhere, pressure clamped to 0; with rigid
+    # motion (v_ij . x_ij = 0) every pair force vanishes, so acc = g up to the FP32
+    # rounding of the input velocities (~1e-8; a non-projected form gives ~1e-1 here)
+    g = np.asarray(sc.params["g"])
+    np.testing.assert_allclose(out["acc"], np.broadcast_to(g, out["acc"].shape), atol=1e-6)
+
+
+def test_viscosity_approximates_laplacian():
+    # v = (A y^2, 0, 0): div v = 0 and lap v = (2A, 0, 0); interior a_visc = nu lap v.
+    # The sum converges to the continuum Laplacian as the lattice refines (the projected
+    # form carries the factor 2(d+2)); at spacing h/2 the lattice error is about 1 %.
+    # The viscous part is isolated by differencing against nu = 0 (the pressure term does
+    # not depend on v).
+    A, n, s = 50.0, 15, 0.01
+    vel = lambda x: np.stack([A * x[:, 1] ** 2, 0 * x[:, 0], 0 * x[:, 0]], 1)
+    acc = {}
+    for nu in (0.0, 1e-3):
+        sc, x = _lattice_scene(n=n, s=s, nu=nu, h=0.02, vel=vel)
+        out = oracle.System(sc, mode=1).substep()
+        centre = np.argmin(np.linalg.norm(x - (n // 2) * s, axis=1))
+        acc[nu] = out["acc"][np.nonzero(out["id"] == centre)[0][0]]
+    a = acc[1e-3] - acc[0.0]
+    assert a[0] == pytest.approx(2 * A * 1e-3, rel=0.03)
+    assert abs(a[1]) < 1e-6 * abs(a[0]) and abs(a[2]) < 1e-6 * abs(a[0])
+
+
+def test_free_fall_is_exact_semi_implicit_euler():
+    p = _params()
+    x0 = np.array([[0.2, 0.2, 0.3]], np.float32)
+    v0 = np.array([[0.1, -0.05, 0.2]], np.float32)
+    sc = scenes.Scene("single", p, x0, v0, 0.02, [])
+    s = oracle.System(sc, mode=0)
+    dt, g = p["dt"], np.asarray(p["g"])
+    for nstep in range(1, 31):
+        out = s.substep()
+    n = 30
+    expect = x0[0] + n * dt * v0[0] + g * dt * dt * n * (n + 1) / 2
+    np.testing.assert_allclose(out["x_new"][0], expect, rtol=0, atol=5e-7)
+    np.testing.assert_allclose(out["v_new"][0], v0[0] + n * dt * g, atol=5e-7)
+
+
+def test_two_particle_pressure_force_is_repulsive_and_symmetric():
+    p = _params(nu=0.0)
+    p["flags"] = 0           # no clamp: the pair is below rest density -> attraction
+    x = np.array([[0.2, 0.2, 0.2], [0.2 + 0.015, 0.2 + 0.01, 0.2]], np.float32)
+    sc = scenes.Scene("pair", p, x, np.zeros_like(x), 0.02, [])
+    out = oracle.System(sc, mode=0).substep()
+    g = np.asarray(p["g"])
+    a = out["acc"] - g
+    ids = out["id"]
+    d = x[1] - x[0]
+    a0, a1 = a[ids == 0][0], a[ids == 1][0]
+    np.testing.assert_allclose(a0, -a1, rtol=1e-12)
+    # below rest density the linear EOS gives negative pressure: particles attract
+    assert np.dot(a0, d) > 0
+    assert np.linalg.norm(np.cross(a0, d)) < 1e-9 * np.linalg.norm(a0) * np.linalg.norm(d)
+    # heavy particles (mass rho0 (0.04)^3, density above rho0, positive pressure) repel
+    sc2 = scenes.Scene("pair", p, x, np.zeros_like(x), 0.04, [])
+    out2 = oracle.System(sc2, mode=0).substep()
+    a2 = out2["acc"] - g
+    assert np.dot(a2[out2["id"] == 0][0], d) < 0
+
+
+@pytest.mark.slow
+def test_hydrostatic_column_settles_to_rho0_g_depth():
+    # settled column: interior pressure p(d) ~ rho0 g d (this fails for a gradient that
+    # is off by a factor of two); run the grid oracle for 1.5 s of simulated time
+    sc = scenes.column(seed=0, n=(5, 5, 16))
+    sc.params["nu"] = 5e-3
+    s = oracle.System(sc, mode=1)
+    for _ in range(1500):
+        out = s.substep()
+    ids = out["id"]
+    fluid = ids < sc.n_fluid
+    z = out["x_new"][fluid, 2]
+    pres = out["pres"][fluid]
+    top = np.sort(z)[-25:].mean()
+    depth = top - z
+    sel = (depth > 0.08) & (depth < 0.26)
+    rho0, g = sc.params["rho0"], 9.81
+    ratio = pres[sel] / (rho0 * g * depth[sel])
+    assert np.median(ratio) == pytest.approx(1.0, abs=0.15)
+    # fluid at rest
+    assert np.abs(out["v_new"][fluid]).max() < 0.05
+    # the walls carry the fluid's weight: F_z on the static body = M_fluid g_z
+    m_f = sc.params["rho0"] * sc.fluid_spacing ** 3
+    weight = sc.n_fluid * m_f * sc.params["g"][2]
+    assert out["wrench"][0, 2] == pytest.approx(weight, rel=0.03)
+    assert abs(out["wrench"][0, 0]) < 0.01 * abs(weight)
+
+
+# ------------------------------------------------------------------- bodies (Sec. 3.2)
+
+def test_fp32_rotation_matches_scipy():
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        R = oracle.rot_f32(q.astype(np.float32)).reshape(3, 3)
+        ref = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        np.testing.assert_allclose(R, ref, atol=3e-7)
+        l = rng.normal(size=3).astype(np.float32)
+        t = rng.normal(size=3).astype(np.float32)
+        np.testing.assert_allclose(oracle.body_point_f32(R.ravel(), t, l), ref @ l + t, atol=2e-6)
+
+
+def test_rigid_body_free_flight():
+    # an isolated rigid body: no pair forces, so it falls with g and spins torque-free
+    p = _params(lo=(-1, -1, -1), hi=(1, 1, 1))
+    loc, _ = scenes.solid_box((0.04, 0.02, 0.06), 0.01)
+    I = scenes._box_inertia(0.3, (0.04, 0.02, 0.06))
+    w0 = np.array([0.0, 0.0, 2.0], np.float32)   # principal axis: stays constant
+    b = scenes.Body(scenes.KIND_RIGID, loc, 0.01, mass=0.3, inertia=I,
+                    pose=np.array([0, 0, 0, 1, 0, 0, 0], np.float32),
+                    vel=np.array([0.1, 0, 0, *w0], np.float32))
+    sc = scenes.Scene("rb", p, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                      0.02, [b])
+    s = oracle.System(sc, mode=0)
+    for _ in range(20):
+        out = s.substep()
+    st = s.body_state(0)
+    dt = p["dt"]
+    np.testing.assert_allclose(st[7:10], [0.1, 0, -9.81 * 20 * dt], atol=1e-6)
+    np.testing.assert_allclose(st[10:13], w0, atol=1e-6)
+    assert np.linalg.norm(st[3:7]) == pytest.approx(1.0, abs=1e-6)
+    # rotation angle about z after 20 steps of dt with w = 2 rad/s
+    ang = 2 * np.arctan2(st[6], st[3])
+    assert ang == pytest.approx(2.0 * 20 * dt, rel=1e-3)
+    assert np.all(out["wrench"] == 0)
+
+
+def test_two_particle_spring_period():
+    # soft body of two particles and one spring, no SPH pressure (clamped), no viscosity,
+    # no damping: relative motion has period 2 pi sqrt(m / (2 k_s))
+    s_ = 0.02
+    p = _params(h=s_, dt=2e-5, nu=0.0, lo=(-1, -1, -1), hi=(1, 1, 1))
+    p["spring_zeta"] = 0.0
+    rest = np.array([[0, 0, 0], [s_, 0, 0]], np.float32)
+    start = np.array([[0, 0, 0], [1.1 * s_, 0, 0]], np.float32)
+    E = 50.0
+    b = scenes.Body(scenes.KIND_SOFT, rest, s_, springs=np.array([[0, 1]], np.int32), young=E)
+    sc = scenes.Scene("spring", p, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                      s_, [b])
+    sysm = oracle.System(sc, mode=0)
+    sysm.x = start.copy()
+    m = 1000.0 * s_ ** 3
+    ks = E * s_ * s_ / s_
+    T = 2 * np.pi * np.sqrt(m / (2 * ks))
+    ext = []
+    nsteps = int(2.5 * T / p["dt"])
+    for _ in range(nsteps):
+        out = sysm.substep()
+        xs = sysm.by_id(out["x_new"])
+        ext.append(xs[1, 0] - xs[0, 0] - s_)
+    ext = np.asarray(ext)
+    cross = np.nonzero((ext[:-1] > 0) & (ext[1:] <= 0))[0]
+    period = (cross[1] - cross[0]) * p["dt"]
+    assert period == pytest.approx(T, rel=0.01)
+
+
+def test_boxcar_smoothing():
+    const = np.tile(np.arange(6, dtype=np.float64), (50, 1))
+    np.testing.assert_allclose(oracle.boxcar(const, 20), const)
+    step = np.zeros((40, 6))
+    step[10:] = 1.0
+    out = oracle.boxcar(step, 20)
+    assert out[9, 0] == 0.0
+    # mean over the last `window` entries (fewer during the first window)
+    expect = [step[max(0, t - 19):t + 1, 0].mean() for t in range(40)]
+    np.testing.assert_allclose(out[:, 0], expect, rtol=1e-15)
+    np.testing.assert_allclose(out[29:, 0], 1.0)

@@ -1,0 +1,251 @@
+/*
+ * sph.h -- C ABI of the GB300 SPH substep with two-way solid coupling
+ * (SPHaptics, arXiv 2511.15908).
+ *
+ * One handle simulates one scene on one GPU: fluid particles, static walls, rigid
+ * bodies and mass-spring soft bodies, all represented as SPH particles (Sec. 3.2).
+ * Each substep runs the spatial hash of Alg. 2 (cell, count, cumulative sum, sorted
+ * index), soft-body springs, the density/pressure pass and the force/integrate pass of
+ * Alg. 1, reduces the boundary-particle coupling forces of every rigid body to a wrench
+ * in FP64, and integrates the free rigid bodies; the grabbed body's wrench is what the
+ * haptic device feels (Sec. 3.3).
+ *
+ * Conventions shared by every call:
+ *   - Ownership: all device memory lives in ONE caller-owned device buffer (the
+ *     workspace) whose size sph_workspace_bytes() returns.  The library never calls
+ *     cudaMalloc or cudaFree; host arrays passed in are copied before the call returns
+ *     and are never retained.  sph_destroy() frees only the host-side handle.
+ *   - Streams: every device operation is enqueued on the stream given at creation, in
+ *     call order.  Calls marked "synchronises" wait for that stream.
+ *   - Errors: every call returns sph_status; nothing throws across the ABI.  Device-side
+ *     conditions (non-finite state, particles leaving the domain, cell overflow, a
+ *     bounded wait that gave up) are latched in a status word in the workspace and
+ *     reported by the next synchronising call.  sph_last_error() gives a message.
+ *   - Particle ids are persistent: fluid particles are 0..n_fluid-1 in the order given
+ *     to sph_create, then each body's particles in the order the bodies were added.
+ *   - Setup calls (sph_add_*) are legal only before the first sph_step (SPH_ERR_STATE).
+ *   - Layouts: positions and velocities are packed xyz triples (n x 3 floats); poses are
+ *     (x, y, z, qw, qx, qy, qz); body velocities (vx, vy, vz, wx, wy, wz); wrenches
+ *     (Fx, Fy, Fz, tx, ty, tz) in doubles, torque about the grab point.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_handle sph_handle;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_ARG = 1,        /* bad argument (null pointer, size out of range) */
+    SPH_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    SPH_ERR_WORKSPACE = 3,  /* workspace too small or misaligned */
+    SPH_ERR_CAPACITY = 4,   /* more particles/bodies/springs than the capacity given */
+    SPH_ERR_NONFINITE = 5,  /* a particle position or velocity became NaN/Inf */
+    SPH_ERR_DOMAIN = 6,     /* a particle left the grid domain (its cell was clamped) */
+    SPH_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up */
+    SPH_ERR_STATE = 8       /* call not legal in the current state */
+} sph_status;
+
+/* sph_params.flags */
+enum {
+    SPH_FLAG_CLAMP_PRESSURE = 1u << 0, /* negative pressures from the linear EOS become 0 */
+    SPH_FLAG_RECORD = 1u << 1,         /* keep per-particle acceleration, neighbour
+                                          counts and static-body wrenches (test hook) */
+    SPH_FLAG_NO_GRAPH = 1u << 2        /* launch kernels directly instead of replaying a
+                                          captured CUDA graph */
+};
+
+/* Body kinds (Sec. 3.2 particle types). */
+enum { SPH_BODY_STATIC = 1, SPH_BODY_RIGID = 2, SPH_BODY_SOFT = 3 };
+
+/*
+ * Scene parameters, copied at creation.
+ *   h            smoothing length of the cubic spline (Sec. 3.1, Eq. kernel); the
+ *                support radius is 2h.
+ *   rho0, k      rest density and pressure constant of p = k (rho - rho0)
+ *                (Sec. 3.1, Eq. pressure).
+ *   nu           kinematic viscosity of F^viscosity = m nu lap v (Alg. 1).
+ *   g            gravity, the external force per unit mass (Alg. 1).
+ *   dt           substep of the semi-implicit Euler update (Sec. 3.1, Eq. euler).
+ *   domain_lo/hi box covered by the uniform grid; one margin cell is added per side.
+ *   cell         grid cell edge; must be >= 2h (the 27-cell neighbourhood covers the
+ *                support).  A cell slightly above 2h (e.g. 2h * 1.001) guarantees that
+ *                FP32 rounding of cell coordinates never hides a neighbour.
+ *   visc_eps     regulariser of the viscous term, r^2 + visc_eps h^2.
+ *   spring_zeta  damping ratio of soft-body springs.
+ *   fluid_spacing lattice spacing of the fluid; fluid SPH mass = rho0 * spacing^3.
+ *   flags        SPH_FLAG_*.
+ *   smooth_window number of update cycles (sph_step calls) in the rolling average of
+ *                the haptic wrench (Sec. 3.3); 1 disables smoothing.
+ */
+typedef struct {
+    float h, rho0, k, nu;
+    float g[3];
+    float dt;
+    float domain_lo[3], domain_hi[3];
+    float cell;
+    float visc_eps, spring_zeta;
+    float fluid_spacing;
+    uint32_t flags;
+    int32_t smooth_window;
+} sph_params;
+
+/*
+ * Capacities fixed at creation (they size the workspace).
+ *   max_particles  fluid + all body particles
+ *   max_bodies     static + rigid + soft bodies (at most 64)
+ *   max_springs    soft-body springs (each counted once)
+ *   max_path       entries of the grab path (sph_set_grab_path) and of the per-substep
+ *                  wrench log
+ */
+typedef struct {
+    int32_t max_particles, max_bodies, max_springs, max_path;
+} sph_capacity;
+
+/* Bytes of device workspace a scene with these parameters and capacities needs
+ * (0 if the arguments are invalid).  The grid size follows from domain and cell. */
+size_t sph_workspace_bytes(const sph_params *p, const sph_capacity *cap);
+
+/*
+ * Create a simulation.
+ *   d_workspace  device pointer, 256-byte aligned, `bytes` >= sph_workspace_bytes();
+ *                owned by the caller and used exclusively by this handle until
+ *                sph_destroy.
+ *   cuda_stream  cudaStream_t on which every device operation is enqueued (0 = legacy
+ *                default stream).
+ *   n_fluid      fluid particles; h_xyz (n_fluid x 3, host, copied) positions,
+ *                h_vel (n_fluid x 3, host, nullable -> zero) velocities.
+ * Synchronises.  Errors: SPH_ERR_ARG, SPH_ERR_WORKSPACE, SPH_ERR_CAPACITY, SPH_ERR_CUDA.
+ */
+sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_workspace,
+                      size_t bytes, void *cuda_stream, int32_t n_fluid, const float *h_xyz,
+                      const float *h_vel, sph_handle **out);
+
+/*
+ * Add a static or rigid body sampled by n boundary particles (Sec. 3.2: a rigid body is
+ * a set of particles at fixed offsets from its parent transform).
+ *   h_local      n x 3 body-frame offsets about the centre of mass (host, copied).
+ *   spacing      sampling spacing; each particle's SPH mass is rho0 * spacing^3.
+ *   body_mass    inertial mass; 0 makes the body static (its particles are placed once
+ *                at pose and never move).
+ *   inertia      3x3 body-frame inertia tensor, row-major (ignored when static).
+ *   pose         initial pose; vel initial (v, w) (nullable -> zero).
+ * Errors: SPH_ERR_ARG, SPH_ERR_CAPACITY, SPH_ERR_STATE, SPH_ERR_CUDA.
+ */
+sph_status sph_add_rigid(sph_handle *h, int32_t n, const float *h_local, float spacing,
+                         float body_mass, const float inertia[9], const float pose[7],
+                         const float vel[6], int32_t *out_body_id);
+
+/*
+ * Add a mass-spring soft body (Sec. 3.2: surface/lattice particles joined by distance
+ * springs, integrated like fluid particles and interacting with everything through SPH).
+ *   h_xyz        n x 3 world positions at creation (host, copied); rest lengths are the
+ *                creation distances.
+ *   h_pairs      n_springs x 2 local particle indices (host, copied); the lookup table
+ *                of Alg. 2's spring pass is built from it here, once.
+ *   young_E      Young's modulus; each spring gets k_s = E s^2 / L0 (E s on lattice axis
+ *                springs) and damping 2 zeta sqrt(k_s m / 2).
+ *   poisson_nu   recorded only: a spring lattice cannot represent a Poisson ratio.
+ * Errors: SPH_ERR_ARG, SPH_ERR_CAPACITY, SPH_ERR_STATE, SPH_ERR_CUDA.
+ */
+sph_status sph_add_soft(sph_handle *h, int32_t n, const float *h_xyz, float spacing,
+                        int32_t n_springs, const int32_t *h_pairs, float young_E,
+                        float poisson_nu, int32_t *out_body_id);
+
+/*
+ * Grab (or release with body_id = -1) a rigid body with the haptic device (Sec. 3.3):
+ * a grabbed body stops integrating; its pose and velocity are set by the device and the
+ * forces on it are read with sph_get_grab_wrench.
+ *   pose, vel         device pose (7) and velocity (6) applied from the next substep.
+ *   grab_point_local  grab point in the body frame (nullable -> centre of mass); the
+ *                     wrench torque is taken about it.
+ * Enqueued on the stream (host arrays copied before return).
+ */
+sph_status sph_set_grab_pose(sph_handle *h, int32_t body_id, const float pose[7],
+                             const float vel[6], const float grab_point_local[3]);
+
+/*
+ * Give the grabbed body a prescribed path: substep s after this call uses entry
+ * min(s, n - 1) of h_path (n x 13: pose 7, velocity 6; host, copied).  n = 0 clears the
+ * path (the last pose stays).  Lets a whole device-motion trajectory run without a host
+ * round trip per substep.
+ */
+sph_status sph_set_grab_path(sph_handle *h, int32_t n, const float *h_path);
+
+/*
+ * Advance n_substeps substeps (Alg. 2 inner loop; rigid bodies updated every substep).
+ * Asynchronous on the handle's stream; replays a captured CUDA graph unless
+ * SPH_FLAG_NO_GRAPH.  One call is one update cycle of the haptic smoothing window.
+ */
+sph_status sph_step(sph_handle *h, int32_t n_substeps);
+
+/*
+ * Wrench on the grabbed body after the last substep (raw, smoothed = 0), or its rolling
+ * average over the last smooth_window update cycles (smoothed = 1) (Sec. 3.3).  Force =
+ * sum of the pair forces on the body's particles (gravity excluded); torque about the
+ * grab point.  Synchronises; returns latched device errors.
+ */
+sph_status sph_get_grab_wrench(sph_handle *h, double out[6], int32_t smoothed);
+
+/* Wrench of any static or rigid body after the last substep (static bodies only with
+ * SPH_FLAG_RECORD).  Synchronises. */
+sph_status sph_get_body_wrench(sph_handle *h, int32_t body_id, double out[6]);
+
+/* Per-substep wrench log of the grabbed body: the last n substeps, oldest first
+ * (n <= min(substeps run, max_path)).  Synchronises. */
+sph_status sph_get_wrench_log(sph_handle *h, int32_t n, double *out);
+
+/* Body state (t 3, q 4, v 3, w 3) after the last substep.  Synchronises. */
+sph_status sph_get_body(sph_handle *h, int32_t body_id, float out[13]);
+
+/*
+ * Particle state in id order (each pointer nullable; host arrays of max n entries):
+ * positions and velocities (n x 3) after the last substep, density (n) of the last
+ * density pass, neighbour counts (n, j != i) and accelerations (n x 3: total for fluid
+ * and soft particles including gravity, pair force / mass for boundary particles) of the
+ * last substep when SPH_FLAG_RECORD is set.  Synchronises.
+ */
+sph_status sph_get_state(sph_handle *h, float *h_x, float *h_v, float *h_rho, int32_t *h_nnbr,
+                         float *h_acc);
+
+/* Overwrite fluid and soft particle positions/velocities (id order, n x 3, host,
+ * nullable); boundary particles follow their bodies.  Synchronises. */
+sph_status sph_set_state(sph_handle *h, const float *h_x, const float *h_v);
+
+/*
+ * Spatial-hash result of the last substep (test hook): cell key of each sorted slot
+ * (n), particle id of each sorted slot (n), cell_start (n_cells + 1).  Nullable.
+ * Synchronises.
+ */
+sph_status sph_get_sort(sph_handle *h, uint32_t *h_keys, int32_t *h_ids, uint32_t *h_cell_start);
+
+/*
+ * Diagnostics of the last substep, FP64: [0..2] sum of all pair forces (Newton's third
+ * law makes it 0), [3] sum of their magnitudes, [4..6] momentum of fluid and soft
+ * particles, [7] sum of m |v|.  Synchronises.
+ */
+sph_status sph_get_diag(sph_handle *h, double out[8]);
+
+/* Counts: particles, fluid particles, grid cells (nx*ny*nz), bodies, substeps run. */
+sph_status sph_get_info(sph_handle *h, int64_t out[5]);
+
+/* Wait for the stream and report latched device errors. */
+sph_status sph_sync(sph_handle *h);
+
+/* Message of the last error on this handle (never NULL; "" if none). */
+const char *sph_last_error(const sph_handle *h);
+
+/* Free the host-side handle and its CUDA graphs; the workspace stays the caller's. */
+void sph_destroy(sph_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_GB300_H */

@@ -1,0 +1,94 @@
+// sph_internal.cuh -- device-side data layout shared by the kernels and the C ABI.
+//
+// Particle state is SoA float4 in HBM: x = (x, y, z, SPH mass), v = (vx, vy, vz, id bits).
+// Two copies exist: B holds the state in the previous substep's sorted order (the
+// "current slot order" the stable sort ties on), A the copy reordered into this
+// substep's cell order, which the density and force passes read.  The force pass writes
+// the new state back into B, still in A's order, so the next substep's hash reads B.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sphgb {
+
+constexpr int kMaxBodies = 64;
+constexpr int kMaxCellRun = 1536;   // particles scanned per x-run of 3 cells before the
+                                    // status word reports SPH_ERR_CAPACITY
+constexpr int kMaxCell = 512;       // particles per cell for the deterministic rank
+constexpr int kScanTile = 2048;     // cells per scan block (256 threads x 8)
+constexpr int kReduceChunk = 1024;  // body particles per wrench-reduction block
+
+// status word bits (mirrors sph_status codes as bit positions)
+enum : uint32_t {
+    ST_NONFINITE = 1u << 5,
+    ST_DOMAIN = 1u << 6,
+    ST_TIMEOUT = 1u << 7,
+    ST_CAPACITY = 1u << 4,
+};
+
+struct DevBody {
+    int kind, first, n, grabbed;
+    int path_n, path_step0, pad0, pad1;
+    float mass;
+    float inertia[9];
+    float t[3], q[4], v[3], w[3];
+    float grab_local[3];
+};
+
+// Everything a substep kernel needs, passed by value (lives in the constant bank).
+struct SimConst {
+    int n, nf, nb, n_body_particles;
+    int nx, ny, nz, ncell;
+    float o[3], inv_cell;
+    float R2, h, inv_h;
+    float rho0, k, nu20;       // nu20 = 2 (d + 2) nu * 2 with d = 3 (the 2 from rho_bar)
+    float eps_h2;
+    float alpha_w;             // 3 / (2 pi h^3)
+    float alpha_g;             // alpha_w / h^2
+    float g[3], dt;
+    uint32_t flags;
+    int grab;                  // grabbed body index or -1 (host view at launch)
+    int max_path;
+    int n_scan_tiles;
+    int n_force_blocks;
+    int n_wblocks;
+    int smooth_window;
+    int body_end[kMaxBodies];  // exclusive id end of each body (ids ascending)
+    int body_kind[kMaxBodies];
+
+    float4 *xA, *vA, *xB, *vB;
+    float2 *prho;              // (rho, p / rho^2) in sorted order
+    uint32_t *key, *rank, *perm, *cnt, *cell_start, *tile_sum;
+    int *slot_of_id;           // id -> sorted slot (soft particles only)
+    float4 *locals;            // per body particle (id - nf): body-frame offset
+    int *spring_row;           // per body particle (id - nf), CSR row start (+1 entry)
+    float4 *spring_e;          // (partner id bits, L0, k_s, c_d)
+    float4 *fb, *xb;           // per body particle: coupling force, position
+    float4 *acc_dbg;
+    int *nnbr;
+    DevBody *body;
+    float *path;               // max_path x 13
+    double *wrench;            // kMaxBodies x 6
+    double *wrench_part;       // n_wblocks x 6
+    int4 *wblock;              // (body, l0, l1, 0) per reduction block
+    double *diag_part;         // n_force_blocks x 8
+    double *diag;              // 8
+    double *wlog;              // max_path x 6
+    double *cyc_log;           // smooth_window x 6
+    uint32_t *status;          // [0] bits, [1] non-finite count, [2] domain count
+    uint32_t *ctr;             // [0] substep counter, [1] reduce ticket, [2] cycle counter
+};
+
+// Launchers (sph_kernels.cu).  All enqueue on `s` and return the launch error.
+cudaError_t launch_substep(const SimConst &c, cudaStream_t s);
+cudaError_t launch_cycle_end(const SimConst &c, cudaStream_t s);
+cudaError_t launch_set_grab(const SimConst &c, cudaStream_t s, int body, int grab,
+                            const float *pose_vel13, const float *grab_local, int set_pose,
+                            int path_n);
+cudaError_t launch_gather_by_id(const SimConst &c, cudaStream_t s, float4 *x_out, float4 *v_out,
+                                float *rho_out, int *nnbr_out, float4 *acc_out);
+cudaError_t launch_scatter_state(const SimConst &c, cudaStream_t s, const float4 *x_in,
+                                 const float4 *v_in);
+cudaError_t launch_sorted_keys(const SimConst &c, cudaStream_t s, uint32_t *keys, int *ids);
+
+}  // namespace sphgb

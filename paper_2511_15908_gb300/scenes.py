@@ -349,3 +349,18 @@ def column(seed=0, n=(6, 6, 20), spacing=0.02, dt=1e-3):
     params = make_params(s, dt, (-3 * s, -3 * s, -3 * s),
                          (box_hi[0] + 3 * s, box_hi[1] + 3 * s, box_hi[2] + 3 * s))
     return Scene("column", params, fluid, np.zeros_like(fluid), s, [walls], n_substeps=2000)
+
+
+def with_velocity_noise(scene: Scene, seed: int = 0, sigma: float = 0.2) -> Scene:
+    """Seeded Gaussian fluid velocities and rigid-body velocities (exercises viscosity
+    and the kinematic boundary velocities from the very first substep)."""
+    rng = np.random.default_rng(seed)
+    scene.fluid_v = rng.normal(0.0, sigma, scene.fluid_x.shape).astype(np.float32)
+    for b in scene.bodies:
+        if b.kind == KIND_RIGID:
+            b.vel = rng.normal(0.0, sigma, 6).astype(np.float32)
+            b.vel[3:] *= 5.0
+    if scene.trajectory is not None:
+        scene.trajectory = scene.trajectory.copy()
+        scene.trajectory[:, 10:13] = rng.normal(0.0, sigma, 3).astype(np.float32)
+    return scene

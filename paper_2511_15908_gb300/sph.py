@@ -1,0 +1,294 @@
+"""Python binding of the C ABI in ``include/sph.h`` (argument marshalling only).
+
+Every step of the substep runs in ``libsph_gb300.so``; this module loads it with ctypes,
+allocates the workspace as one torch uint8 CUDA tensor and passes plain pointers.  There
+is no CPU fallback: without the built library or a CUDA device, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import scenes as _scenes
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsph_gb300.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_CAPACITY, ERR_NONFINITE, ERR_DOMAIN, ERR_TIMEOUT, \
+    ERR_STATE = range(9)
+FLAG_CLAMP_PRESSURE, FLAG_RECORD, FLAG_NO_GRAPH = 1, 2, 4
+BODY_STATIC, BODY_RIGID, BODY_SOFT = 1, 2, 3
+
+# Every symbol the header declares (checked by the CPU test suite).
+SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
+           "sph_set_grab_pose", "sph_set_grab_path", "sph_step", "sph_get_grab_wrench",
+           "sph_get_body_wrench", "sph_get_wrench_log", "sph_get_body", "sph_get_state",
+           "sph_set_state", "sph_get_sort", "sph_get_diag", "sph_get_info", "sph_sync",
+           "sph_last_error", "sph_destroy"]
+
+
+class SphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"sph status {status}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_float), ("rho0", ctypes.c_float), ("k", ctypes.c_float),
+                ("nu", ctypes.c_float), ("g", ctypes.c_float * 3), ("dt", ctypes.c_float),
+                ("domain_lo", ctypes.c_float * 3), ("domain_hi", ctypes.c_float * 3),
+                ("cell", ctypes.c_float), ("visc_eps", ctypes.c_float),
+                ("spring_zeta", ctypes.c_float), ("fluid_spacing", ctypes.c_float),
+                ("flags", ctypes.c_uint32), ("smooth_window", ctypes.c_int32)]
+
+
+class Capacity(ctypes.Structure):
+    _fields_ = [("max_particles", ctypes.c_int32), ("max_bodies", ctypes.c_int32),
+                ("max_springs", ctypes.c_int32), ("max_path", ctypes.c_int32)]
+
+
+_lib = None
+_f32p = ctypes.POINTER(ctypes.c_float)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+
+def load(path: str = LIB_PATH):
+    """Load the sm_103a library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2511_15908_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    st = ctypes.c_int
+    L.sph_workspace_bytes.restype = ctypes.c_size_t
+    L.sph_workspace_bytes.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Capacity)]
+    L.sph_create.restype = st
+    L.sph_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Capacity), _vp, ctypes.c_size_t,
+                             _vp, ctypes.c_int32, _f32p, _f32p, ctypes.POINTER(_vp)]
+    L.sph_add_rigid.restype = st
+    L.sph_add_rigid.argtypes = [_vp, ctypes.c_int32, _f32p, ctypes.c_float, ctypes.c_float, _f32p,
+                                _f32p, _f32p, _i32p]
+    L.sph_add_soft.restype = st
+    L.sph_add_soft.argtypes = [_vp, ctypes.c_int32, _f32p, ctypes.c_float, ctypes.c_int32, _i32p,
+                               ctypes.c_float, ctypes.c_float, _i32p]
+    L.sph_set_grab_pose.restype = st
+    L.sph_set_grab_pose.argtypes = [_vp, ctypes.c_int32, _f32p, _f32p, _f32p]
+    L.sph_set_grab_path.restype = st
+    L.sph_set_grab_path.argtypes = [_vp, ctypes.c_int32, _f32p]
+    L.sph_step.restype = st
+    L.sph_step.argtypes = [_vp, ctypes.c_int32]
+    L.sph_get_grab_wrench.restype = st
+    L.sph_get_grab_wrench.argtypes = [_vp, _f64p, ctypes.c_int32]
+    L.sph_get_body_wrench.restype = st
+    L.sph_get_body_wrench.argtypes = [_vp, ctypes.c_int32, _f64p]
+    L.sph_get_wrench_log.restype = st
+    L.sph_get_wrench_log.argtypes = [_vp, ctypes.c_int32, _f64p]
+    L.sph_get_body.restype = st
+    L.sph_get_body.argtypes = [_vp, ctypes.c_int32, _f32p]
+    L.sph_get_state.restype = st
+    L.sph_get_state.argtypes = [_vp, _f32p, _f32p, _f32p, _i32p, _f32p]
+    L.sph_set_state.restype = st
+    L.sph_set_state.argtypes = [_vp, _f32p, _f32p]
+    L.sph_get_sort.restype = st
+    L.sph_get_sort.argtypes = [_vp, _u32p, _i32p, _u32p]
+    L.sph_get_diag.restype = st
+    L.sph_get_diag.argtypes = [_vp, _f64p]
+    L.sph_get_info.restype = st
+    L.sph_get_info.argtypes = [_vp, _i64p]
+    L.sph_sync.restype = st
+    L.sph_sync.argtypes = [_vp]
+    L.sph_last_error.restype = ctypes.c_char_p
+    L.sph_last_error.argtypes = [_vp]
+    L.sph_destroy.restype = None
+    L.sph_destroy.argtypes = [_vp]
+    _lib = L
+    return L
+
+
+def _ptr(a: Optional[np.ndarray], ctype):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def make_params(p: dict, fluid_spacing: float, flags: Optional[int] = None) -> Params:
+    P = Params()
+    P.h, P.rho0, P.k, P.nu = p["h"], p["rho0"], p["k"], p["nu"]
+    for a in range(3):
+        P.g[a] = p["g"][a]
+        P.domain_lo[a] = p["lo"][a]
+        P.domain_hi[a] = p["hi"][a]
+    P.dt, P.cell = p["dt"], p["cell"]
+    P.visc_eps, P.spring_zeta = p["visc_eps"], p["spring_zeta"]
+    P.fluid_spacing = fluid_spacing
+    P.flags = int(p["flags"] if flags is None else flags)
+    P.smooth_window = int(p.get("smooth_window", 20))
+    return P
+
+
+class Simulation:
+    """One scene on one GPU behind the C ABI.  The workspace is a torch CUDA tensor."""
+
+    def __init__(self, scene: _scenes.Scene, flags: Optional[int] = None, max_path: Optional[int] = None,
+                 device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the SPH library needs a CUDA device")
+        self.L = load()
+        self.scene = scene
+        self.device = torch.device("cuda", device)
+        self.params = make_params(scene.params, scene.fluid_spacing, flags)
+        n_springs = sum(0 if b.springs is None else int(b.springs.shape[0]) for b in scene.bodies)
+        traj_n = 0 if scene.trajectory is None else int(scene.trajectory.shape[0])
+        self.cap = Capacity(scene.n_total, max(1, len(scene.bodies)), n_springs,
+                            max_path if max_path is not None else max(traj_n, 4096))
+        nbytes = self.L.sph_workspace_bytes(ctypes.byref(self.params), ctypes.byref(self.cap))
+        if nbytes == 0:
+            raise SphError(ERR_ARG, "invalid parameters or capacities")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        x = np.ascontiguousarray(scene.fluid_x, np.float32)
+        v = np.ascontiguousarray(scene.fluid_v, np.float32)
+        h = _vp()
+        st = self.L.sph_create(ctypes.byref(self.params), ctypes.byref(self.cap),
+                               self.workspace.data_ptr(), nbytes, self.stream.cuda_stream,
+                               x.shape[0], _ptr(x, ctypes.c_float), _ptr(v, ctypes.c_float),
+                               ctypes.byref(h))
+        if st != OK:
+            raise SphError(st, "sph_create failed")
+        self.h = h
+        self.body_ids = []
+        for b in scene.bodies:
+            bid = ctypes.c_int32()
+            xyz = np.ascontiguousarray(b.xyz, np.float32)
+            if b.kind == _scenes.KIND_SOFT:
+                pairs = np.ascontiguousarray(b.springs, np.int32)
+                self._check(self.L.sph_add_soft(self.h, b.n, _ptr(xyz, ctypes.c_float), b.spacing,
+                                                pairs.shape[0], _ptr(pairs, ctypes.c_int32),
+                                                b.young, b.poisson, ctypes.byref(bid)))
+            else:
+                mass = b.mass if b.kind == _scenes.KIND_RIGID else 0.0
+                inertia = np.ascontiguousarray(b.inertia, np.float32).reshape(9)
+                pose = np.ascontiguousarray(b.pose, np.float32)
+                vel = np.ascontiguousarray(b.vel, np.float32)
+                self._check(self.L.sph_add_rigid(self.h, b.n, _ptr(xyz, ctypes.c_float), b.spacing,
+                                                 mass, _ptr(inertia, ctypes.c_float),
+                                                 _ptr(pose, ctypes.c_float), _ptr(vel, ctypes.c_float),
+                                                 ctypes.byref(bid)))
+            self.body_ids.append(bid.value)
+        if scene.grab_body >= 0:
+            gl = np.ascontiguousarray(scene.bodies[scene.grab_body].grab_local, np.float32)
+            traj = scene.trajectory
+            pose = np.ascontiguousarray(traj[0, :7] if traj is not None else scene.bodies[scene.grab_body].pose,
+                                        np.float32)
+            vel = np.ascontiguousarray(traj[0, 7:] if traj is not None else np.zeros(6), np.float32)
+            self._check(self.L.sph_set_grab_pose(self.h, self.body_ids[scene.grab_body],
+                                                 _ptr(pose, ctypes.c_float), _ptr(vel, ctypes.c_float),
+                                                 _ptr(gl, ctypes.c_float)))
+            if traj is not None:
+                t = np.ascontiguousarray(traj[: self.cap.max_path], np.float32)
+                self._check(self.L.sph_set_grab_path(self.h, t.shape[0], _ptr(t, ctypes.c_float)))
+
+    # -- helpers
+    def _check(self, st):
+        if st != OK:
+            msg = self.L.sph_last_error(self.h).decode() if getattr(self, "h", None) else ""
+            raise SphError(st, msg)
+
+    @property
+    def n(self) -> int:
+        return self.info()[0]
+
+    def info(self):
+        out = np.zeros(5, np.int64)
+        self._check(self.L.sph_get_info(self.h, _ptr(out, ctypes.c_int64)))
+        return out
+
+    # -- the calls a user makes
+    def step(self, n: int = 1):
+        self._check(self.L.sph_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.L.sph_sync(self.h))
+
+    def grab_wrench(self, smoothed: bool = False) -> np.ndarray:
+        out = np.zeros(6, np.float64)
+        self._check(self.L.sph_get_grab_wrench(self.h, _ptr(out, ctypes.c_double), int(smoothed)))
+        return out
+
+    def body_wrench(self, b: int) -> np.ndarray:
+        out = np.zeros(6, np.float64)
+        self._check(self.L.sph_get_body_wrench(self.h, b, _ptr(out, ctypes.c_double)))
+        return out
+
+    def wrench_log(self, n: int) -> np.ndarray:
+        out = np.zeros((n, 6), np.float64)
+        self._check(self.L.sph_get_wrench_log(self.h, n, _ptr(out, ctypes.c_double)))
+        return out
+
+    def set_grab_pose(self, body: int, pose, vel=None, grab_local=None):
+        pose = None if pose is None else np.ascontiguousarray(pose, np.float32)
+        vel = None if vel is None else np.ascontiguousarray(vel, np.float32)
+        gl = None if grab_local is None else np.ascontiguousarray(grab_local, np.float32)
+        self._check(self.L.sph_set_grab_pose(self.h, body, _ptr(pose, ctypes.c_float),
+                                             _ptr(vel, ctypes.c_float), _ptr(gl, ctypes.c_float)))
+
+    def set_grab_path(self, path):
+        path = np.ascontiguousarray(path, np.float32).reshape(-1, 13)
+        self._check(self.L.sph_set_grab_path(self.h, path.shape[0], _ptr(path, ctypes.c_float)))
+
+    def body(self, b: int) -> np.ndarray:
+        out = np.zeros(13, np.float32)
+        self._check(self.L.sph_get_body(self.h, b, _ptr(out, ctypes.c_float)))
+        return out
+
+    def state(self, record: bool = False):
+        n = self.n
+        x = np.zeros((n, 3), np.float32)
+        v = np.zeros((n, 3), np.float32)
+        rho = np.zeros(n, np.float32)
+        nn = np.zeros(n, np.int32) if record else None
+        acc = np.zeros((n, 3), np.float32) if record else None
+        self._check(self.L.sph_get_state(self.h, _ptr(x, ctypes.c_float), _ptr(v, ctypes.c_float),
+                                         _ptr(rho, ctypes.c_float), _ptr(nn, ctypes.c_int32),
+                                         _ptr(acc, ctypes.c_float)))
+        return dict(x=x, v=v, rho=rho, nnbr=nn, acc=acc)
+
+    def set_state(self, x=None, v=None):
+        x = None if x is None else np.ascontiguousarray(x, np.float32)
+        v = None if v is None else np.ascontiguousarray(v, np.float32)
+        self._check(self.L.sph_set_state(self.h, _ptr(x, ctypes.c_float), _ptr(v, ctypes.c_float)))
+
+    def sort(self):
+        n = self.n
+        ncell = int(self.info()[2])
+        keys = np.zeros(n, np.uint32)
+        ids = np.zeros(n, np.int32)
+        cs = np.zeros(ncell + 1, np.uint32)
+        self._check(self.L.sph_get_sort(self.h, _ptr(keys, ctypes.c_uint32), _ptr(ids, ctypes.c_int32),
+                                        _ptr(cs, ctypes.c_uint32)))
+        return keys, ids, cs
+
+    def diag(self) -> np.ndarray:
+        out = np.zeros(8, np.float64)
+        self._check(self.L.sph_get_diag(self.h, _ptr(out, ctypes.c_double)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.sph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,277 @@
+"""GPU parity: the sm_103a substep against the FP64 oracle, element by element.
+
+Bar (one substep from the same seeded FP32 state): cell keys, sorted order, cell_start
+and neighbour counts bit-exact; densities within 1e-5 relative; accelerations within
+1e-4 * max(|a|, 0.1 g); body wrench force and torque within 1e-4 relative (torque
+relative to the moment scale sum |x - x_g| |f| when the net torque nearly cancels).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_15908_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+G = 9.81
+RHO_TOL = 1e-5
+ACC_TOL = 1e-4
+WRENCH_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15908_gb300 import build, sph as _sph
+    build.build()
+    _sph.load()
+    return _sph
+
+
+def _by_id(ref, key, n):
+    out = np.empty((n,) + ref[key].shape[1:], ref[key].dtype)
+    out[ref["id"]] = ref[key]
+    return out
+
+
+def _kinds(sc):
+    kinds = np.zeros(sc.n_total, int)
+    first = sc.n_fluid
+    for b in sc.bodies:
+        kinds[first:first + b.n] = b.kind
+        first += b.n
+    return kinds
+
+
+def check_one_substep(sph, sc, mode, record=True):
+    """Run one substep on the GPU and in the oracle; assert the parity bar."""
+    flags = sc.params["flags"] | (sph.FLAG_RECORD if record else 0)
+    sim = sph.Simulation(sc, flags=flags)
+    n = sc.n_total
+    v0 = None
+    if not record:
+        v0 = sim.state()["v"]
+    sim.step(1)
+    keys, ids, cs = sim.sort()
+    st = sim.state(record=record)
+    bodies = [sim.body(b) for b in range(len(sc.bodies))]
+    wr = [sim.body_wrench(i) if (record or body.kind == scenes.KIND_RIGID) else None
+          for i, body in enumerate(sc.bodies)]
+    ref = oracle.System(sc, mode=mode).substep()
+
+    # integer results: bit-exact
+    np.testing.assert_array_equal(keys, ref["key"])
+    np.testing.assert_array_equal(ids, ref["id"])
+    np.testing.assert_array_equal(cs, ref["cell_start"])
+    if record:
+        np.testing.assert_array_equal(st["nnbr"], _by_id(ref, "nnbr", n))
+
+    # density
+    rho_ref = _by_id(ref, "rho", n)
+    rel = np.abs(st["rho"] - rho_ref) / rho_ref
+    assert rel.max() <= RHO_TOL, f"density rel err {rel.max():.3e}"
+
+    # accelerations
+    kinds = _kinds(sc)
+    acc_ref = _by_id(ref, "acc", n)
+    if record:
+        acc = st["acc"].astype(np.float64)
+        sel = np.ones(n, bool)
+    else:
+        acc = (st["v"].astype(np.float64) - v0) / sc.params["dt"]
+        sel = (kinds == 0) | (kinds == scenes.KIND_SOFT)
+    scale = np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * G)
+    err = np.linalg.norm(acc - acc_ref, axis=1) / scale
+    assert err[sel].max() <= ACC_TOL, f"acc err {err[sel].max():.3e} at id {np.argmax(err * sel)}"
+
+    # wrenches and rigid update
+    for b, body in enumerate(sc.bodies):
+        if body.kind == scenes.KIND_SOFT or wr[b] is None:
+            continue
+        F, T = wr[b][:3], wr[b][3:]
+        Fr, Tr = ref["wrench"][b, :3], ref["wrench"][b, 3:]
+        fscale = max(np.linalg.norm(Fr), 1e-9)
+        assert np.linalg.norm(F - Fr) <= WRENCH_TOL * fscale + 1e-9, (b, F, Fr)
+        assert np.linalg.norm(T - Tr) <= WRENCH_TOL * max(np.linalg.norm(Tr), 1e-9) + 1e-9 or \
+            np.linalg.norm(T - Tr) <= 1e-6 * fscale, (b, T, Tr)
+        if body.kind == scenes.KIND_RIGID and sc.grab_body != b and body.mass > 0:
+            np.testing.assert_allclose(bodies[b][:3], ref["body_new"][b, :3], atol=1e-6)
+            np.testing.assert_allclose(bodies[b][7:], ref["body_new"][b, 7:],
+                                       atol=1e-4 * max(1.0, np.abs(ref["body_new"][b, 7:]).max()))
+    # new positions
+    x_ref = _by_id(ref, "x_new", n)
+    assert np.abs(st["x"] - x_ref).max() < 2e-6 * max(1.0, np.abs(x_ref).max())
+    sim.close()
+    return st, ref
+
+
+def test_tiny_scene_all_body_kinds(sph):
+    sc = scenes.tiny(seed=0, n=(6, 6, 6))
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_tiny_scene_no_clamp_random_velocity(sph):
+    sc = scenes.with_velocity_noise(scenes.tiny(seed=1, n=(7, 5, 6)), seed=1, sigma=0.5)
+    sc.params["flags"] = 0
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_dam_break_full_brute_force(sph):
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=0), seed=2, sigma=0.3)
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_dam_break_grabbed_cube(sph):
+    sc = scenes.dam_break(seed=3, grab=True, cube_pos=(0.2, 0.2, 0.2))
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_stirring_tank_reduced(sph):
+    sc = scenes.with_velocity_noise(
+        scenes.stirring_tank(seed=0, n_fluid=30_000, cols=(50, 50), tank=(0.4, 0.4, 0.3),
+                             n_substeps=10, paddle=(0.02, 0.1, 0.2)), seed=3, sigma=0.2)
+    check_one_substep(sph, sc, mode=1)
+
+
+def test_coupled_reduced_with_soft_body(sph):
+    sc = scenes.with_velocity_noise(
+        scenes.coupled(seed=0, n_fluid=60_000, cols=(60, 40), tank=(0.6, 0.4, 0.4), n_substeps=10,
+                       probe_r=0.04, soft_n=8), seed=4, sigma=0.2)
+    check_one_substep(sph, sc, mode=1)
+
+
+def test_stirring_tank_full_size_bench_config(sph):
+    # full size, launched exactly as the benchmark launches it (no record flag)
+    sc = scenes.with_velocity_noise(scenes.stirring_tank(seed=0, n_substeps=10), seed=5, sigma=0.2)
+    check_one_substep(sph, sc, mode=1, record=False)
+
+
+def test_coupled_full_size_bench_config(sph):
+    sc = scenes.with_velocity_noise(scenes.coupled(seed=0, n_substeps=10), seed=6, sigma=0.2)
+    check_one_substep(sph, sc, mode=1, record=False)
+
+
+# ------------------------------------------------------------ properties, edge cases
+
+def test_sort_is_stable_over_substeps_and_deterministic(sph):
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=1), seed=7, sigma=0.5)
+    runs = []
+    for rep in range(2):
+        sim = sph.Simulation(sc)
+        sim.step(1)
+        _, prev_ids, _ = sim.sort()
+        for s in range(5):
+            sim.step(1)
+            keys, ids, cs = sim.sort()
+            assert np.all(np.diff(keys.astype(np.int64)) >= 0)
+            assert np.array_equal(np.sort(ids), np.arange(sc.n_total))
+            prev_slot = np.empty(sc.n_total, np.int64)
+            prev_slot[prev_ids] = np.arange(sc.n_total)
+            ps = prev_slot[ids]
+            same = keys[1:] == keys[:-1]
+            assert np.all(ps[1:][same] > ps[:-1][same]), "ties not in previous-slot order"
+            np.testing.assert_array_equal(cs, np.searchsorted(keys, np.arange(cs.size)))
+            prev_ids = ids
+        st = sim.state()
+        runs.append((st["x"].copy(), st["v"].copy(), sim.body(1).copy()))
+        sim.close()
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b), "two runs of the same scene differ"
+
+
+def test_graph_replay_equals_direct_launches(sph):
+    sc = scenes.dam_break(seed=2)
+    out = []
+    for flags in (sc.params["flags"], sc.params["flags"] | sph.FLAG_NO_GRAPH):
+        sim = sph.Simulation(sc, flags=flags)
+        sim.step(20)
+        sim.step(3)
+        st = sim.state()
+        out.append((st["x"], st["v"], sim.body(1)))
+        sim.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+def test_short_horizon_invariants(sph):
+    sc = scenes.with_velocity_noise(scenes.tiny(seed=3, n=(8, 8, 8)), seed=8, sigma=0.3)
+    sim = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_RECORD)
+    for _ in range(30):
+        sim.step(1)
+        d = sim.diag()
+        # Newton's third law: all pair forces cancel (FP32 pair sums, FP64 reduction)
+        assert np.linalg.norm(d[0:3]) <= 1e-5 * d[3]
+    st = sim.state(record=True)
+    assert np.all(np.isfinite(st["x"])) and np.all(np.isfinite(st["v"]))
+    sim.close()
+
+
+def test_free_fall_single_particle(sph):
+    p = scenes.make_params(0.02, 1e-3, (-1, -1, -1), (1, 1, 1))
+    x0 = np.array([[0.1, 0.2, 0.5]], np.float32)
+    v0 = np.array([[0.3, -0.1, 0.2]], np.float32)
+    sc = scenes.Scene("one", p, x0, v0, 0.02, [])
+    sim = sph.Simulation(sc)
+    sim.step(40)
+    st = sim.state()
+    n, dt = 40, p["dt"]
+    g = np.asarray(p["g"])
+    expect = x0[0] + n * dt * v0[0] + g * dt * dt * n * (n + 1) / 2
+    np.testing.assert_allclose(st["x"][0], expect, atol=2e-6)
+    sim.close()
+
+
+def test_empty_and_body_only_scenes(sph):
+    p = scenes.make_params(0.02, 1e-3, (-0.2, -0.2, -0.2), (0.2, 0.2, 0.2))
+    empty = scenes.Scene("empty", p, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                         0.02, [])
+    sim = sph.Simulation(empty)
+    sim.step(3)
+    sim.sync()
+    sim.close()
+    sc = scenes.tiny(seed=4)
+    sc.fluid_x = np.zeros((0, 3), np.float32)
+    sc.fluid_v = np.zeros((0, 3), np.float32)
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_domain_and_nonfinite_errors_are_reported(sph):
+    p = scenes.make_params(0.02, 1e-3, (0, 0, 0), (0.2, 0.2, 0.2))
+    x = np.array([[0.1, 0.1, 0.1], [5.0, 0.1, 0.1]], np.float32)
+    sc = scenes.Scene("out", p, x, np.zeros_like(x), 0.02, [])
+    sim = sph.Simulation(sc)
+    sim.step(1)
+    with pytest.raises(sph.SphError) as e:
+        sim.sync()
+    assert e.value.status == sph.ERR_DOMAIN
+    sim.sync()            # reported once, then cleared
+    sim.close()
+    x = np.array([[0.1, 0.1, 0.1], [np.nan, 0.1, 0.1]], np.float32)
+    sc = scenes.Scene("nan", p, x, np.zeros_like(x), 0.02, [])
+    sim = sph.Simulation(sc)
+    sim.step(1)
+    with pytest.raises(sph.SphError) as e:
+        sim.sync()
+    assert e.value.status == sph.ERR_NONFINITE
+    sim.close()
+
+
+def test_haptic_smoothing_and_wrench_log(sph):
+    sc = scenes.dam_break(seed=5, grab=True, n_substeps=400, cube_pos=(0.2, 0.2, 0.15))
+    sim = sph.Simulation(sc)
+    W = sc.params["smooth_window"]
+    cycle_raw = []
+    for cyc in range(W + 5):
+        sim.step(4)
+        cycle_raw.append(sim.grab_wrench(smoothed=False))
+        log = sim.wrench_log(4)
+        np.testing.assert_array_equal(log[-1], cycle_raw[-1])
+        sm = sim.grab_wrench(smoothed=True)
+        expect = np.mean(cycle_raw[-W:], axis=0)
+        np.testing.assert_allclose(sm, expect, rtol=1e-12, atol=1e-12)
+    # the grabbed body follows its path exactly
+    b = sim.body(1)
+    np.testing.assert_allclose(b[:3], sc.trajectory[4 * (W + 5) - 1, :3], atol=0)
+    sim.close()

@@ -1,0 +1,368 @@
+"""Benchmark of the SPH coupling substep on GB300 (one JSON line on stdout).
+
+Workload (N=1): the coupled scene -- 1,000,000 fluid particles at 0.01 m in a 2 x 1 x 0.6 m
+tank, two-layer static walls, a 30k-particle sphere probe on a seeded random-walk grab
+path and a 24^3 soft cube (1,161,538 particles in total), dt 5e-4 s.  One step = one
+substep (hash, scan, stable reorder, springs, density, forces + integrate, FP64 wrench
+reduction + rigid update), replayed from the captured CUDA graph.  The state starts in
+HBM; a 256 MB buffer is written between timed steps so every step starts with a cold
+L2 (the working set, ~100-190 MB, is of L2 size).  `value` = fluid particle-steps per
+second over all ranks.
+
+With --gpus N (torchrun) every rank runs its own independent replica (the substep of
+one scene does not shard); value = sum of particles over ranks x steps / max time.
+--impl reference times the FP64 CPU oracle on this host's cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s at 1M particles (fluid particles x substeps / s)"
+UNIT = "particle-steps/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_2511_15908_gb300", "csrc", "sph_kernels.cu")
+
+# Algorithmic cost model (documented in the design notes):
+BYTES_PER_PARTICLE_STEP = 168          # HBM bytes of one substep per particle
+FORCE_BYTES_PER_PARTICLE = 72          # force pass: read x, v, (rho, P); write x, v
+FORCE_FLOPS_PER_PAIR = 42              # pressure + viscosity pair term (FMA = 2 flops)
+DENSITY_FLOPS_PER_PAIR = 21
+FP32_LANES_PER_SM, SMS = 128, 152
+
+
+def _peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _kernel_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel is unchanged."""
+    try:
+        with open(TRAFFIC_PATH) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_sha") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(name):
+    from paper_2511_15908_gb300 import scenes
+    if name == "coupled":
+        return scenes.coupled(seed=0, n_substeps=4096)
+    if name == "stirring":
+        return scenes.stirring_tank(seed=0, n_substeps=4096)
+    if name == "dam_break":
+        return scenes.dam_break(seed=0, n_substeps=4096)
+    raise ValueError(name)
+
+
+def _oracle_substep_time(sc, max_seconds=60.0):
+    """Time one FP64 grid-oracle substep of `sc` on all host cores; returns (s, result)."""
+    import oracle
+    sysm = oracle.System(sc, mode=1)
+    t0 = time.perf_counter()
+    out = sysm.substep()
+    return time.perf_counter() - t0, out
+
+
+def _reference_sample(seed=0):
+    """A bounded sample of the coupled workload for the CPU oracle: the same tank height,
+    spacing, probe and soft cube, on a 1/4-length slab (250k fluid particles)."""
+    from paper_2511_15908_gb300 import scenes
+    return scenes.coupled(seed=seed, n_fluid=250_000, cols=(50, 100), tank=(0.5, 1.0, 0.6),
+                          n_substeps=16)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on this host's cores."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    sc = _reference_sample()
+    sysm = oracle.System(sc, mode=1)
+    for _ in range(args.warmup):
+        sysm.substep()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sysm.substep()
+    dt = time.perf_counter() - t0
+    value = sc.n_fluid * args.steps / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "coupled scene sample: 250k fluid slab of the 1M tank, "
+                                   "FP64 uniform-grid oracle", "particles": sc.n_total},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} substeps of a 250k-fluid slab "
+                                       f"({sc.n_total} particles) of the coupled scene"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2511_15908_gb300 import build, sph
+    build.build()
+    sc = _workload(args.workload)
+    peaks, peak_kind = _peaks()
+
+    # CPU baseline (rank 0, N = 1): the oracle as it stands, one substep, host cores;
+    # its first-substep wrench is also the FP64 reference of the grab-wrench error.
+    cpu = None
+    ref_wrench = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t_cpu, out = _oracle_substep_time(sc)
+        ref_wrench = out["wrench"][sc.grab_body]
+        cpu = {"value": sc.n_fluid / t_cpu, "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"1 substep of the full coupled scene ({sc.n_total} particles), "
+                         f"FP64 uniform-grid oracle, {t_cpu:.1f} s"}
+
+    # neighbour statistics of the first substep (record run) for the algorithmic flop count
+    rec = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_RECORD)
+    rec.step(1)
+    nn = rec.state(record=True)["nnbr"]
+    pairs = float(np.sum(nn, dtype=np.int64) + sc.n_total)   # density includes self
+    rec.close()
+    del rec
+
+    sim = sph.Simulation(sc)
+    sim.set_profiling(True)
+    n_all = sc.n_total
+    # first substep: grab-wrench error against the FP64 oracle
+    sim.step(1)
+    w_gpu = sim.grab_wrench()
+    wrench_err = None
+    if ref_wrench is not None:
+        fe = np.linalg.norm(w_gpu[:3] - ref_wrench[:3]) / max(np.linalg.norm(ref_wrench[:3]), 1e-30)
+        te = np.linalg.norm(w_gpu[3:] - ref_wrench[3:]) / max(np.linalg.norm(ref_wrench[3:]), 1e-30)
+        wrench_err = {"force_rel": float(fe), "torque_rel": float(te)}
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    stream = sim.stream
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+
+    for _ in range(args.warmup):
+        flush_l2()
+        sim.step(1)
+    sim.sync()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ktimes = np.zeros((args.steps, len(sph.KERNELS)))
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush_l2()
+            ev0[i].record(stream)
+            sim.step(1)
+            ev1[i].record(stream)
+            ktimes[i] = sim.kernel_times()          # synchronises the stream
+        torch.cuda.synchronize()
+    sim.sync()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    total_s = float(step_ms.sum()) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        torch.distributed.barrier()
+    value = world * sc.n_fluid * args.steps / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+
+    kmean = ktimes.mean(axis=0)
+    shares = {k: float(v) for k, v in zip(sph.KERNELS, kmean / kmean.sum())}
+    dom = int(np.argmax(kmean))
+    dom_name = sph.KERNELS[dom]
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12      # TFLOP/s
+    t_dom = kmean[dom] / 1e3
+    if dom_name == "force":
+        flops = FORCE_FLOPS_PER_PAIR * (pairs - n_all)
+    elif dom_name == "density":
+        flops = DENSITY_FLOPS_PER_PAIR * pairs
+    else:
+        flops = None
+    if flops is not None:
+        achieved = flops / t_dom / 1e12
+        roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": alu_peak,
+                    "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                    "traffic": _traffic(dom_name),
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz "
+                                   f"(sm_max_mhz of {peak_kind} peaks)"}
+    else:
+        bytes_ = FORCE_BYTES_PER_PARTICLE * n_all
+        achieved = bytes_ / t_dom / 1e9
+        roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                    "traffic": _traffic(dom_name)}
+    force_hbm = FORCE_BYTES_PER_PARTICLE * n_all / (kmean[6] / 1e3) / 1e9
+    step_hbm = BYTES_PER_PARTICLE_STEP * n_all / (ms_per_step / 1e3) / 1e9
+
+    # end to end through the public API: host pose in, one substep, host wrench out
+    path = sc.trajectory
+    e2e_s = 0.0
+    pose_h = torch.empty(13, dtype=torch.float32).pin_memory().numpy()
+    for i in range(args.steps):
+        flush_l2()
+        torch.cuda.synchronize()
+        row = path[(args.warmup + args.steps + i) % path.shape[0]]
+        t0 = time.perf_counter()
+        pose_h[:] = row
+        sim.set_grab_pose(sim.body_ids[sc.grab_body], pose_h[:7], pose_h[7:])
+        sim.step(1)
+        w = sim.grab_wrench()
+        e2e_s += time.perf_counter() - t0
+    e2e_value = world * sc.n_fluid * args.steps / e2e_s
+    sim.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (f64 wrench/momentum reductions)", "data": "synthetic",
+                "config": {"workload": f"{args.workload} scene: {sc.n_fluid} fluid + "
+                                       f"{n_all - sc.n_fluid} boundary/soft particles, dt "
+                                       f"{sc.params['dt']}", "particles_all": n_all,
+                           "particles_fluid": sc.n_fluid, "l2": "flushed between steps",
+                           "parallelism": f"replicas x{world}",
+                           "all_particle_steps_per_s": value * n_all / sc.n_fluid},
+                "gpu_launches": 8 * args.steps,
+                "kernel_ms": {k: float(v) for k, v in zip(sph.KERNELS, kmean)},
+                "kernel_share": shares,
+                "roofline": roofline,
+                "hbm_step": {"bytes_per_particle": BYTES_PER_PARTICLE_STEP,
+                             "achieved_gbs": step_hbm, "peak_gbs": peaks["hbm_gbs"],
+                             "frac": step_hbm / peaks["hbm_gbs"]},
+                "force_hbm_frac": force_hbm / peaks["hbm_gbs"],
+                "grab_wrench_err_vs_oracle": wrench_err,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64,
+                        "d2h_bytes_per_step": 60,
+                        "what": "sph_set_grab_pose (host pose) + sph_step(1) + "
+                                "sph_get_grab_wrench (host wrench, synchronising)"},
+                "clocks": clk.summary(),
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="coupled", choices=["coupled", "stirring", "dam_break"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -235,6 +235,17 @@ sph_status sph_get_diag(sph_handle *h, double out[8]);
 /* Counts: particles, fluid particles, grid cells (nx*ny*nz), bodies, substeps run. */
 sph_status sph_get_info(sph_handle *h, int64_t out[5]);
 
+/*
+ * Per-kernel timing hook (benchmarks).  With profiling on, every later substep records a
+ * CUDA event before and after each of its 8 kernels (as event-record nodes inside the
+ * captured graph, on the handle's stream).  sph_get_kernel_times synchronises and returns
+ * the durations of the last substep in milliseconds, in launch order: hash, scan tiles,
+ * scan apply, scatter, rank + gather, density, force + integrate, wrench reduction.
+ * The events are created by sph_set_profiling(h, 1) (no device memory is allocated).
+ */
+sph_status sph_set_profiling(sph_handle *h, int32_t on);
+sph_status sph_get_kernel_times(sph_handle *h, float out_ms[8]);
+
 /* Wait for the stream and report latched device errors. */
 sph_status sph_sync(sph_handle *h);
 

@@ -98,21 +98,26 @@ def _declare(L):
     L.orc_substep.restype = ctypes.c_int
     L.orc_substep.argtypes = [_P(Params), ctypes.c_int, ctypes.c_int, _f32p, _f32p, _f32p, _i32p,
                               ctypes.c_int, _P(BodyC), ctypes.c_int, _u32p, _i32p, _u32p,
-                              _f64p, _f64p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+                              _f64p, _f64p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
     L.orc_boxcar.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p]
     if hasattr(L, "orc_mlp_forward"):
         from . import mlp as _mlp
         _mlp.declare(L)
 
 
+def _f32(x) -> float:
+    """The method's parameters are FP32 values; the oracle computes with those values."""
+    return float(np.float32(x))
+
+
 def params(p: dict) -> Params:
     P = Params()
-    P.h, P.rho0, P.k, P.nu = p["h"], p["rho0"], p["k"], p["nu"]
+    P.h, P.rho0, P.k, P.nu = _f32(p["h"]), _f32(p["rho0"]), _f32(p["k"]), _f32(p["nu"])
     for a in range(3):
-        P.g[a] = p["g"][a]
+        P.g[a] = _f32(p["g"][a])
         P.lo[a] = p["lo"][a]
         P.hi[a] = p["hi"][a]
-    P.dt, P.visc_eps, P.spring_zeta = p["dt"], p["visc_eps"], p["spring_zeta"]
+    P.dt, P.visc_eps, P.spring_zeta = _f32(p["dt"]), _f32(p["visc_eps"]), _f32(p["spring_zeta"])
     P.cell = p["cell"]
     P.flags = int(p["flags"]) & CLAMP_PRESSURE
     return P
@@ -206,9 +211,15 @@ class System:
         self.mode = mode
         rho0 = np.float32(p["rho0"])
         nf = scene.n_fluid
+
+        def pmass(spacing):
+            # SPH mass rho0 * s^3 as the FP32 value the method stores (each product rounded)
+            s32 = np.float32(spacing)
+            return np.float32(rho0 * np.float32(np.float32(s32 * s32) * s32))
+
         xs = [np.asarray(scene.fluid_x, np.float32)]
         vs = [np.asarray(scene.fluid_v, np.float32)]
-        ms = [np.full(nf, rho0 * np.float32(scene.fluid_spacing) ** 3, np.float32)]
+        ms = [np.full(nf, pmass(scene.fluid_spacing), np.float32)]
         self.bodies = []
         first = nf
         self._keep = []
@@ -232,7 +243,7 @@ class System:
             local = np.ascontiguousarray(b.xyz, np.float32)
             self._keep.append(local)
             bc.local = local.ctypes.data_as(_P(ctypes.c_float))
-            pm = rho0 * np.float32(b.spacing) ** 3
+            pm = pmass(b.spacing)
             if b.kind == KIND_SOFT:
                 pairs = np.ascontiguousarray(b.springs, np.int32)
                 L0, ks, cd = soft_setup(pairs, b.xyz, b.young, b.spacing, float(pm),
@@ -287,14 +298,15 @@ class System:
                    cell_start=np.zeros(self.ncell + 1, np.uint32), rho=np.zeros(n),
                    pres=np.zeros(n), nnbr=np.zeros(n, np.int32), acc=np.zeros(n * 3),
                    x_new=np.zeros(n * 3), v_new=np.zeros(n * 3), wrench=np.zeros(max(1, nb) * 6),
-                   body_new=np.zeros(max(1, nb) * 13), diag=np.zeros(8))
+                   body_new=np.zeros(max(1, nb) * 13), diag=np.zeros(8), cond=np.zeros(2 * n))
         out["clamped"] = lib().orc_substep(
             ctypes.byref(self.P), n, self.nf, self.x, self.v, self.m, self.id, nb,
             self.body_arr, mode, out["key"], out["src"], out["cell_start"], out["rho"],
             out["pres"], out["nnbr"], out["acc"], out["x_new"], out["v_new"], out["wrench"],
-            out["body_new"], out["diag"])
+            out["body_new"], out["diag"], out["cond"])
         for k in ("acc", "x_new", "v_new"):
             out[k] = out[k].reshape(n, 3)
+        out["cond"] = out["cond"].reshape(n, 2)
         out["wrench"] = out["wrench"].reshape(-1, 6)[:nb]
         out["body_new"] = out["body_new"].reshape(-1, 13)[:nb]
         src = out["src"]

@@ -168,7 +168,7 @@ float orc_support2(const orc_params *P)
 void orc_nnbr_brute(const orc_params *P, int n, const float *x, int *nnbr)
 {
     float R2 = orc_support2(P);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n > 4096)
     for (int i = 0; i < n; ++i) {
         int c = 0;
         for (int j = 0; j < n; ++j)
@@ -284,6 +284,7 @@ typedef struct {
     const int *kind_of;         /* sorted slot -> kind (0 fluid) */
     double h;
     double acc[3], rho_sum;
+    double gabs, fabs_sum;      /* sum_j m_j |grad W_ij|, sum_j |F_ij| / m_i */
     int count;
 } orc_pair_ctx;
 
@@ -319,6 +320,8 @@ static void visit_force(int p, int q, void *vctx)
     double fv = 2.0 * (3 + 2) * P->nu * c->m[q] * (2.0 / (rp + rq)) * vx
                 / (r2 + P->visc_eps * c->h * c->h);
     for (int a = 0; a < 3; ++a) c->acc[a] += (fp + fv) * gw * x[a];
+    c->gabs += c->m[q] * fabs(gw) * r;
+    c->fabs_sum += fabs(fp + fv) * fabs(gw) * r;
     c->count++;
 }
 
@@ -342,7 +345,7 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
                 const float *m, const int *id, int nb, const orc_body *B, int mode,
                 uint32_t *key_out, int *src_out, uint32_t *cell_start_out, double *rho,
                 double *pres, int *nnbr, double *acc, double *x_new, double *v_new,
-                double *wrench, double *body_new, double *diag)
+                double *wrench, double *body_new, double *diag, double *cond)
 {
     const double h = P->h;
     float *xf = (float *)malloc(sizeof(float) * 3 * (size_t)n);
@@ -418,7 +421,7 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
     orc_nbrs N = { mode, n, { dims[0], dims[1], dims[2] }, xs, ks, cs, orc_support2(P) };
 
     /* a6: density (Eq. density, self term included) and pressure (Eq. pressure). */
-#pragma omp parallel for schedule(dynamic, 256)
+#pragma omp parallel for schedule(dynamic, 256) if (n > 4096)
     for (int p = 0; p < n; ++p) {
         orc_pair_ctx c;
         memset(&c, 0, sizeof c);
@@ -457,13 +460,14 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
 
     /* a7: pair forces, acceleration and semi-implicit Euler (Alg. 1, Eq. euler). */
     double dt = P->dt;
-#pragma omp parallel for schedule(dynamic, 256)
+#pragma omp parallel for schedule(dynamic, 256) if (n > 4096)
     for (int p = 0; p < n; ++p) {
         orc_pair_ctx c;
         memset(&c, 0, sizeof c);
         c.P = P; c.xd = xd; c.vd = vd; c.m = ms; c.rho = rho; c.pres = pres;
         c.body_of = body_of; c.kind_of = kind_of; c.h = h;
         orc_for_neighbours(&N, p, visit_force, &c);
+        if (cond) { cond[2 * p] = c.gabs; cond[2 * p + 1] = c.fabs_sum; }
         int kp = kind_of[p];
         for (int a = 0; a < 3; ++a) {
             double ap = c.acc[a] + fs[3 * p + a] / ms[p];

@@ -114,7 +114,9 @@ struct sph_handle {
     int n_springs = 0;
     int grab = -1;
     bool finalized = false;
-    cudaGraphExec_t exec1 = nullptr, exec16 = nullptr;
+    cudaGraphExec_t exec1 = nullptr, exec16 = nullptr, exec_prof = nullptr;
+    bool profiling = false;
+    cudaEvent_t ev[kSubstepKernels + 1] = {};
     int64_t substeps = 0;
     std::string err;
 };
@@ -199,12 +201,15 @@ sph_status finalize(sph_handle *h)
     }
     // reduction table: rigid bodies (and static ones when recording)
     std::vector<int4> wb;
+    for (int b = 0; b < kMaxBodies; ++b) { c.wfirst[b] = 0; c.wcount[b] = 0; }
     for (int b = 0; b < c.nb; ++b) {
         const DevBody &B = h->bodies[b];
         bool want = B.kind == SPH_BODY_RIGID || (B.kind == SPH_BODY_STATIC && (h->p.flags & SPH_FLAG_RECORD));
+        c.wfirst[b] = (int)wb.size();
         if (!want) continue;
         for (int l0 = 0; l0 < B.n; l0 += kReduceChunk)
             wb.push_back(make_int4(b, l0, std::min(B.n, l0 + kReduceChunk), 0));
+        c.wcount[b] = (int)wb.size() - c.wfirst[b];
     }
     if ((int)wb.size() > h->L.max_wblocks) return fail(h, SPH_ERR_CAPACITY, "too many reduction blocks");
     c.n_wblocks = (int)wb.size();
@@ -233,12 +238,13 @@ sph_status finalize(sph_handle *h)
     return SPH_OK;
 }
 
-sph_status capture(sph_handle *h, int count, cudaGraphExec_t *out)
+sph_status capture(sph_handle *h, int count, cudaGraphExec_t *out, bool prof = false)
 {
     cudaGraph_t g = nullptr;
     SPH_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
-    for (int i = 0; i < count && le == cudaSuccess; ++i) le = launch_substep(h->c, h->stream);
+    for (int i = 0; i < count && le == cudaSuccess; ++i)
+        le = launch_substep(h->c, h->stream, prof ? h->ev : nullptr, prof);
     cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, le, "capture launch"); }
     if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
@@ -287,7 +293,14 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     c.k = p->k;
     c.nu20 = 20.0f * p->nu;
     c.eps_h2 = p->visc_eps * p->h * p->h;
-    c.alpha_w = (float)(3.0 / (2.0 * M_PI * (double)p->h * p->h * p->h));
+    {
+        const double hd = (double)p->h;
+        const double a6 = 1.0 / (4.0 * M_PI * hd * hd * hd), ih = 1.0 / hd;
+        c.alpha6_hi = (float)a6;
+        c.alpha6_lo = (float)(a6 - (double)c.alpha6_hi);
+        c.invh_hi = (float)ih;
+        c.invh_lo = (float)(ih - (double)c.invh_hi);
+    }
     c.alpha_g = (float)(3.0 / (2.0 * M_PI * (double)p->h * p->h * p->h) / ((double)p->h * p->h));
     for (int a = 0; a < 3; ++a) c.g[a] = p->g[a];
     c.dt = p->dt;
@@ -365,8 +378,23 @@ static sph_status add_particles(sph_handle *h, int kind, int32_t n, const float 
         B.w[a] = vel ? vel[3 + a] : 0.0f;
     }
     for (int a = 0; a < 4; ++a) B.q[a] = ps[3 + a];
-    if (inertia)
-        for (int a = 0; a < 9; ++a) B.inertia[a] = inertia[a];
+    if (inertia) {
+        double I[9], det;
+        for (int a = 0; a < 9; ++a) { B.inertia[a] = inertia[a]; I[a] = inertia[a]; }
+        det = I[0] * (I[4] * I[8] - I[5] * I[7]) - I[1] * (I[3] * I[8] - I[5] * I[6]) +
+              I[2] * (I[3] * I[7] - I[4] * I[6]);
+        if (kind == SPH_BODY_RIGID && !(std::fabs(det) > 0.0))
+            return fail(h, SPH_ERR_ARG, "singular inertia tensor");
+        if (kind == SPH_BODY_RIGID) {
+            const double inv[9] = {I[4] * I[8] - I[5] * I[7], I[2] * I[7] - I[1] * I[8],
+                                   I[1] * I[5] - I[2] * I[4], I[5] * I[6] - I[3] * I[8],
+                                   I[0] * I[8] - I[2] * I[6], I[2] * I[3] - I[0] * I[5],
+                                   I[3] * I[7] - I[4] * I[6], I[1] * I[6] - I[0] * I[7],
+                                   I[0] * I[4] - I[1] * I[3]};
+            for (int a = 0; a < 9; ++a) B.inertia_inv[a] = (float)(inv[a] / det);
+        }
+    }
+    B.inv_mass = mass > 0.0f ? 1.0f / mass : 0.0f;
     const float pm = h->p.rho0 * (spacing * spacing * spacing);
     const float tagged = (kind == SPH_BODY_SOFT) ? pm : -pm;   // negative mass tags boundary
     for (int i = 0; i < n; ++i) {
@@ -499,7 +527,16 @@ sph_status sph_step(sph_handle *h, int32_t n_substeps)
     if (h->c.n == 0 || n_substeps == 0) return SPH_OK;
     const bool graphs = !(h->p.flags & SPH_FLAG_NO_GRAPH) && h->stream != nullptr;
     int left = n_substeps;
-    if (graphs) {
+    if (h->profiling) {
+        if (graphs && !h->exec_prof) {
+            st = capture(h, 1, &h->exec_prof, true);
+            if (st != SPH_OK) return st;
+        }
+        for (; left > 0; --left) {
+            if (graphs) SPH_CUDA(h, cudaGraphLaunch(h->exec_prof, h->stream));
+            else SPH_CUDA(h, launch_substep(h->c, h->stream, h->ev, false));
+        }
+    } else if (graphs) {
         if (!h->exec1) {
             st = capture(h, 1, &h->exec1);
             if (st != SPH_OK) return st;
@@ -676,6 +713,25 @@ sph_status sph_get_info(sph_handle *h, int64_t out[5])
     return SPH_OK;
 }
 
+sph_status sph_set_profiling(sph_handle *h, int32_t on)
+{
+    if (!h) return SPH_ERR_ARG;
+    if (on && !h->ev[0])
+        for (int i = 0; i <= kSubstepKernels; ++i) SPH_CUDA(h, cudaEventCreate(&h->ev[i]));
+    h->profiling = on != 0;
+    return SPH_OK;
+}
+
+sph_status sph_get_kernel_times(sph_handle *h, float out_ms[8])
+{
+    if (!h || !out_ms) return SPH_ERR_ARG;
+    if (!h->ev[0]) return fail(h, SPH_ERR_STATE, "profiling was never enabled");
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < kSubstepKernels; ++i)
+        SPH_CUDA(h, cudaEventElapsedTime(&out_ms[i], h->ev[i], h->ev[i + 1]));
+    return read_status(h);
+}
+
 sph_status sph_sync(sph_handle *h)
 {
     if (!h) return SPH_ERR_ARG;
@@ -693,6 +749,9 @@ void sph_destroy(sph_handle *h)
     if (h->stream || h->finalized) cudaStreamSynchronize(h->stream);
     if (h->exec1) cudaGraphExecDestroy(h->exec1);
     if (h->exec16) cudaGraphExecDestroy(h->exec16);
+    if (h->exec_prof) cudaGraphExecDestroy(h->exec_prof);
+    for (int i = 0; i <= kSubstepKernels; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     delete h;
 }
 

@@ -29,8 +29,9 @@ enum : uint32_t {
 struct DevBody {
     int kind, first, n, grabbed;
     int path_n, path_step0, pad0, pad1;
-    float mass;
+    float mass, inv_mass;
     float inertia[9];
+    float inertia_inv[9];      // body frame, computed once at creation
     float t[3], q[4], v[3], w[3];
     float grab_local[3];
 };
@@ -43,11 +44,11 @@ struct SimConst {
     float R2, h, inv_h;
     float rho0, k, nu20;       // nu20 = 2 (d + 2) nu * 2 with d = 3 (the 2 from rho_bar)
     float eps_h2;
-    float alpha_w;             // 3 / (2 pi h^3)
-    float alpha_g;             // alpha_w / h^2
+    float alpha6_hi, alpha6_lo; // alpha / 6 = 1 / (4 pi h^3) as an unevaluated float pair
+    float invh_hi, invh_lo;     // 1 / h as an unevaluated float pair
+    float alpha_g;             // alpha / h^2, alpha = 3 / (2 pi h^3)
     float g[3], dt;
     uint32_t flags;
-    int grab;                  // grabbed body index or -1 (host view at launch)
     int max_path;
     int n_scan_tiles;
     int n_force_blocks;
@@ -55,6 +56,8 @@ struct SimConst {
     int smooth_window;
     int body_end[kMaxBodies];  // exclusive id end of each body (ids ascending)
     int body_kind[kMaxBodies];
+    int wfirst[kMaxBodies];    // first reduction block of each body
+    int wcount[kMaxBodies];    // its number of reduction blocks
 
     float4 *xA, *vA, *xB, *vB;
     float2 *prho;              // (rho, p / rho^2) in sorted order
@@ -80,15 +83,15 @@ struct SimConst {
 };
 
 // Launchers (sph_kernels.cu).  All enqueue on `s` and return the launch error.
-cudaError_t launch_substep(const SimConst &c, cudaStream_t s);
+constexpr int kSubstepKernels = 8;
+// ev (nullable): kSubstepKernels + 1 events recorded around the kernels; external = record
+// them as graph nodes when the stream is being captured.
+cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev = nullptr,
+                           bool external = false);
 cudaError_t launch_cycle_end(const SimConst &c, cudaStream_t s);
 cudaError_t launch_set_grab(const SimConst &c, cudaStream_t s, int body, int grab,
                             const float *pose_vel13, const float *grab_local, int set_pose,
                             int path_n);
-cudaError_t launch_gather_by_id(const SimConst &c, cudaStream_t s, float4 *x_out, float4 *v_out,
-                                float *rho_out, int *nnbr_out, float4 *acc_out);
-cudaError_t launch_scatter_state(const SimConst &c, cudaStream_t s, const float4 *x_in,
-                                 const float4 *v_in);
 cudaError_t launch_sorted_keys(const SimConst &c, cudaStream_t s, uint32_t *keys, int *ids);
 
 }  // namespace sphgb

@@ -296,12 +296,18 @@ __global__ void __launch_bounds__(256) k_rank_gather(SimConst c)
 
 // ------------------------------------------------------------------- density pass
 
+// Density to a few 1e-8: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000 into a
+// pressure change that moves free-surface accelerations by ~1e-4 m/s^2, so every term is
+// unbiased (q = r/h from the float pair 1/h with one rounding -- r * fl(1/h) alone biases
+// q low), the shape is evaluated as (2-q)^3 - 4(1-q)^3 (no cancellation near q = 1), the
+// sum is compensated (Kahan), and rho - rho0 is formed with an FMA against alpha/6 kept
+// as a float pair.
 __global__ void __launch_bounds__(256) k_density(SimConst c)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= c.n) return;
     const float4 xi = c.xA[p];
-    float sum = 0.0f;
+    float S = 0.0f, C = 0.0f;
     int cnt = 0;
     uint32_t bad = 0;
     for_each_candidate(c, xi, bad, [&](int q) {
@@ -309,16 +315,30 @@ __global__ void __launch_bounds__(256) k_density(SimConst c)
         float dx, dy, dz;
         float r2 = dist2(xi, xj, dx, dy, dz);
         if (r2 < c.R2) {
-            float r = r2 > 0.0f ? r2 * rsqrtf(r2) : 0.0f;
-            float s = r * c.inv_h;
-            float t = 2.0f - s;
-            float w = s < 1.0f ? (0.6666666667f - s * s + 0.5f * s * s * s) : (t * t * t * 0.16666667f);
-            sum += fabsf(xj.w) * w;
+            float r = 0.0f;
+            if (r2 > 0.0f) {                  // sqrt: rsqrt + one Newton step (~1 ulp)
+                float rs = rsqrtf(r2);
+                r = r2 * rs;
+                r = __fmaf_rn(0.5f * rs, __fmaf_rn(-r, r, r2), r);
+            }
+            // q = r / h with a single rounding of r * (1/h)_hi + r * (1/h)_lo
+            float s = __fmaf_rn(r, c.invh_hi, r * c.invh_lo);
+            // 6 w(q) = (2-q)^3 - 4 (1-q)^3 for q < 1, (2-q)^3 for 1 <= q < 2
+            float t = 2.0f - s, u1 = 1.0f - s;
+            float w6 = t * t * t;
+            if (s < 1.0f) w6 = __fmaf_rn(-4.0f * u1, u1 * u1, w6);
+            float y = __fsub_rn(fabsf(xj.w) * w6, C);
+            float u = __fadd_rn(S, y);
+            C = __fsub_rn(__fsub_rn(u, S), y);
+            S = u;
             ++cnt;
         }
     });
-    float rho = c.alpha_w * sum;
-    float pr = c.k * (rho - c.rho0);
+    // rho - rho0 = alpha6 * (S - C) - rho0 with alpha6 = hi + lo
+    float drho = __fmaf_rn(c.alpha6_hi, S, -c.rho0) +
+                 __fmaf_rn(c.alpha6_lo, S, -c.alpha6_hi * C);
+    float rho = c.rho0 + drho;
+    float pr = c.k * drho;
     if ((c.flags & FLAG_CLAMP) && pr < 0.0f) pr = 0.0f;
     c.prho[p] = make_float2(rho, pr / (rho * rho));
     if (c.flags & FLAG_RECORD) c.nnbr[p] = cnt - 1;
@@ -330,6 +350,9 @@ __global__ void __launch_bounds__(256) k_density(SimConst c)
 __global__ void __launch_bounds__(256) k_force(SimConst c)
 {
     __shared__ double sd[8][8];
+    __shared__ unsigned s_done;
+    if (threadIdx.x == 0) s_done = 0u;
+    __syncthreads();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     float dg[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // pair force xyz, |f|, m v xyz, m|v|
     uint32_t bad = 0;
@@ -360,8 +383,13 @@ __global__ void __launch_bounds__(256) k_force(SimConst c)
                     int jd = __float_as_int(vj.w);
                     if ((unsigned)(jd - excl_lo) >= (unsigned)excl_n) {
                         float2 pj = __ldg(c.prho + q);
-                        float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;   // coincident: no force
-                        float s = r2 * rinv * c.inv_h;
+                        float rinv = 0.0f;                 // coincident particles: no force
+                        if (r2 > 0.0f) {
+                            rinv = rsqrtf(r2);
+                            rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);
+                        }
+                        float s = r2 * rinv;
+                        s = __fmaf_rn(s, c.invh_hi, s * c.invh_lo);
                         float t = 2.0f - s;
                         // w'(q)/q of the cubic spline (finite at q -> 0)
                         float gq = s < 1.0f ? (-2.0f + 1.5f * s) : (-0.5f * t * t * c.h * rinv);
@@ -421,18 +449,26 @@ __global__ void __launch_bounds__(256) k_force(SimConst c)
         }
     }
     report(c, bad);
-    // FP32 within the warp, FP64 above it
+    // FP32 within the warp, FP64 above it; the last warp of the block to finish sums the
+    // per-warp partials in a fixed order (no block barrier, so no warp waits for another)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
         float s = warp_sum(dg[a]);
         if (lane == 0) sd[wid][a] = (double)s;
     }
-    __syncthreads();
-    if (threadIdx.x < 8) {
+    unsigned last = 0;
+    if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last && lane < 8) {
+        __threadfence_block();
+        volatile double *v = &sd[0][0];
         double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sd[w][threadIdx.x];
-        c.diag_part[(size_t)blockIdx.x * 8 + threadIdx.x] = t;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
+        c.diag_part[(size_t)blockIdx.x * 8 + lane] = t;
     }
 }
 
@@ -467,30 +503,28 @@ __device__ void rigid_update(const SimConst &c, DevBody &B, const Pose &P, const
 {
     double R[9], xg[3];
     grab_point(P, B, xg, R);
-    const double dt = c.dt, M = B.mass;
+    const double dt = c.dt;
     double vn[3], arm[3], tc[3], w[3], F[3] = {W[0], W[1], W[2]};
     for (int a = 0; a < 3; ++a) {
-        vn[a] = (double)P.v[a] + (W[a] / M + (double)c.g[a]) * dt;
+        vn[a] = (double)P.v[a] + (W[a] * (double)B.inv_mass + (double)c.g[a]) * dt;
         arm[a] = xg[a] - (double)P.t[a];
         w[a] = P.w[a];
     }
     cross3d(arm, F, tc);
     for (int a = 0; a < 3; ++a) tc[a] += W[3 + a];
-    double Iw[9];
+    // I_w = R I_b R^T and I_w^-1 = R I_b^-1 R^T (the body-frame inverse is precomputed)
+    double Iw[9], inv[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
+            double s = 0.0, si = 0.0;
             for (int k = 0; k < 3; ++k)
-                for (int l = 0; l < 3; ++l) s += R[3 * i + k] * (double)B.inertia[3 * k + l] * R[3 * j + l];
+                for (int l = 0; l < 3; ++l) {
+                    s += R[3 * i + k] * (double)B.inertia[3 * k + l] * R[3 * j + l];
+                    si += R[3 * i + k] * (double)B.inertia_inv[3 * k + l] * R[3 * j + l];
+                }
             Iw[3 * i + j] = s;
+            inv[3 * i + j] = si;
         }
-    double det = Iw[0] * (Iw[4] * Iw[8] - Iw[5] * Iw[7]) - Iw[1] * (Iw[3] * Iw[8] - Iw[5] * Iw[6]) +
-                 Iw[2] * (Iw[3] * Iw[7] - Iw[4] * Iw[6]);
-    double inv[9] = {(Iw[4] * Iw[8] - Iw[5] * Iw[7]) / det, (Iw[2] * Iw[7] - Iw[1] * Iw[8]) / det,
-                     (Iw[1] * Iw[5] - Iw[2] * Iw[4]) / det, (Iw[5] * Iw[6] - Iw[3] * Iw[8]) / det,
-                     (Iw[0] * Iw[8] - Iw[2] * Iw[6]) / det, (Iw[2] * Iw[3] - Iw[0] * Iw[5]) / det,
-                     (Iw[3] * Iw[7] - Iw[4] * Iw[6]) / det, (Iw[1] * Iw[6] - Iw[0] * Iw[7]) / det,
-                     (Iw[0] * Iw[4] - Iw[1] * Iw[3]) / det};
     double L[3], gyro[3], wn[3];
     for (int i = 0; i < 3; ++i) L[i] = Iw[3 * i] * w[0] + Iw[3 * i + 1] * w[1] + Iw[3 * i + 2] * w[2];
     cross3d(w, L, gyro);
@@ -505,18 +539,21 @@ __device__ void rigid_update(const SimConst &c, DevBody &B, const Pose &P, const
     qn[0] = (double)P.q[0] + 0.5 * dt * dq0;
     for (int a = 0; a < 3; ++a) qn[1 + a] = qv[a] + 0.5 * dt * ((double)P.q[0] * wn[a] + wq[a]);
     for (int a = 0; a < 4; ++a) nq += qn[a] * qn[a];
-    nq = sqrt(nq);
+    nq = rsqrt(nq);
     for (int a = 0; a < 3; ++a) {
         B.v[a] = (float)vn[a];
         B.t[a] = (float)((double)P.t[a] + vn[a] * dt);
         B.w[a] = (float)wn[a];
     }
-    for (int a = 0; a < 4; ++a) B.q[a] = (float)(qn[a] / nq);
+    for (int a = 0; a < 4; ++a) B.q[a] = (float)(qn[a] * nq);
 }
 
-__global__ void __launch_bounds__(256) k_wrench(SimConst c)
+constexpr int kWrenchThreads = 1024;
+
+__global__ void __launch_bounds__(kWrenchThreads) k_wrench(SimConst c)
 {
-    __shared__ double sw[8][6];
+    __shared__ double sw[kWrenchThreads / 32][6];
+    __shared__ double sdiag[kWrenchThreads];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t step = c.ctr[0];
@@ -553,22 +590,42 @@ __global__ void __launch_bounds__(256) k_wrench(SimConst c)
         if (!s_last) return;
         __threadfence();
     }
-    // ---- last block: per-body sums in a fixed order, diagnostics, rigid update
-    if (threadIdx.x < 8) {
+    // ---- last block: diagnostics (fixed partition + fixed tree: deterministic)
+    {
+        const int a = threadIdx.x & 7;
         double t = 0.0;
-        for (int b = 0; b < c.n_force_blocks; ++b) t += __ldcg(c.diag_part + (size_t)b * 8 + threadIdx.x);
-        c.diag[threadIdx.x] = t;
-    }
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < c.nb; ++b)
-            for (int a = 0; a < 6; ++a) c.wrench[6 * b + a] = 0.0;
-        for (int k = 0; k < c.n_wblocks; ++k) {
-            int b = c.wblock[k].x;
-            for (int a = 0; a < 6; ++a) c.wrench[6 * b + a] += __ldcg(c.wrench_part + (size_t)k * 6 + a);
+        const int stride = blockDim.x >> 3;
+        int b = threadIdx.x >> 3;
+        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        for (; b + 3 * stride < c.n_force_blocks; b += 4 * stride) {
+            t += __ldcg(c.diag_part + (size_t)b * 8 + a);
+            t1 += __ldcg(c.diag_part + (size_t)(b + stride) * 8 + a);
+            t2 += __ldcg(c.diag_part + (size_t)(b + 2 * stride) * 8 + a);
+            t3 += __ldcg(c.diag_part + (size_t)(b + 3 * stride) * 8 + a);
         }
-        for (int b = 0; b < c.nb; ++b) {
-            DevBody &B = c.body[b];
-            if (B.kind != KIND_RIGID) continue;
+        for (; b < c.n_force_blocks; b += stride) t += __ldcg(c.diag_part + (size_t)b * 8 + a);
+        t = (t + t1) + (t2 + t3);
+        sdiag[threadIdx.x] = t;
+        __syncthreads();
+        for (int stride = blockDim.x >> 1; stride >= 8; stride >>= 1) {
+            if ((int)threadIdx.x < stride) sdiag[threadIdx.x] += sdiag[threadIdx.x + stride];
+            __syncthreads();
+        }
+        if (threadIdx.x < 8) c.diag[threadIdx.x] = sdiag[threadIdx.x];
+    }
+    // ---- per-body sums (one thread per body component, fixed block order)
+    if ((int)threadIdx.x < 6 * c.nb) {
+        const int b = threadIdx.x / 6, a = threadIdx.x % 6;
+        double t = 0.0;
+        for (int k = 0; k < c.wcount[b]; ++k) t += __ldcg(c.wrench_part + (size_t)(c.wfirst[b] + k) * 6 + a);
+        c.wrench[6 * b + a] = t;
+    }
+    __syncthreads();
+    // ---- rigid bodies (one thread per body): grabbed bodies log, free bodies integrate
+    if ((int)threadIdx.x < c.nb) {
+        const int b = threadIdx.x;
+        DevBody &B = c.body[b];
+        if (B.kind == KIND_RIGID) {
             Pose P = body_pose(c, B, step);
             if (B.grabbed) {
                 for (int a = 0; a < 3; ++a) { B.t[a] = P.t[a]; B.v[a] = P.v[a]; B.w[a] = P.w[a]; }
@@ -580,6 +637,8 @@ __global__ void __launch_bounds__(256) k_wrench(SimConst c)
                 rigid_update(c, B, P, c.wrench + 6 * b);
             }
         }
+    }
+    if (threadIdx.x == 0) {
         c.ctr[1] = 0u;
         c.ctr[0] = step + 1u;
         __threadfence();
@@ -642,17 +701,31 @@ __global__ void k_sorted_keys(SimConst c, uint32_t *keys, int *ids)
 
 static inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
-cudaError_t launch_substep(const SimConst &c, cudaStream_t s)
+cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, bool external)
 {
     const int nb = blocks_for(c.n, 256);
+    int k = 0;
+    auto mark = [&]() {
+        if (ev) cudaEventRecordWithFlags(ev[k], s, external ? cudaEventRecordExternal : 0);
+        ++k;
+    };
+    mark();
     k_hash<<<nb, 256, 0, s>>>(c);
+    mark();
     k_scan_tiles<<<c.n_scan_tiles, 256, 0, s>>>(c);
+    mark();
     k_scan_apply<<<c.n_scan_tiles, 256, 0, s>>>(c);
+    mark();
     k_scatter<<<nb, 256, 0, s>>>(c);
+    mark();
     k_rank_gather<<<nb, 256, 0, s>>>(c);
+    mark();
     k_density<<<nb, 256, 0, s>>>(c);
+    mark();
     k_force<<<c.n_force_blocks, 256, 0, s>>>(c);
-    k_wrench<<<c.n_wblocks > 0 ? c.n_wblocks : 1, 256, 0, s>>>(c);
+    mark();
+    k_wrench<<<c.n_wblocks > 0 ? c.n_wblocks : 1, kWrenchThreads, 0, s>>>(c);
+    mark();
     return cudaGetLastError();
 }
 

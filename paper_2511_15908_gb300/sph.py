@@ -27,7 +27,9 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_set_grab_pose", "sph_set_grab_path", "sph_step", "sph_get_grab_wrench",
            "sph_get_body_wrench", "sph_get_wrench_log", "sph_get_body", "sph_get_state",
            "sph_set_state", "sph_get_sort", "sph_get_diag", "sph_get_info", "sph_sync",
-           "sph_last_error", "sph_destroy"]
+           "sph_last_error", "sph_destroy", "sph_set_profiling", "sph_get_kernel_times"]
+KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
+           "wrench"]
 
 
 class SphError(RuntimeError):
@@ -103,6 +105,10 @@ def load(path: str = LIB_PATH):
     L.sph_get_diag.argtypes = [_vp, _f64p]
     L.sph_get_info.restype = st
     L.sph_get_info.argtypes = [_vp, _i64p]
+    L.sph_set_profiling.restype = st
+    L.sph_set_profiling.argtypes = [_vp, ctypes.c_int32]
+    L.sph_get_kernel_times.restype = st
+    L.sph_get_kernel_times.argtypes = [_vp, _f32p]
     L.sph_sync.restype = st
     L.sph_sync.argtypes = [_vp]
     L.sph_last_error.restype = ctypes.c_char_p
@@ -280,6 +286,14 @@ class Simulation:
     def diag(self) -> np.ndarray:
         out = np.zeros(8, np.float64)
         self._check(self.L.sph_get_diag(self.h, _ptr(out, ctypes.c_double)))
+        return out
+
+    def set_profiling(self, on: bool = True):
+        self._check(self.L.sph_set_profiling(self.h, int(on)))
+
+    def kernel_times(self) -> np.ndarray:
+        out = np.zeros(8, np.float32)
+        self._check(self.L.sph_get_kernel_times(self.h, _ptr(out, ctypes.c_float)))
         return out
 
     def close(self):

@@ -20,6 +20,11 @@ from paper_2511_15908_gb300 import scenes
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
+def _g(p):
+    """Gravity as the FP32 values the method computes with."""
+    return np.asarray(p["g"], np.float32).astype(np.float64)
+
+
 def _params(h=0.02, dt=1e-3, lo=(-0.1,) * 3, hi=(0.5,) * 3, **kw):
     p = scenes.make_params(h, dt, lo, hi)
     p.update(kw)
@@ -175,7 +180,7 @@ def _pair_forces(sc, out, sysm):
     for b in sc.bodies:
         kinds[(ids >= first) & (ids < first + b.n)] = b.kind
         first += b.n
-    g = np.asarray(sc.params["g"])
+    g = _g(sc.params)
     f = m[:, None].astype(np.float64) * out["acc"]
     integ = (kinds == 0) | (kinds == scenes.KIND_SOFT)
     f[integ] -= m[integ, None] * g
@@ -196,7 +201,8 @@ def test_pair_forces_cancel_linear_and_angular_momentum():
     x[:] = out["x_new"]  # boundary x unchanged; integrated x moved, so rebuild positions:
     # positions fed to the substep: boundary x_new == x_in; fluid/soft x_in = x_new - v_new dt
     integ = (kinds == 0) | (kinds == scenes.KIND_SOFT)
-    x[integ] = out["x_new"][integ] - out["v_new"][integ] * sc.params["dt"]
+    dt = float(np.float32(sc.params["dt"]))        # the method's FP32 time step
+    x[integ] = out["x_new"][integ] - out["v_new"][integ] * dt
     torque = np.cross(x, f).sum(0)
     scale = np.sum(np.linalg.norm(x, axis=1) * np.linalg.norm(f, axis=1))
     assert np.linalg.norm(torque) <= 1e-9 * scale
@@ -233,7 +239,7 @@ def test_viscosity_vanishes_for_rigid_motion():
     # perfect lattice: density below rho0 everywhere, pressure clamped to 0; with rigid
     # motion (v_ij . x_ij = 0) every pair force vanishes, so acc = g up to the FP32
     # rounding of the input velocities (~1e-8; a non-projected form gives ~1e-1 here)
-    g = np.asarray(sc.params["g"])
+    g = _g(sc.params)
     np.testing.assert_allclose(out["acc"], np.broadcast_to(g, out["acc"].shape), atol=1e-6)
 
 
@@ -262,7 +268,7 @@ def test_free_fall_is_exact_semi_implicit_euler():
     v0 = np.array([[0.1, -0.05, 0.2]], np.float32)
     sc = scenes.Scene("single", p, x0, v0, 0.02, [])
     s = oracle.System(sc, mode=0)
-    dt, g = p["dt"], np.asarray(p["g"])
+    dt, g = float(np.float32(p["dt"])), _g(p)
     for nstep in range(1, 31):
         out = s.substep()
     n = 30
@@ -277,7 +283,7 @@ def test_two_particle_pressure_force_is_repulsive_and_symmetric():
     x = np.array([[0.2, 0.2, 0.2], [0.2 + 0.015, 0.2 + 0.01, 0.2]], np.float32)
     sc = scenes.Scene("pair", p, x, np.zeros_like(x), 0.02, [])
     out = oracle.System(sc, mode=0).substep()
-    g = np.asarray(p["g"])
+    g = _g(p)
     a = out["acc"] - g
     ids = out["id"]
     d = x[1] - x[0]

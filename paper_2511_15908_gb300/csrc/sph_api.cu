@@ -24,7 +24,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t xA, vA, xB, vB, prho, key, rank, perm, cnt, cell_start, tile_sum, slot_of_id, locals,
         spring_row, spring_e, fb, xb, acc_dbg, nnbr, body, path, wrench, wrench_part, wblock,
-        diag_part, diag, wlog, cyc_log, status, ctr, total;
+        diag_part, diag_part2, nmask, novf, diag, wlog, cyc_log, status, ctr, total;
     int dims[3], ncell, n_scan_tiles, max_wblocks, max_force_blocks;
 };
 
@@ -88,6 +88,9 @@ Layout make_layout(const sph_params &p, const sph_capacity &cap)
     L.wrench_part = take(8 * 6 * (size_t)L.max_wblocks);
     L.wblock = take(16 * (size_t)L.max_wblocks);
     L.diag_part = take(8 * 8 * (size_t)L.max_force_blocks);
+    L.diag_part2 = take(8 * 8 * (size_t)std::max(L.max_wblocks, kWrenchMinBlocks));
+    L.nmask = take(4 * (size_t)kRuns * N);
+    L.novf = take(4 * N);
     L.diag = take(8 * 8);
     L.wlog = take(8 * 6 * (size_t)std::max(cap.max_path, 1));
     L.cyc_log = take(8 * 6 * (size_t)W);
@@ -213,6 +216,7 @@ sph_status finalize(sph_handle *h)
     }
     if ((int)wb.size() > h->L.max_wblocks) return fail(h, SPH_ERR_CAPACITY, "too many reduction blocks");
     c.n_wblocks = (int)wb.size();
+    c.n_wgrid = std::max(c.n_wblocks, kWrenchMinBlocks);
     cudaStream_t s = h->stream;
     if (n > 0) {
         SPH_CUDA(h, cudaMemcpyAsync(c.xB, h->hx.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s));
@@ -326,6 +330,9 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     c.wrench_part = at<double>(h, L.wrench_part);
     c.wblock = at<int4>(h, L.wblock);
     c.diag_part = at<double>(h, L.diag_part);
+    c.diag_part2 = at<double>(h, L.diag_part2);
+    c.nmask = at<uint32_t>(h, L.nmask);
+    c.novf = at<uint32_t>(h, L.novf);
     c.diag = at<double>(h, L.diag);
     c.wlog = at<double>(h, L.wlog);
     c.cyc_log = at<double>(h, L.cyc_log);

@@ -16,7 +16,9 @@ constexpr int kMaxCellRun = 1536;   // particles scanned per x-run of 3 cells be
                                     // status word reports SPH_ERR_CAPACITY
 constexpr int kMaxCell = 512;       // particles per cell for the deterministic rank
 constexpr int kScanTile = 2048;     // cells per scan block (256 threads x 8)
-constexpr int kReduceChunk = 1024;  // body particles per wrench-reduction block
+constexpr int kReduceChunk = 256;   // body particles per wrench-reduction block
+constexpr int kWrenchMinBlocks = 128; // the FP64 reduction is spread over at least this many
+constexpr int kRuns = 9;            // x-runs of 3 cells covering the 27-cell neighbourhood
 
 // status word bits (mirrors sph_status codes as bit positions)
 enum : uint32_t {
@@ -53,6 +55,7 @@ struct SimConst {
     int n_scan_tiles;
     int n_force_blocks;
     int n_wblocks;
+    int n_wgrid;               // wrench kernel grid = max(n_wblocks, kWrenchMinBlocks)
     int smooth_window;
     int body_end[kMaxBodies];  // exclusive id end of each body (ids ascending)
     int body_kind[kMaxBodies];
@@ -75,6 +78,9 @@ struct SimConst {
     double *wrench_part;       // n_wblocks x 6
     int4 *wblock;              // (body, l0, l1, 0) per reduction block
     double *diag_part;         // n_force_blocks x 8
+    double *diag_part2;        // wrench grid x 8 (second level)
+    uint32_t *nmask;           // kRuns x n: neighbour bits of each run (density -> force)
+    uint32_t *novf;            // per particle: runs longer than 32 candidates (re-tested)
     double *diag;              // 8
     double *wlog;              // max_path x 6
     double *cyc_log;           // smooth_window x 6

@@ -21,6 +21,10 @@
 
 namespace sphgb {
 
+#ifndef SPH_FORCE_MINB
+#define SPH_FORCE_MINB 4      // resident 256-thread blocks per SM the force pass is built for
+#endif
+
 constexpr int KIND_STATIC = 1, KIND_RIGID = 2, KIND_SOFT = 3;
 constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u;
 
@@ -131,6 +135,32 @@ __device__ __forceinline__ void for_each_candidate(const SimConst &c, float4 x, 
             if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
 #pragma unroll 2
             for (int q = s; q < e; ++q) f(q);
+        }
+    }
+}
+
+// Calls f(r, s, e) for each of the 9 x-runs r = 3 (dz+1) + (dy+1) that lie inside the
+// grid; [s, e) is the run's range of sorted slots (cells x-1 .. x+1 are contiguous).
+template <class F>
+__device__ __forceinline__ void for_each_run(const SimConst &c, float4 x, uint32_t &bad, F &&f)
+{
+    int cx, cy, cz;
+    uint32_t dummy = 0;
+    cell_of(c, x, cx, cy, cz, dummy);
+    const int x0 = cx > 0 ? cx - 1 : 0;
+    const int x1 = cx < c.nx - 1 ? cx + 1 : c.nx - 1;
+#pragma unroll 1
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (z < 0 || z >= c.nz || y < 0 || y >= c.ny) continue;
+            int base = (z * c.ny + y) * c.nx;
+            int s = (int)__ldg(c.cell_start + base + x0);
+            int e = (int)__ldg(c.cell_start + base + x1 + 1);
+            if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
+            f(3 * (dz + 1) + (dy + 1), s, e);
         }
     }
 }
@@ -309,31 +339,39 @@ __global__ void __launch_bounds__(256) k_density(SimConst c)
     const float4 xi = c.xA[p];
     float S = 0.0f, C = 0.0f;
     int cnt = 0;
-    uint32_t bad = 0;
-    for_each_candidate(c, xi, bad, [&](int q) {
-        float4 xj = __ldg(c.xA + q);
-        float dx, dy, dz;
-        float r2 = dist2(xi, xj, dx, dy, dz);
-        if (r2 < c.R2) {
-            float r = 0.0f;
-            if (r2 > 0.0f) {                  // sqrt: rsqrt + one Newton step (~1 ulp)
-                float rs = rsqrtf(r2);
-                r = r2 * rs;
-                r = __fmaf_rn(0.5f * rs, __fmaf_rn(-r, r, r2), r);
+    uint32_t bad = 0, ovf = 0;
+    for_each_run(c, xi, bad, [&](int run, int s0, int e0) {
+        uint32_t m = 0;
+#pragma unroll 2
+        for (int q = s0; q < e0; ++q) {
+            float4 xj = __ldg(c.xA + q);
+            float dx, dy, dz;
+            float r2 = dist2(xi, xj, dx, dy, dz);
+            if (r2 < c.R2) {
+                float r = 0.0f;
+                if (r2 > 0.0f) {              // sqrt: rsqrt + one Newton step (~1 ulp)
+                    float rs = rsqrtf(r2);
+                    r = r2 * rs;
+                    r = __fmaf_rn(0.5f * rs, __fmaf_rn(-r, r, r2), r);
+                }
+                // q = r / h with a single rounding of r * (1/h)_hi + r * (1/h)_lo
+                float s = __fmaf_rn(r, c.invh_hi, r * c.invh_lo);
+                // 6 w(q) = (2-q)^3 - 4 (1-q)^3 for q < 1, (2-q)^3 for 1 <= q < 2
+                float t = 2.0f - s, u1 = 1.0f - s;
+                float w6 = t * t * t;
+                if (s < 1.0f) w6 = __fmaf_rn(-4.0f * u1, u1 * u1, w6);
+                float y = __fsub_rn(fabsf(xj.w) * w6, C);
+                float u = __fadd_rn(S, y);
+                C = __fsub_rn(__fsub_rn(u, S), y);
+                S = u;
+                ++cnt;
+                m |= 1u << ((q - s0) & 31);
             }
-            // q = r / h with a single rounding of r * (1/h)_hi + r * (1/h)_lo
-            float s = __fmaf_rn(r, c.invh_hi, r * c.invh_lo);
-            // 6 w(q) = (2-q)^3 - 4 (1-q)^3 for q < 1, (2-q)^3 for 1 <= q < 2
-            float t = 2.0f - s, u1 = 1.0f - s;
-            float w6 = t * t * t;
-            if (s < 1.0f) w6 = __fmaf_rn(-4.0f * u1, u1 * u1, w6);
-            float y = __fsub_rn(fabsf(xj.w) * w6, C);
-            float u = __fadd_rn(S, y);
-            C = __fsub_rn(__fsub_rn(u, S), y);
-            S = u;
-            ++cnt;
         }
+        if (e0 - s0 > 32) ovf |= 1u << run;
+        c.nmask[(size_t)run * c.n + p] = m;
     });
+    c.novf[p] = ovf;
     // rho - rho0 = alpha6 * (S - C) - rho0 with alpha6 = hi + lo
     float drho = __fmaf_rn(c.alpha6_hi, S, -c.rho0) +
                  __fmaf_rn(c.alpha6_lo, S, -c.alpha6_hi * C);
@@ -347,7 +385,7 @@ __global__ void __launch_bounds__(256) k_density(SimConst c)
 
 // -------------------------------------------------------------- force + integrate
 
-__global__ void __launch_bounds__(256) k_force(SimConst c)
+__global__ void __launch_bounds__(256, SPH_FORCE_MINB) k_force(SimConst c)
 {
     __shared__ double sd[8][8];
     __shared__ unsigned s_done;
@@ -374,32 +412,48 @@ __global__ void __launch_bounds__(256) k_force(SimConst c)
         const bool skip = (kind == KIND_STATIC) && !(c.flags & FLAG_RECORD);
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
         if (!skip) {
-            for_each_candidate(c, xi, bad, [&](int q) {
-                float4 xj = __ldg(c.xA + q);
-                float dx, dy, dz;
-                float r2 = dist2(xi, xj, dx, dy, dz);
-                if (r2 < c.R2 && q != p) {
-                    float4 vj = __ldg(c.vA + q);
-                    int jd = __float_as_int(vj.w);
-                    if ((unsigned)(jd - excl_lo) >= (unsigned)excl_n) {
-                        float2 pj = __ldg(c.prho + q);
-                        float rinv = 0.0f;                 // coincident particles: no force
-                        if (r2 > 0.0f) {
-                            rinv = rsqrtf(r2);
-                            rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);
-                        }
-                        float s = r2 * rinv;
-                        s = __fmaf_rn(s, c.invh_hi, s * c.invh_lo);
-                        float t = 2.0f - s;
-                        // w'(q)/q of the cubic spline (finite at q -> 0)
-                        float gq = s < 1.0f ? (-2.0f + 1.5f * s) : (-0.5f * t * t * c.h * rinv);
-                        // v_ij . x_ij with x_ij = -d
-                        float vx = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
-                        float visc = __fdividef(c.nu20 * vx, (pi.x + pj.x) * (r2 + c.eps_h2));
-                        float coef = fabsf(xj.w) * (visc - (pi.y + pj.y)) * gq;
-                        ax -= coef * dx;
-                        ay -= coef * dy;
-                        az -= coef * dz;
+            auto pair = [&](int q, float4 xj, float dx, float dy, float dz, float r2) {
+                float4 vj = __ldg(c.vA + q);
+                int jd = __float_as_int(vj.w);
+                if ((unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
+                float2 pj = __ldg(c.prho + q);
+                float rinv = 0.0f;                 // coincident particles: no force
+                if (r2 > 0.0f) {
+                    rinv = rsqrtf(r2);
+                    rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);
+                }
+                float s = r2 * rinv;
+                s = __fmaf_rn(s, c.invh_hi, s * c.invh_lo);
+                float t = 2.0f - s;
+                // w'(q)/q of the cubic spline (finite at q -> 0)
+                float gq = s < 1.0f ? (-2.0f + 1.5f * s) : (-0.5f * t * t * c.h * rinv);
+                // v_ij . x_ij with x_ij = -d
+                float vx = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
+                float visc = __fdividef(c.nu20 * vx, (pi.x + pj.x) * (r2 + c.eps_h2));
+                float coef = fabsf(xj.w) * (visc - (pi.y + pj.y)) * gq;
+                ax -= coef * dx;
+                ay -= coef * dy;
+                az -= coef * dz;
+            };
+            const uint32_t ovf = c.novf[p];
+            for_each_run(c, xi, bad, [&](int run, int s0, int e0) {
+                if (ovf & (1u << run)) {           // long run: test every candidate again
+                    for (int q = s0; q < e0; ++q) {
+                        float4 xj = __ldg(c.xA + q);
+                        float dx, dy, dz;
+                        float r2 = dist2(xi, xj, dx, dy, dz);
+                        if (r2 < c.R2 && q != p) pair(q, xj, dx, dy, dz, r2);
+                    }
+                } else {                           // neighbours recorded by the density pass
+                    uint32_t m = __ldg(c.nmask + (size_t)run * c.n + p);
+                    while (m) {
+                        int q = s0 + __ffs(m) - 1;
+                        m &= m - 1u;
+                        if (q == p) continue;
+                        float4 xj = __ldg(c.xA + q);
+                        float dx, dy, dz;
+                        float r2 = dist2(xi, xj, dx, dy, dz);
+                        pair(q, xj, dx, dy, dz, r2);
                     }
                 }
             });
@@ -548,77 +602,100 @@ __device__ void rigid_update(const SimConst &c, DevBody &B, const Pose &P, const
     for (int a = 0; a < 4; ++a) B.q[a] = (float)(qn[a] * nq);
 }
 
-constexpr int kWrenchThreads = 1024;
+constexpr int kWrenchThreads = 256;
 
+// Grid = max(n_wblocks, kWrenchMinBlocks) blocks: block k reduces body chunk k (if any) in
+// FP64 and a slice of the force pass's FP64 diagnostic partials; the last block to finish
+// forms the per-body wrenches and diagnostics in a fixed order and updates rigid bodies.
+// GB300 runs FP64 at a small fraction of FP32, so this work is spread over many SMs.
 __global__ void __launch_bounds__(kWrenchThreads) k_wrench(SimConst c)
 {
     __shared__ double sw[kWrenchThreads / 32][6];
-    __shared__ double sdiag[kWrenchThreads];
+    __shared__ double sdg[kWrenchThreads / 32][8];
+    __shared__ double sxg[3];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = kWrenchThreads / 32;
     const uint32_t step = c.ctr[0];
-    if (blockIdx.x < (unsigned)c.n_wblocks) {
-        int4 wb = c.wblock[blockIdx.x];
-        const DevBody &B = c.body[wb.x];
-        Pose P = body_pose(c, B, step);
-        double R[9], xg[3];
-        grab_point(P, B, xg, R);
-        double acc[6] = {0, 0, 0, 0, 0, 0};
-        for (int l = wb.y + threadIdx.x; l < wb.z; l += blockDim.x) {
-            int i = B.first - c.nf + l;
+    const bool has_body = blockIdx.x < (unsigned)c.n_wblocks;
+    int4 wb = make_int4(0, 0, 0, 0);
+    if (has_body) {
+        wb = c.wblock[blockIdx.x];
+        if (threadIdx.x == 0) {
+            Pose P = body_pose(c, c.body[wb.x], step);
+            double R[9], xg[3];
+            grab_point(P, c.body[wb.x], xg, R);
+            sxg[0] = xg[0]; sxg[1] = xg[1]; sxg[2] = xg[2];
+        }
+    }
+    __syncthreads();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (has_body) {
+        const int l = wb.y + threadIdx.x;
+        if (l < wb.z) {
+            int i = c.body[wb.x].first - c.nf + l;
             float4 f = c.fb[i], x = c.xb[i];
             double fd[3] = {f.x, f.y, f.z};
-            double r[3] = {(double)x.x - xg[0], (double)x.y - xg[1], (double)x.z - xg[2]}, t[3];
+            double r[3] = {(double)x.x - sxg[0], (double)x.y - sxg[1], (double)x.z - sxg[2]}, t[3];
             cross3d(r, fd, t);
-            for (int a = 0; a < 3; ++a) { acc[a] += fd[a]; acc[3 + a] += t[a]; }
+            for (int a = 0; a < 3; ++a) { acc[a] = fd[a]; acc[3 + a] = t[a]; }
         }
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-            double s = warp_sum(acc[a]);
-            if (lane == 0) sw[wid][a] = s;
-        }
-        __syncthreads();
-        if (threadIdx.x < 6) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sw[w][threadIdx.x];
-            c.wrench_part[(size_t)blockIdx.x * 6 + threadIdx.x] = t;
-        }
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last = (atomicAdd(c.ctr + 1, 1u) == (unsigned)c.n_wblocks - 1);
-        __syncthreads();
-        if (!s_last) return;
-        __threadfence();
     }
-    // ---- last block: diagnostics (fixed partition + fixed tree: deterministic)
+    // slice of the diagnostic partials: component threadIdx.x & 7, fixed block partition
+    double dacc = 0.0;
     {
+        const long long F = c.n_force_blocks, G = gridDim.x;
+        const int lo = (int)(F * blockIdx.x / G), hi = (int)(F * (blockIdx.x + 1) / G);
         const int a = threadIdx.x & 7;
-        double t = 0.0;
-        const int stride = blockDim.x >> 3;
-        int b = threadIdx.x >> 3;
-        double t1 = 0.0, t2 = 0.0, t3 = 0.0;
-        for (; b + 3 * stride < c.n_force_blocks; b += 4 * stride) {
-            t += __ldcg(c.diag_part + (size_t)b * 8 + a);
-            t1 += __ldcg(c.diag_part + (size_t)(b + stride) * 8 + a);
-            t2 += __ldcg(c.diag_part + (size_t)(b + 2 * stride) * 8 + a);
-            t3 += __ldcg(c.diag_part + (size_t)(b + 3 * stride) * 8 + a);
-        }
-        for (; b < c.n_force_blocks; b += stride) t += __ldcg(c.diag_part + (size_t)b * 8 + a);
-        t = (t + t1) + (t2 + t3);
-        sdiag[threadIdx.x] = t;
-        __syncthreads();
-        for (int stride = blockDim.x >> 1; stride >= 8; stride >>= 1) {
-            if ((int)threadIdx.x < stride) sdiag[threadIdx.x] += sdiag[threadIdx.x + stride];
-            __syncthreads();
-        }
-        if (threadIdx.x < 8) c.diag[threadIdx.x] = sdiag[threadIdx.x];
+        for (int b = lo + (threadIdx.x >> 3); b < hi; b += kWrenchThreads >> 3)
+            dacc += __ldcg(c.diag_part + (size_t)b * 8 + a);
     }
-    // ---- per-body sums (one thread per body component, fixed block order)
-    if ((int)threadIdx.x < 6 * c.nb) {
-        const int b = threadIdx.x / 6, a = threadIdx.x % 6;
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        double s = warp_sum(acc[a]);
+        if (lane == 0) sw[wid][a] = s;
+    }
+    dacc += __shfl_xor_sync(0xffffffffu, dacc, 8);
+    dacc += __shfl_xor_sync(0xffffffffu, dacc, 16);
+    if (lane < 8) sdg[wid][lane] = dacc;
+    __syncthreads();
+    if (threadIdx.x < 6 && has_body) {
         double t = 0.0;
-        for (int k = 0; k < c.wcount[b]; ++k) t += __ldcg(c.wrench_part + (size_t)(c.wfirst[b] + k) * 6 + a);
-        c.wrench[6 * b + a] = t;
+        for (int w = 0; w < nw; ++w) t += sw[w][threadIdx.x];
+        c.wrench_part[(size_t)blockIdx.x * 6 + threadIdx.x] = t;
+    }
+    if (threadIdx.x >= 32 && threadIdx.x < 40) {
+        const int a = threadIdx.x - 32;
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sdg[w][a];
+        c.diag_part2[(size_t)blockIdx.x * 8 + a] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(c.ctr + 1, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // ---- last block: fixed-order sums
+    // Every column is summed by 32 threads (rows strided by 32) and a fixed shuffle tree,
+    // so the L2 loads overlap instead of forming one dependent chain.
+    {
+        // diagnostics: 8 columns x gridDim.x rows -> warps 0..7, column = warp index
+        for (int col = wid; col < 8; col += nw) {
+            double t = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(c.diag_part2 + (size_t)b * 8 + col);
+            t = warp_sum(t);
+            if (lane == 0) c.diag[col] = t;
+        }
+        // wrenches: 6 columns per body x wcount rows
+        for (int col = wid; col < 6 * c.nb; col += nw) {
+            const int b = col / 6, a = col % 6;
+            double t = 0.0;
+            for (int k = lane; k < c.wcount[b]; k += 32)
+                t += __ldcg(c.wrench_part + (size_t)(c.wfirst[b] + k) * 6 + a);
+            t = warp_sum(t);
+            if (lane == 0) c.wrench[6 * b + a] = t;
+        }
     }
     __syncthreads();
     // ---- rigid bodies (one thread per body): grabbed bodies log, free bodies integrate
@@ -724,7 +801,7 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     mark();
     k_force<<<c.n_force_blocks, 256, 0, s>>>(c);
     mark();
-    k_wrench<<<c.n_wblocks > 0 ? c.n_wblocks : 1, kWrenchThreads, 0, s>>>(c);
+    k_wrench<<<c.n_wgrid, kWrenchThreads, 0, s>>>(c);
     mark();
     return cudaGetLastError();
 }

@@ -246,6 +246,54 @@ sph_status sph_get_info(sph_handle *h, int64_t out[5]);
 sph_status sph_set_profiling(sph_handle *h, int32_t on);
 sph_status sph_get_kernel_times(sph_handle *h, float out_ms[8]);
 
+/*
+ * Batched form: many independent scenes of uneven particle counts advanced by ONE
+ * persistent cooperative launch per substep (captured into a CUDA graph).  Every scene is
+ * a handle set up with the calls above; the batch only adds a small table in its own
+ * caller-owned workspace (sph_batch_workspace_bytes).  A batched substep performs, tile
+ * for tile, the same arithmetic as sph_step on each scene, so results are bit-identical.
+ * Member handles must not be stepped or queried while a batched launch is in flight:
+ * call sph_batch_sync first.  The grid barriers between phases are bounded; a barrier
+ * that gives up latches SPH_ERR_TIMEOUT, reported (and reset) by sph_batch_sync.
+ */
+typedef struct sph_batch sph_batch;
+
+size_t sph_batch_workspace_bytes(int32_t n_scenes);
+
+/* scenes: n_scenes handles (finalized here, their streams synchronised); d_workspace:
+ * device, 256-byte aligned, >= sph_batch_workspace_bytes(n_scenes); cuda_stream: the
+ * stream of the batched launches. */
+sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d_workspace,
+                            size_t bytes, void *cuda_stream, sph_batch **out);
+
+/* Launch geometry: resident blocks per SM (1 .. occupancy limit) and work-queue tiles
+ * taken per fetch (1 .. 64). */
+sph_status sph_batch_configure(sph_batch *b, int32_t blocks_per_sm, int32_t tiles_per_fetch);
+
+/* Autotuner: times substeps_per_trial substeps for every blocks-per-SM and tiles-per-fetch
+ * candidate, keeps the fastest, and returns it in out_choice (nullable).  Advances the
+ * scenes by the trial substeps. */
+sph_status sph_batch_tune(sph_batch *b, int32_t substeps_per_trial, int32_t out_choice[2]);
+
+/* Advance every scene by n_substeps substeps (one update cycle per scene).  Asynchronous. */
+sph_status sph_batch_step(sph_batch *b, int32_t n_substeps);
+
+/* Wait for the batch stream; reports SPH_ERR_TIMEOUT if a barrier gave up. */
+sph_status sph_batch_sync(sph_batch *b);
+
+/* scenes, SMs, blocks per SM, tiles per fetch. */
+sph_status sph_batch_info(sph_batch *b, int32_t out[4]);
+
+/* Test hook for the bounded wait: launches one grid barrier that expects missing_blocks
+ * more arrivals than blocks exist, so every block gives up after spin_limit sleeps of
+ * ~64 ns; the next sph_batch_sync reports SPH_ERR_TIMEOUT and resets the barrier. */
+sph_status sph_batch_test_barrier(sph_batch *b, int32_t missing_blocks, int32_t spin_limit);
+
+const char *sph_batch_last_error(const sph_batch *b);
+
+/* Free the host-side batch and its graphs (the workspace and the scenes stay). */
+void sph_batch_destroy(sph_batch *b);
+
 /* Wait for the stream and report latched device errors. */
 sph_status sph_sync(sph_handle *h);
 

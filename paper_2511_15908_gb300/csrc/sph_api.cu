@@ -260,6 +260,23 @@ sph_status capture(sph_handle *h, int count, cudaGraphExec_t *out, bool prof = f
 
 }  // namespace
 
+namespace sphgb {
+
+// Batch support: finalize a scene, wait for its stream, and hand out its SimConst.
+sph_status scene_for_batch(sph_handle *h, SimConst *out)
+{
+    sph_status st = finalize(h);
+    if (st != SPH_OK) return st;
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+    *out = h->c;
+    return SPH_OK;
+}
+
+// Batch support: the batch advanced this scene by n substeps (one update cycle).
+void scene_advanced(sph_handle *h, int n) { h->substeps += n; }
+
+}  // namespace sphgb
+
 extern "C" {
 
 size_t sph_workspace_bytes(const sph_params *p, const sph_capacity *cap)

@@ -1,0 +1,750 @@
+// sph_device.cuh -- per-tile device functions of one SPH substep (SPHaptics, arXiv 2511.15908).
+//
+// Each *_item function processes one tile (one 256-thread block's worth of work) of one
+// phase for one scene.  The plain path launches one kernel per phase whose blocks are the
+// tiles (sph_kernels.cu); the batched path runs every phase of many scenes in one
+// persistent kernel that takes tiles from a work queue (sph_batch.cu).  Both therefore do
+// exactly the same arithmetic in the same order.
+//
+// Phases (Alg. 2 inner loop and Alg. 1):
+//   hash        "calculate uniform grid cell": rigid boundary particles follow their body
+//               (Sec. 3.2), FP32 cell key, atomic per-cell count
+//   scan_tiles  "cumulative sum of cell particle count", level 1 (tile sums)
+//   scan_apply  level 2: exclusive scan into cell_start, counts reset for the next substep
+//   scatter     "sorted index": every particle claims a slot in its cell
+//   rank_gather stable order inside each cell (ascending previous slot), SoA float4 gather
+//   density     Alg. 1 loop 1: rho_i = sum_j m_j W_ij (Eq. density), p = k(rho - rho0)
+//               (Eq. pressure); 9 contiguous x-runs of 3 cells cover the 27-cell block
+//   force       Alg. 1 loops 2-3: pressure + viscosity pair forces, soft springs (Sec. 3.2),
+//               gravity, semi-implicit Euler (Eq. euler); boundary particles store their
+//               coupling force; FP64 momentum diagnostics
+//   wrench      FP64 reduction of coupling forces into per-body force and torque about
+//               the grab point (Sec. 3.3); the last tile integrates free rigid bodies
+//               (Sec. 3.2) and advances the substep counter
+#pragma once
+#include "sph_internal.cuh"
+
+namespace sphgb {
+
+constexpr int kTile = 256;     // threads per block = particles per tile
+
+
+#ifndef SPH_FORCE_MINB
+#define SPH_FORCE_MINB 4      // resident 256-thread blocks per SM the force pass is built for
+#endif
+
+constexpr int KIND_STATIC = 1, KIND_RIGID = 2, KIND_SOFT = 3;
+constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u;
+
+// ------------------------------------------------------------------ small helpers
+
+__device__ __forceinline__ int body_of(const SimConst &c, int id)
+{
+    int b = 0;
+    while (b < c.nb - 1 && id >= c.body_end[b]) ++b;
+    return b;
+}
+
+struct Pose {
+    float t[3], q[4], v[3], w[3];
+};
+
+// Pose used during substep `step`: a grabbed body with a path follows the path entry.
+__device__ __forceinline__ Pose body_pose(const SimConst &c, const DevBody &B, uint32_t step)
+{
+    Pose P;
+    if (B.grabbed && B.path_n > 0) {
+        int s = (int)(step - (uint32_t)B.path_step0);
+        s = s < 0 ? 0 : (s >= B.path_n ? B.path_n - 1 : s);
+        const float *r = c.path + 13 * s;
+        for (int a = 0; a < 3; ++a) { P.t[a] = r[a]; P.v[a] = r[7 + a]; P.w[a] = r[10 + a]; }
+        for (int a = 0; a < 4; ++a) P.q[a] = r[3 + a];
+    } else {
+        for (int a = 0; a < 3; ++a) { P.t[a] = B.t[a]; P.v[a] = B.v[a]; P.w[a] = B.w[a]; }
+        for (int a = 0; a < 4; ++a) P.q[a] = B.q[a];
+    }
+    return P;
+}
+
+// FP32 rotation matrix of (w,x,y,z), every product and sum rounded separately (no FMA),
+// so boundary positions -- which decide cell keys -- are bit-defined.
+__device__ __forceinline__ void rot_f32(const float q[4], float R[9])
+{
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+    float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+    R[0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+    R[1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+    R[2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+    R[3] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+    R[4] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+    R[5] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+    R[6] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+    R[7] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+    R[8] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+}
+
+__device__ __forceinline__ float body_coord(const float R[9], const float t[3], float4 l, int a)
+{
+    float s = __fmul_rn(R[3 * a], l.x);
+    s = __fadd_rn(s, __fmul_rn(R[3 * a + 1], l.y));
+    s = __fadd_rn(s, __fmul_rn(R[3 * a + 2], l.z));
+    return __fadd_rn(s, t[a]);
+}
+
+// Cell coordinate on one axis: floor((x - o) * inv) in FP32, clamped to [0, n-1].
+__device__ __forceinline__ int cell_axis(float x, float o, float inv, int n, uint32_t &bad)
+{
+    if (!isfinite(x)) { bad |= ST_NONFINITE; return 0; }
+    float f = floorf(__fmul_rn(__fsub_rn(x, o), inv));
+    if (f < 0.0f) { bad |= ST_DOMAIN; return 0; }
+    if (f > (float)(n - 1)) { bad |= ST_DOMAIN; return n - 1; }
+    return (int)f;
+}
+
+__device__ __forceinline__ void cell_of(const SimConst &c, float4 x, int &cx, int &cy, int &cz,
+                                        uint32_t &bad)
+{
+    cx = cell_axis(x.x, c.o[0], c.inv_cell, c.nx, bad);
+    cy = cell_axis(x.y, c.o[1], c.inv_cell, c.ny, bad);
+    cz = cell_axis(x.z, c.o[2], c.inv_cell, c.nz, bad);
+}
+
+// Neighbour predicate: d = x_j - x_i, r2 = fma(dz,dz, fma(dy,dy, dx*dx)) < R2 (FP32).
+__device__ __forceinline__ float dist2(float4 xi, float4 xj, float &dx, float &dy, float &dz)
+{
+    dx = __fsub_rn(xj.x, xi.x);
+    dy = __fsub_rn(xj.y, xi.y);
+    dz = __fsub_rn(xj.z, xi.z);
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Calls f(q) for every particle q of the 27 cells around x (9 contiguous x-runs).
+template <class F>
+__device__ __forceinline__ void for_each_candidate(const SimConst &c, float4 x, uint32_t &bad, F &&f)
+{
+    int cx, cy, cz;
+    uint32_t dummy = 0;
+    cell_of(c, x, cx, cy, cz, dummy);
+    const int x0 = cx > 0 ? cx - 1 : 0;
+    const int x1 = cx < c.nx - 1 ? cx + 1 : c.nx - 1;
+#pragma unroll 1
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (z < 0 || z >= c.nz) continue;
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (y < 0 || y >= c.ny) continue;
+            int base = (z * c.ny + y) * c.nx;
+            int s = (int)__ldg(c.cell_start + base + x0);
+            int e = (int)__ldg(c.cell_start + base + x1 + 1);
+            if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
+#pragma unroll 2
+            for (int q = s; q < e; ++q) f(q);
+        }
+    }
+}
+
+// Calls f(r, s, e) for each of the 9 x-runs r = 3 (dz+1) + (dy+1) that lie inside the
+// grid; [s, e) is the run's range of sorted slots (cells x-1 .. x+1 are contiguous).
+template <class F>
+__device__ __forceinline__ void for_each_run(const SimConst &c, float4 x, uint32_t &bad, F &&f)
+{
+    int cx, cy, cz;
+    uint32_t dummy = 0;
+    cell_of(c, x, cx, cy, cz, dummy);
+    const int x0 = cx > 0 ? cx - 1 : 0;
+    const int x1 = cx < c.nx - 1 ? cx + 1 : c.nx - 1;
+#pragma unroll 1
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (z < 0 || z >= c.nz || y < 0 || y >= c.ny) continue;
+            int base = (z * c.ny + y) * c.nx;
+            int s = (int)__ldg(c.cell_start + base + x0);
+            int e = (int)__ldg(c.cell_start + base + x1 + 1);
+            if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
+            f(3 * (dz + 1) + (dy + 1), s, e);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void report(const SimConst &c, uint32_t bad)
+{
+    if (bad) {
+        atomicOr(c.status, bad);
+        if (bad & ST_NONFINITE) atomicAdd(c.status + 1, 1u);
+        if (bad & ST_DOMAIN) atomicAdd(c.status + 2, 1u);
+    }
+}
+
+// ------------------------------------------------------------------ spatial hash
+
+__device__ __forceinline__ void hash_item(const SimConst &c, int blk)
+{
+    int e = blk * kTile + threadIdx.x;
+    if (e >= c.n) return;
+    float4 x = c.xB[e];
+    if (x.w < 0.0f) {                       // boundary particle (negative mass tag)
+        float4 v = c.vB[e];
+        int id = __float_as_int(v.w);
+        int b = body_of(c, id);
+        if (c.body_kind[b] == KIND_RIGID) {
+            Pose P = body_pose(c, c.body[b], c.ctr[0]);
+            float R[9];
+            rot_f32(P.q, R);
+            float4 l = c.locals[id - c.nf];
+            x.x = body_coord(R, P.t, l, 0);
+            x.y = body_coord(R, P.t, l, 1);
+            x.z = body_coord(R, P.t, l, 2);
+            float r0 = x.x - P.t[0], r1 = x.y - P.t[1], r2 = x.z - P.t[2];
+            v.x = P.v[0] + (P.w[1] * r2 - P.w[2] * r1);
+            v.y = P.v[1] + (P.w[2] * r0 - P.w[0] * r2);
+            v.z = P.v[2] + (P.w[0] * r1 - P.w[1] * r0);
+            c.xB[e] = x;
+            c.vB[e] = v;
+        }
+    }
+    uint32_t bad = 0;
+    int cx, cy, cz;
+    cell_of(c, x, cx, cy, cz, bad);
+    uint32_t k = (uint32_t)((cz * c.ny + cy) * c.nx + cx);
+    c.key[e] = k;
+    c.rank[e] = atomicAdd(c.cnt + k, 1u);
+    report(c, bad);
+}
+
+// --------------------------------------------------------------- two-level scan
+
+__device__ __forceinline__ void scan_tiles_item(const SimConst &c, int blk)
+{
+    __shared__ uint32_t ws[8];
+    int base = blk * kScanTile;
+    uint32_t s = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += 256) {
+        int ci = base + i;
+        if (ci < c.ncell) s += c.cnt[ci];
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        c.tile_sum[blk] = t;
+    }
+}
+
+__device__ __forceinline__ void scan_apply_item(const SimConst &c, int blk)
+{
+    __shared__ uint32_t ws[8];
+    __shared__ uint32_t s_pre;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // prefix of the earlier tiles
+    uint32_t pre = 0;
+    for (int t = threadIdx.x; t < blk; t += 256) pre += c.tile_sum[t];
+    pre = warp_sum(pre);
+    if (lane == 0) ws[wid] = pre;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += ws[w];
+        s_pre = t;
+    }
+    __syncthreads();
+    // 8 consecutive cells per thread
+    const int base = blk * kScanTile + threadIdx.x * 8;
+    uint32_t v[8], tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        v[i] = (base + i < c.ncell) ? c.cnt[base + i] : 0u;
+        tot += v[i];
+    }
+    // inclusive warp scan of the thread totals
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    __syncthreads();
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += ws[w];
+    uint32_t run = s_pre + wpre + inc - tot;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int ci = base + i;
+        if (ci < c.ncell) {
+            c.cell_start[ci] = run;
+            c.cnt[ci] = 0u;                 // ready for the next substep's count
+            run += v[i];
+            if (ci == c.ncell - 1) c.cell_start[c.ncell] = run;
+        }
+    }
+}
+
+// --------------------------------------------------------- scatter + stable gather
+
+__device__ __forceinline__ void scatter_item(const SimConst &c, int blk)
+{
+    int e = blk * kTile + threadIdx.x;
+    if (e >= c.n) return;
+    c.perm[c.cell_start[c.key[e]] + c.rank[e]] = (uint32_t)e;
+}
+
+// Within a cell the atomic claim order is arbitrary; the final slot of particle e is
+// cell_start + #{members with a smaller previous slot}, i.e. a stable counting sort.
+__device__ __forceinline__ void rank_gather_item(const SimConst &c, int blk)
+{
+    int p = blk * kTile + threadIdx.x;
+    if (p >= c.n) return;
+    uint32_t e = c.perm[p];
+    uint32_t k = c.key[e];
+    int cs = (int)c.cell_start[k], ce = (int)c.cell_start[k + 1];
+    int dst;
+    if (ce - cs <= kMaxCell) {
+        int r = 0;
+        for (int q = cs; q < ce; ++q) r += (c.perm[q] < e);
+        dst = cs + r;
+    } else {
+        dst = cs + (int)c.rank[e];          // still a permutation; order not stable
+        atomicOr(c.status, (uint32_t)ST_CAPACITY);
+    }
+    float4 x = c.xB[e];
+    float4 v = c.vB[e];
+    c.xA[dst] = x;
+    c.vA[dst] = v;
+    int id = __float_as_int(v.w);
+    if (id >= c.nf && c.body_kind[body_of(c, id)] == KIND_SOFT) c.slot_of_id[id] = dst;
+}
+
+// ------------------------------------------------------------------- density pass
+
+// Density to a few 1e-8: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000 into a
+// pressure change that moves free-surface accelerations by ~1e-4 m/s^2, so every term is
+// unbiased (q = r/h from the float pair 1/h with one rounding -- r * fl(1/h) alone biases
+// q low), the shape is evaluated as (2-q)^3 - 4(1-q)^3 (no cancellation near q = 1), the
+// sum is compensated (Kahan), and rho - rho0 is formed with an FMA against alpha/6 kept
+// as a float pair.
+__device__ __forceinline__ void density_item(const SimConst &c, int blk)
+{
+    int p = blk * kTile + threadIdx.x;
+    if (p >= c.n) return;
+    const float4 xi = c.xA[p];
+    float S = 0.0f, C = 0.0f;
+    int cnt = 0;
+    uint32_t bad = 0, ovf = 0;
+    for_each_run(c, xi, bad, [&](int run, int s0, int e0) {
+        uint32_t m = 0;
+#pragma unroll 2
+        for (int q = s0; q < e0; ++q) {
+            float4 xj = __ldg(c.xA + q);
+            float dx, dy, dz;
+            float r2 = dist2(xi, xj, dx, dy, dz);
+            if (r2 < c.R2) {
+                float r = 0.0f;
+                if (r2 > 0.0f) {              // sqrt: rsqrt + one Newton step (~1 ulp)
+                    float rs = rsqrtf(r2);
+                    r = r2 * rs;
+                    r = __fmaf_rn(0.5f * rs, __fmaf_rn(-r, r, r2), r);
+                }
+                // q = r / h with a single rounding of r * (1/h)_hi + r * (1/h)_lo
+                float s = __fmaf_rn(r, c.invh_hi, r * c.invh_lo);
+                // 6 w(q) = (2-q)^3 - 4 (1-q)^3 for q < 1, (2-q)^3 for 1 <= q < 2
+                float t = 2.0f - s, u1 = 1.0f - s;
+                float w6 = t * t * t;
+                if (s < 1.0f) w6 = __fmaf_rn(-4.0f * u1, u1 * u1, w6);
+                float y = __fsub_rn(fabsf(xj.w) * w6, C);
+                float u = __fadd_rn(S, y);
+                C = __fsub_rn(__fsub_rn(u, S), y);
+                S = u;
+                ++cnt;
+                m |= 1u << ((q - s0) & 31);
+            }
+        }
+        if (e0 - s0 > 32) ovf |= 1u << run;
+        c.nmask[(size_t)run * c.n + p] = m;
+    });
+    c.novf[p] = ovf;
+    // rho - rho0 = alpha6 * (S - C) - rho0 with alpha6 = hi + lo
+    float drho = __fmaf_rn(c.alpha6_hi, S, -c.rho0) +
+                 __fmaf_rn(c.alpha6_lo, S, -c.alpha6_hi * C);
+    float rho = c.rho0 + drho;
+    float pr = c.k * drho;
+    if ((c.flags & FLAG_CLAMP) && pr < 0.0f) pr = 0.0f;
+    c.prho[p] = make_float2(rho, pr / (rho * rho));
+    if (c.flags & FLAG_RECORD) c.nnbr[p] = cnt - 1;
+    report(c, bad);
+}
+
+// -------------------------------------------------------------- force + integrate
+
+__device__ __forceinline__ void force_item(const SimConst &c, int blk)
+{
+    __shared__ double sd[8][8];
+    __shared__ unsigned s_done;
+    if (threadIdx.x == 0) s_done = 0u;
+    __syncthreads();
+    const int p = blk * kTile + threadIdx.x;
+    float dg[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // pair force xyz, |f|, m v xyz, m|v|
+    uint32_t bad = 0;
+    if (p < c.n) {
+        const float4 xi = c.xA[p];
+        const float4 vi = c.vA[p];
+        const float2 pi = c.prho[p];
+        const int id = __float_as_int(vi.w);
+        const float mi = fabsf(xi.w);
+        int kind = 0, excl_lo = 0, excl_n = 0, b = -1;
+        if (id >= c.nf) {
+            b = body_of(c, id);
+            kind = c.body_kind[b];
+            if (kind != KIND_SOFT) {
+                excl_lo = b == 0 ? c.nf : c.body_end[b - 1];
+                excl_n = c.body_end[b] - excl_lo;
+            }
+        }
+        const bool skip = (kind == KIND_STATIC) && !(c.flags & FLAG_RECORD);
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        if (!skip) {
+            auto pair = [&](int q, float4 xj, float dx, float dy, float dz, float r2) {
+                float4 vj = __ldg(c.vA + q);
+                int jd = __float_as_int(vj.w);
+                if ((unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
+                float2 pj = __ldg(c.prho + q);
+                float rinv = 0.0f;                 // coincident particles: no force
+                if (r2 > 0.0f) {
+                    rinv = rsqrtf(r2);
+                    rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);
+                }
+                float s = r2 * rinv;
+                s = __fmaf_rn(s, c.invh_hi, s * c.invh_lo);
+                float t = 2.0f - s;
+                // w'(q)/q of the cubic spline (finite at q -> 0)
+                float gq = s < 1.0f ? (-2.0f + 1.5f * s) : (-0.5f * t * t * c.h * rinv);
+                // v_ij . x_ij with x_ij = -d
+                float vx = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
+                float visc = __fdividef(c.nu20 * vx, (pi.x + pj.x) * (r2 + c.eps_h2));
+                float coef = fabsf(xj.w) * (visc - (pi.y + pj.y)) * gq;
+                ax -= coef * dx;
+                ay -= coef * dy;
+                az -= coef * dz;
+            };
+            const uint32_t ovf = c.novf[p];
+            for_each_run(c, xi, bad, [&](int run, int s0, int e0) {
+                if (ovf & (1u << run)) {           // long run: test every candidate again
+                    for (int q = s0; q < e0; ++q) {
+                        float4 xj = __ldg(c.xA + q);
+                        float dx, dy, dz;
+                        float r2 = dist2(xi, xj, dx, dy, dz);
+                        if (r2 < c.R2 && q != p) pair(q, xj, dx, dy, dz, r2);
+                    }
+                } else {                           // neighbours recorded by the density pass
+                    uint32_t m = __ldg(c.nmask + (size_t)run * c.n + p);
+                    while (m) {
+                        int q = s0 + __ffs(m) - 1;
+                        m &= m - 1u;
+                        if (q == p) continue;
+                        float4 xj = __ldg(c.xA + q);
+                        float dx, dy, dz;
+                        float r2 = dist2(xi, xj, dx, dy, dz);
+                        pair(q, xj, dx, dy, dz, r2);
+                    }
+                }
+            });
+            ax *= c.alpha_g;
+            ay *= c.alpha_g;
+            az *= c.alpha_g;
+        }
+        float fx = mi * ax, fy = mi * ay, fz = mi * az;   // pair force on i
+        dg[0] = fx; dg[1] = fy; dg[2] = fz;
+        dg[3] = sqrtf(fx * fx + fy * fy + fz * fz);
+        if (kind == 0 || kind == KIND_SOFT) {
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            if (kind == KIND_SOFT) {
+                int l = id - c.nf;
+                for (int e = c.spring_row[l]; e < c.spring_row[l + 1]; ++e) {
+                    float4 sp = c.spring_e[e];
+                    int q = c.slot_of_id[__float_as_int(sp.x)];
+                    float4 xj = c.xA[q], vj = c.vA[q];
+                    float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z;
+                    float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                    float il = 1.0f / L;
+                    d0 *= il; d1 *= il; d2 *= il;
+                    float vr = (vi.x - vj.x) * d0 + (vi.y - vj.y) * d1 + (vi.z - vj.z) * d2;
+                    float f = -sp.z * (L - sp.y) - sp.w * vr;
+                    sx += f * d0; sy += f * d1; sz += f * d2;
+                }
+            }
+            float im = 1.0f / mi;
+            float a0 = ax + sx * im + c.g[0];
+            float a1 = ay + sy * im + c.g[1];
+            float a2 = az + sz * im + c.g[2];
+            float4 vn = make_float4(vi.x + a0 * c.dt, vi.y + a1 * c.dt, vi.z + a2 * c.dt, vi.w);
+            float4 xn = make_float4(xi.x + vn.x * c.dt, xi.y + vn.y * c.dt, xi.z + vn.z * c.dt, xi.w);
+            if (!(isfinite(xn.x) && isfinite(xn.y) && isfinite(xn.z))) bad |= ST_NONFINITE;
+            c.xB[p] = xn;
+            c.vB[p] = vn;
+            dg[4] = mi * vn.x; dg[5] = mi * vn.y; dg[6] = mi * vn.z;
+            dg[7] = mi * sqrtf(vn.x * vn.x + vn.y * vn.y + vn.z * vn.z);
+            if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(a0, a1, a2, 0.0f);
+        } else {
+            c.xB[p] = xi;
+            c.vB[p] = vi;
+            int l = id - c.nf;
+            c.fb[l] = make_float4(fx, fy, fz, 0.0f);
+            c.xb[l] = xi;
+            if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(ax, ay, az, 0.0f);
+        }
+    }
+    report(c, bad);
+    // FP32 within the warp, FP64 above it; the last warp of the block to finish sums the
+    // per-warp partials in a fixed order (no block barrier, so no warp waits for another)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        float s = warp_sum(dg[a]);
+        if (lane == 0) sd[wid][a] = (double)s;
+    }
+    unsigned last = 0;
+    if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last && lane < 8) {
+        __threadfence_block();
+        volatile double *v = &sd[0][0];
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
+        c.diag_part[(size_t)blk * 8 + lane] = t;
+    }
+}
+
+// ------------------------------------------------------- FP64 wrench + rigid update
+
+static __device__ void rot_f64(const double q[4], double R[9])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static __device__ void grab_point(const Pose &P, const DevBody &B, double xg[3], double R[9])
+{
+    double q[4] = {P.q[0], P.q[1], P.q[2], P.q[3]};
+    rot_f64(q, R);
+    for (int a = 0; a < 3; ++a)
+        xg[a] = R[3 * a] * B.grab_local[0] + R[3 * a + 1] * B.grab_local[1] +
+                R[3 * a + 2] * B.grab_local[2] + (double)P.t[a];
+}
+
+static __device__ void cross3d(const double a[3], const double b[3], double o[3])
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Semi-implicit rigid update in FP64 from the FP64 wrench (force, torque about x_g).
+static __device__ void rigid_update(const SimConst &c, DevBody &B, const Pose &P, const double W[6])
+{
+    double R[9], xg[3];
+    grab_point(P, B, xg, R);
+    const double dt = c.dt;
+    double vn[3], arm[3], tc[3], w[3], F[3] = {W[0], W[1], W[2]};
+    for (int a = 0; a < 3; ++a) {
+        vn[a] = (double)P.v[a] + (W[a] * (double)B.inv_mass + (double)c.g[a]) * dt;
+        arm[a] = xg[a] - (double)P.t[a];
+        w[a] = P.w[a];
+    }
+    cross3d(arm, F, tc);
+    for (int a = 0; a < 3; ++a) tc[a] += W[3 + a];
+    // I_w = R I_b R^T and I_w^-1 = R I_b^-1 R^T (the body-frame inverse is precomputed)
+    double Iw[9], inv[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0, si = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    s += R[3 * i + k] * (double)B.inertia[3 * k + l] * R[3 * j + l];
+                    si += R[3 * i + k] * (double)B.inertia_inv[3 * k + l] * R[3 * j + l];
+                }
+            Iw[3 * i + j] = s;
+            inv[3 * i + j] = si;
+        }
+    double L[3], gyro[3], wn[3];
+    for (int i = 0; i < 3; ++i) L[i] = Iw[3 * i] * w[0] + Iw[3 * i + 1] * w[1] + Iw[3 * i + 2] * w[2];
+    cross3d(w, L, gyro);
+    for (int i = 0; i < 3; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < 3; ++j) s += inv[3 * i + j] * (tc[j] - gyro[j]);
+        wn[i] = w[i] + s * dt;
+    }
+    double qv[3] = {P.q[1], P.q[2], P.q[3]}, wq[3], qn[4], nq = 0.0;
+    cross3d(wn, qv, wq);
+    double dq0 = -(wn[0] * qv[0] + wn[1] * qv[1] + wn[2] * qv[2]);
+    qn[0] = (double)P.q[0] + 0.5 * dt * dq0;
+    for (int a = 0; a < 3; ++a) qn[1 + a] = qv[a] + 0.5 * dt * ((double)P.q[0] * wn[a] + wq[a]);
+    for (int a = 0; a < 4; ++a) nq += qn[a] * qn[a];
+    nq = rsqrt(nq);
+    for (int a = 0; a < 3; ++a) {
+        B.v[a] = (float)vn[a];
+        B.t[a] = (float)((double)P.t[a] + vn[a] * dt);
+        B.w[a] = (float)wn[a];
+    }
+    for (int a = 0; a < 4; ++a) B.q[a] = (float)(qn[a] * nq);
+}
+
+constexpr int kWrenchThreads = kTile;
+
+// Grid = max(n_wblocks, kWrenchMinBlocks) blocks: block k reduces body chunk k (if any) in
+// FP64 and a slice of the force pass's FP64 diagnostic partials; the last block to finish
+// forms the per-body wrenches and diagnostics in a fixed order and updates rigid bodies.
+// GB300 runs FP64 at a small fraction of FP32, so this work is spread over many SMs.
+__device__ __forceinline__ void wrench_item(const SimConst &c, int blk)
+{
+    __shared__ double sw[kWrenchThreads / 32][6];
+    __shared__ double sdg[kWrenchThreads / 32][8];
+    __shared__ double sxg[3];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = kWrenchThreads / 32;
+    const uint32_t step = c.ctr[0];
+    const int G = c.n_wgrid;
+    const bool has_body = blk < c.n_wblocks;
+    int4 wb = make_int4(0, 0, 0, 0);
+    if (has_body) {
+        wb = c.wblock[blk];
+        if (threadIdx.x == 0) {
+            Pose P = body_pose(c, c.body[wb.x], step);
+            double R[9], xg[3];
+            grab_point(P, c.body[wb.x], xg, R);
+            sxg[0] = xg[0]; sxg[1] = xg[1]; sxg[2] = xg[2];
+        }
+    }
+    __syncthreads();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    if (has_body) {
+        const int l = wb.y + threadIdx.x;
+        if (l < wb.z) {
+            int i = c.body[wb.x].first - c.nf + l;
+            float4 f = c.fb[i], x = c.xb[i];
+            double fd[3] = {f.x, f.y, f.z};
+            double r[3] = {(double)x.x - sxg[0], (double)x.y - sxg[1], (double)x.z - sxg[2]}, t[3];
+            cross3d(r, fd, t);
+            for (int a = 0; a < 3; ++a) { acc[a] = fd[a]; acc[3 + a] = t[a]; }
+        }
+    }
+    // slice of the diagnostic partials: component threadIdx.x & 7, fixed block partition
+    double dacc = 0.0;
+    {
+        const long long F = c.n_force_blocks;
+        const int lo = (int)(F * blk / G), hi = (int)(F * (blk + 1) / G);
+        const int a = threadIdx.x & 7;
+        for (int b = lo + (threadIdx.x >> 3); b < hi; b += kWrenchThreads >> 3)
+            dacc += __ldcg(c.diag_part + (size_t)b * 8 + a);
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        double s = warp_sum(acc[a]);
+        if (lane == 0) sw[wid][a] = s;
+    }
+    dacc += __shfl_xor_sync(0xffffffffu, dacc, 8);
+    dacc += __shfl_xor_sync(0xffffffffu, dacc, 16);
+    if (lane < 8) sdg[wid][lane] = dacc;
+    __syncthreads();
+    if (threadIdx.x < 6 && has_body) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sw[w][threadIdx.x];
+        c.wrench_part[(size_t)blk * 6 + threadIdx.x] = t;
+    }
+    if (threadIdx.x >= 32 && threadIdx.x < 40) {
+        const int a = threadIdx.x - 32;
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sdg[w][a];
+        c.diag_part2[(size_t)blk * 8 + a] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(c.ctr + 1, 1u) == (unsigned)G - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // ---- last block: fixed-order sums
+    // Every column is summed by 32 threads (rows strided by 32) and a fixed shuffle tree,
+    // so the L2 loads overlap instead of forming one dependent chain.
+    {
+        // diagnostics: 8 columns x G rows -> warps 0..7, column = warp index
+        for (int col = wid; col < 8; col += nw) {
+            double t = 0.0;
+            for (int b = lane; b < G; b += 32) t += __ldcg(c.diag_part2 + (size_t)b * 8 + col);
+            t = warp_sum(t);
+            if (lane == 0) c.diag[col] = t;
+        }
+        // wrenches: 6 columns per body x wcount rows
+        for (int col = wid; col < 6 * c.nb; col += nw) {
+            const int b = col / 6, a = col % 6;
+            double t = 0.0;
+            for (int k = lane; k < c.wcount[b]; k += 32)
+                t += __ldcg(c.wrench_part + (size_t)(c.wfirst[b] + k) * 6 + a);
+            t = warp_sum(t);
+            if (lane == 0) c.wrench[6 * b + a] = t;
+        }
+    }
+    __syncthreads();
+    // ---- rigid bodies (one thread per body): grabbed bodies log, free bodies integrate
+    if ((int)threadIdx.x < c.nb) {
+        const int b = threadIdx.x;
+        DevBody &B = c.body[b];
+        if (B.kind == KIND_RIGID) {
+            Pose P = body_pose(c, B, step);
+            if (B.grabbed) {
+                for (int a = 0; a < 3; ++a) { B.t[a] = P.t[a]; B.v[a] = P.v[a]; B.w[a] = P.w[a]; }
+                for (int a = 0; a < 4; ++a) B.q[a] = P.q[a];
+                if (c.max_path > 0)
+                    for (int a = 0; a < 6; ++a)
+                        c.wlog[(size_t)(step % (uint32_t)c.max_path) * 6 + a] = c.wrench[6 * b + a];
+            } else if (B.mass > 0.0f) {
+                rigid_update(c, B, P, c.wrench + 6 * b);
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        c.ctr[1] = 0u;
+        c.ctr[0] = step + 1u;
+        __threadfence();
+    }
+}
+
+// ---------------------------------------------------------------- per-call kernels
+
+// End of an update cycle: record the grabbed body's wrench for the rolling average.
+__device__ __forceinline__ void cycle_end_item(const SimConst &c)
+{
+    uint32_t cyc = c.ctr[2];
+    int g = -1;
+    for (int b = 0; b < c.nb; ++b)
+        if (c.body[b].grabbed) g = b;
+    if (c.smooth_window > 0) {
+        double *dst = c.cyc_log + (size_t)(cyc % (uint32_t)c.smooth_window) * 6;
+        for (int a = 0; a < 6; ++a) dst[a] = g >= 0 ? c.wrench[6 * g + a] : 0.0;
+    }
+    c.ctr[2] = cyc + 1u;
+}
+
+}  // namespace sphgb

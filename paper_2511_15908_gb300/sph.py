@@ -27,7 +27,10 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_set_grab_pose", "sph_set_grab_path", "sph_step", "sph_get_grab_wrench",
            "sph_get_body_wrench", "sph_get_wrench_log", "sph_get_body", "sph_get_state",
            "sph_set_state", "sph_get_sort", "sph_get_diag", "sph_get_info", "sph_sync",
-           "sph_last_error", "sph_destroy", "sph_set_profiling", "sph_get_kernel_times"]
+           "sph_last_error", "sph_destroy", "sph_set_profiling", "sph_get_kernel_times",
+           "sph_batch_workspace_bytes", "sph_batch_create", "sph_batch_configure", "sph_batch_tune",
+           "sph_batch_step", "sph_batch_sync", "sph_batch_info", "sph_batch_last_error",
+           "sph_batch_destroy", "sph_batch_test_barrier"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -109,6 +112,27 @@ def load(path: str = LIB_PATH):
     L.sph_set_profiling.argtypes = [_vp, ctypes.c_int32]
     L.sph_get_kernel_times.restype = st
     L.sph_get_kernel_times.argtypes = [_vp, _f32p]
+    L.sph_batch_workspace_bytes.restype = ctypes.c_size_t
+    L.sph_batch_workspace_bytes.argtypes = [ctypes.c_int32]
+    L.sph_batch_create.restype = st
+    L.sph_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, _vp, ctypes.c_size_t, _vp,
+                                   ctypes.POINTER(_vp)]
+    L.sph_batch_configure.restype = st
+    L.sph_batch_configure.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
+    L.sph_batch_tune.restype = st
+    L.sph_batch_tune.argtypes = [_vp, ctypes.c_int32, _i32p]
+    L.sph_batch_step.restype = st
+    L.sph_batch_step.argtypes = [_vp, ctypes.c_int32]
+    L.sph_batch_sync.restype = st
+    L.sph_batch_sync.argtypes = [_vp]
+    L.sph_batch_info.restype = st
+    L.sph_batch_info.argtypes = [_vp, _i32p]
+    L.sph_batch_test_barrier.restype = st
+    L.sph_batch_test_barrier.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
+    L.sph_batch_last_error.restype = ctypes.c_char_p
+    L.sph_batch_last_error.argtypes = [_vp]
+    L.sph_batch_destroy.restype = None
+    L.sph_batch_destroy.argtypes = [_vp]
     L.sph_sync.restype = st
     L.sph_sync.argtypes = [_vp]
     L.sph_last_error.restype = ctypes.c_char_p
@@ -300,6 +324,67 @@ class Simulation:
         if getattr(self, "h", None):
             self.L.sph_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many Simulations advanced by one persistent launch per substep (batched form)."""
+
+    def __init__(self, sims, stream=None):
+        import torch
+        self.L = load()
+        self.sims = list(sims)
+        n = len(self.sims)
+        nbytes = self.L.sph_batch_workspace_bytes(n)
+        if nbytes == 0:
+            raise SphError(ERR_ARG, "empty batch")
+        dev = self.sims[0].device
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        handles = (_vp * n)(*[s.h for s in self.sims])
+        b = _vp()
+        st = self.L.sph_batch_create(handles, n, self.workspace.data_ptr(), nbytes,
+                                     self.stream.cuda_stream, ctypes.byref(b))
+        if st != OK:
+            raise SphError(st, "sph_batch_create failed")
+        self.b = b
+
+    def _check(self, st):
+        if st != OK:
+            raise SphError(st, self.L.sph_batch_last_error(self.b).decode())
+
+    def configure(self, blocks_per_sm: int, tiles_per_fetch: int = 1):
+        self._check(self.L.sph_batch_configure(self.b, blocks_per_sm, tiles_per_fetch))
+
+    def tune(self, substeps_per_trial: int = 2):
+        out = np.zeros(2, np.int32)
+        self._check(self.L.sph_batch_tune(self.b, substeps_per_trial, _ptr(out, ctypes.c_int32)))
+        return int(out[0]), int(out[1])
+
+    def step(self, n: int = 1):
+        self._check(self.L.sph_batch_step(self.b, int(n)))
+
+    def sync(self):
+        self._check(self.L.sph_batch_sync(self.b))
+
+    def info(self):
+        out = np.zeros(4, np.int32)
+        self._check(self.L.sph_batch_info(self.b, _ptr(out, ctypes.c_int32)))
+        return dict(scenes=int(out[0]), sms=int(out[1]), blocks_per_sm=int(out[2]),
+                    tiles_per_fetch=int(out[3]))
+
+    def test_barrier(self, missing_blocks: int = 1, spin_limit: int = 4096):
+        self._check(self.L.sph_batch_test_barrier(self.b, missing_blocks, spin_limit))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.L.sph_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -266,13 +266,17 @@ size_t sph_batch_workspace_bytes(int32_t n_scenes);
 sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d_workspace,
                             size_t bytes, void *cuda_stream, sph_batch **out);
 
-/* Launch geometry: resident blocks per SM (1 .. occupancy limit) and work-queue tiles
- * taken per fetch (1 .. 64). */
+/* Launch structure: blocks_per_sm = 1 .. occupancy limit runs the persistent kernel with
+ * that many resident blocks per SM, taking tiles_per_fetch (1 .. 64) tiles per work-queue
+ * fetch; blocks_per_sm = 0 runs one kernel per phase over all scenes' tiles instead (same
+ * tiles, same results; each phase at its own occupancy). */
 sph_status sph_batch_configure(sph_batch *b, int32_t blocks_per_sm, int32_t tiles_per_fetch);
 
-/* Autotuner: times substeps_per_trial substeps for every blocks-per-SM and tiles-per-fetch
- * candidate, keeps the fastest, and returns it in out_choice (nullable).  Advances the
- * scenes by the trial substeps. */
+/* Autotuner: times substeps_per_trial substeps (after one warm-up substep) for every
+ * launch-structure candidate -- per-phase kernels, and the persistent kernel at every
+ * blocks-per-SM x {1, 2, 4} tiles per fetch -- keeps the fastest and returns it in
+ * out_choice (nullable).  Advances the scenes by (3 max_bps + 1)(1 + substeps_per_trial)
+ * substeps. */
 sph_status sph_batch_tune(sph_batch *b, int32_t substeps_per_trial, int32_t out_choice[2]);
 
 /* Advance every scene by n_substeps substeps (one update cycle per scene).  Asynchronous. */

@@ -81,9 +81,18 @@ __device__ __forceinline__ int scene_of(const int *prefix, int n, int item)
     return lo;
 }
 
-__global__ void __launch_bounds__(kTile) k_batch(BatchConst b, int n_substeps, int cycle_end)
+#ifndef SPH_BATCH_MINB
+#define SPH_BATCH_MINB 4      // resident blocks per SM the persistent kernel is built for
+#endif
+
+// The scene's constants are staged in shared memory for each tile: read through a global
+// reference they would be reloaded after every global store (possible aliasing), while
+// shared-memory loads cannot alias the particle arrays.
+__global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, int n_substeps, int cycle_end)
 {
     __shared__ int s_item;
+    __shared__ __align__(16) SimConst s_c;
+    static_assert(sizeof(SimConst) % 16 == 0, "SimConst is copied as int4");
     for (int sub = 0; sub < n_substeps; ++sub) {
         for (int ph = 0; ph < kPhases; ++ph) {
             const int *pre = b.prefix + ph * (b.n_scenes + 1);
@@ -97,7 +106,14 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchConst b, int n_substeps, i
                 for (int it = base; it < end; ++it) {
                     const int s = scene_of(pre, b.n_scenes, it);
                     const int blk = it - pre[s];
-                    const SimConst &c = b.scenes[s];
+                    {
+                        const int4 *src = reinterpret_cast<const int4 *>(b.scenes + s);
+                        int4 *dst = reinterpret_cast<int4 *>(&s_c);
+                        for (int w = threadIdx.x; w < (int)(sizeof(SimConst) / 16); w += kTile)
+                            dst[w] = __ldg(src + w);
+                    }
+                    __syncthreads();
+                    const SimConst &c = s_c;
                     switch (ph) {
                     case P_HASH: hash_item(c, blk); break;
                     case P_SCAN_T: scan_tiles_item(c, blk); break;
@@ -121,6 +137,41 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchConst b, int n_substeps, i
         for (int s = blockIdx.x; s < b.n_scenes; s += gridDim.x) cycle_end_item(b.scenes[s]);
 }
 
+// Per-phase alternative: one kernel per phase whose blocks are that phase's tiles over all
+// scenes (no grid barrier; each phase keeps its own register budget and occupancy).
+template <int PH>
+__global__ void __launch_bounds__(kTile) k_batch_phase(BatchConst b)
+{
+    __shared__ __align__(16) SimConst s_c;
+    const int *pre = b.prefix + PH * (b.n_scenes + 1);
+    const int it = blockIdx.x;
+    const int s = scene_of(pre, b.n_scenes, it);
+    const int blk = it - pre[s];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(b.scenes + s);
+        int4 *dst = reinterpret_cast<int4 *>(&s_c);
+        for (int w = threadIdx.x; w < (int)(sizeof(SimConst) / 16); w += kTile) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    const SimConst &c = s_c;
+    switch (PH) {
+    case P_HASH: hash_item(c, blk); break;
+    case P_SCAN_T: scan_tiles_item(c, blk); break;
+    case P_SCAN_A: scan_apply_item(c, blk); break;
+    case P_SCATTER: scatter_item(c, blk); break;
+    case P_GATHER: rank_gather_item(c, blk); break;
+    case P_DENSITY: density_item(c, blk); break;
+    case P_FORCE: force_item(c, blk); break;
+    default: wrench_item(c, blk); break;
+    }
+}
+
+__global__ void k_batch_cycle_end(BatchConst b)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < b.n_scenes; s += gridDim.x * blockDim.x)
+        cycle_end_item(b.scenes[s]);
+}
+
 // One barrier and nothing else (exercises the bounded wait of the barrier).
 __global__ void __launch_bounds__(kTile) k_batch_barrier_only(BatchConst b) { grid_barrier(b); }
 
@@ -140,7 +191,7 @@ struct sph_batch {
     char *ws = nullptr;
     cudaStream_t stream = nullptr;
     BatchConst bc;
-    int sms = 0, max_bps = 0, bps = 0;
+    int sms = 0, max_bps = 0, bps = 0;   // bps == 0: per-phase kernels instead of one launch
     cudaGraphExec_t exec1 = nullptr, exec16 = nullptr;
     bool use_graph = true;
     std::string err;
@@ -181,8 +232,26 @@ sph_status bfail(sph_batch *b, sph_status s, const std::string &m)
             return bfail((b), SPH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+cudaError_t launch_phases(sph_batch *b, int n_substeps, int cycle_end)
+{
+    const BatchConst &bc = b->bc;
+    for (int i = 0; i < n_substeps; ++i) {
+        if (bc.total[P_HASH]) k_batch_phase<P_HASH><<<bc.total[P_HASH], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_SCAN_T]) k_batch_phase<P_SCAN_T><<<bc.total[P_SCAN_T], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_SCAN_A]) k_batch_phase<P_SCAN_A><<<bc.total[P_SCAN_A], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_SCATTER]) k_batch_phase<P_SCATTER><<<bc.total[P_SCATTER], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_GATHER]) k_batch_phase<P_GATHER><<<bc.total[P_GATHER], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_DENSITY]) k_batch_phase<P_DENSITY><<<bc.total[P_DENSITY], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_FORCE]) k_batch_phase<P_FORCE><<<bc.total[P_FORCE], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_WRENCH]) k_batch_phase<P_WRENCH><<<bc.total[P_WRENCH], kTile, 0, b->stream>>>(bc);
+    }
+    if (cycle_end) k_batch_cycle_end<<<(bc.n_scenes + 127) / 128, 128, 0, b->stream>>>(bc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch(sph_batch *b, int n_substeps, int cycle_end)
 {
+    if (b->bps == 0) return launch_phases(b, n_substeps, cycle_end);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(b->bps * b->sms));
     cfg.blockDim = dim3(kTile);
@@ -315,7 +384,7 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
 sph_status sph_batch_configure(sph_batch *b, int32_t blocks_per_sm, int32_t tiles_per_fetch)
 {
     if (!b) return SPH_ERR_ARG;
-    if (blocks_per_sm < 1 || blocks_per_sm > b->max_bps || tiles_per_fetch < 1 || tiles_per_fetch > 64)
+    if (blocks_per_sm < 0 || blocks_per_sm > b->max_bps || tiles_per_fetch < 1 || tiles_per_fetch > 64)
         return bfail(b, SPH_ERR_ARG, "geometry outside the resident limit");
     if (blocks_per_sm != b->bps || tiles_per_fetch != b->bc.chunk) drop_graphs(b);
     b->bps = blocks_per_sm;
@@ -353,8 +422,8 @@ sph_status sph_batch_tune(sph_batch *b, int32_t substeps_per_trial, int32_t out_
     float best = 1e30f;
     int best_bps = b->bps, best_chunk = b->bc.chunk;
     const int chunks[3] = {1, 2, 4};
-    for (int bps = 1; bps <= b->max_bps; ++bps)
-        for (int ci = 0; ci < 3; ++ci) {
+    for (int bps = 0; bps <= b->max_bps; ++bps)
+        for (int ci = 0; ci < (bps == 0 ? 1 : 3); ++ci) {
             sph_status st = sph_batch_configure(b, bps, chunks[ci]);
             if (st != SPH_OK) return st;
             BATCH_CUDA(b, launch_batch(b, 1, 0));          // warm-up
@@ -370,7 +439,7 @@ sph_status sph_batch_tune(sph_batch *b, int32_t substeps_per_trial, int32_t out_
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (sph_handle *h : b->handles) scene_advanced(h, b->max_bps * 3 * (1 + substeps_per_trial));
+    for (sph_handle *h : b->handles) scene_advanced(h, (b->max_bps * 3 + 1) * (1 + substeps_per_trial));
     sph_status st = sph_batch_configure(b, best_bps, best_chunk);
     if (out_choice) { out_choice[0] = best_bps; out_choice[1] = best_chunk; }
     return st;
@@ -399,7 +468,7 @@ sph_status sph_batch_test_barrier(sph_batch *b, int32_t missing_blocks, int32_t 
     bc.expect_extra = (unsigned)missing_blocks;
     bc.spin_limit = (unsigned)spin_limit;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(b->bps * b->sms));
+    cfg.gridDim = dim3((unsigned)(std::max(b->bps, 1) * b->sms));
     cfg.blockDim = dim3(kTile);
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];

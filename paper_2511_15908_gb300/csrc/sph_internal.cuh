@@ -39,7 +39,7 @@ struct DevBody {
 };
 
 // Everything a substep kernel needs, passed by value (lives in the constant bank).
-struct SimConst {
+struct __align__(16) SimConst {
     int n, nf, nb, n_body_particles;
     int nx, ny, nz, ncell;
     float o[3], inv_cell;

@@ -91,17 +91,31 @@ def test_autotuner_picks_a_valid_geometry_and_keeps_results(sph):
     batch = sph.Batch(bsims)
     max_bps = batch.info()["blocks_per_sm"]
     bps, chunk = batch.tune(substeps_per_trial=1)
-    assert 1 <= bps <= max_bps and chunk in (1, 2, 4)
-    trials = max_bps * 3 * 2             # warm-up + 1 timed substep per candidate
+    assert 0 <= bps <= max_bps and chunk in (1, 2, 4)
     batch.step(2)
     batch.sync()
     for sc, b in zip(scs, bsims):
         a = sph.Simulation(sc)
-        for _ in range(max_bps * 3):      # one update cycle per tuner candidate
+        for _ in range(max_bps * 3 + 1):  # warm-up + 1 timed substep per tuner candidate
             a.step(2)
         a.step(2)
         assert np.array_equal(a.state()["x"], b.state()["x"])
     batch.close()
+
+
+def test_per_phase_launches_equal_persistent(sph):
+    scs = _scene_set()[:4]
+    out = []
+    for bps in (0, 1):
+        sims = [sph.Simulation(sc) for sc in scs]
+        batch = sph.Batch(sims)
+        batch.configure(bps, 2)
+        batch.step(5)
+        batch.sync()
+        out.append([s.state()["x"] for s in sims])
+        batch.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
 
 
 def test_grid_barrier_gives_up_and_reports_timeout(sph):

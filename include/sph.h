@@ -232,6 +232,55 @@ sph_status sph_get_sort(sph_handle *h, uint32_t *h_keys, int32_t *h_ids, uint32_
  */
 sph_status sph_get_diag(sph_handle *h, double out[8]);
 
+/*
+ * Learned haptic-rate wrench surrogate (form 4 of the build; the paper has no learned
+ * part -- it motivates one by the ~60 Hz update rate of the engine loop, Sec. 3.3).
+ *
+ * sph_get_descriptor writes the 269 surrogate inputs of the grabbed body for the last
+ * substep into DEVICE memory d_out (enqueued on the handle's stream): pose (x y z qw qx qy
+ * qz), velocity (vx vy vz wx wy wz), then 4 x 4 x 4 cells of edge 2h centred on the grab
+ * point (x fastest), each with the mean density of its fluid particles and their
+ * mass-weighted mean velocity (zeros when empty).  Errors: SPH_ERR_STATE (nothing grabbed
+ * or no substep run).
+ */
+sph_status sph_get_descriptor(sph_handle *h, float *d_out);
+
+/*
+ * The model: a 269-128-128-128-6 multilayer perceptron with tanh-form GELU, BF16 weights
+ * and FP32 accumulation on tcgen05 tensor cores; inputs standardised and outputs
+ * de-standardised by the kernels.  Parameters (68,358 FP32 master values) in the order
+ * W1[128][269] b1[128] W2[128][128] b2[128] W3[128][128] b3[128] W4[6][128] b4[6].
+ * All buffers live in one caller-owned workspace sized for max_batch rows.
+ */
+typedef struct sph_mlp sph_mlp;
+
+int32_t sph_mlp_param_count(void);
+size_t sph_mlp_workspace_bytes(int32_t max_batch);
+sph_status sph_mlp_create(void *d_workspace, size_t bytes, void *cuda_stream, int32_t max_batch,
+                          sph_mlp **out);
+
+/* Host parameters (param_count FP32) and, if h_norm is not NULL, the standardisation
+ * xmean[269] xstd[269] ymean[6] ystd[6]; resets the Adam state.  Synchronises. */
+sph_status sph_mlp_set_params(sph_mlp *m, const float *h_params, const float *h_norm);
+sph_status sph_mlp_get_params(sph_mlp *m, float *h_params);
+
+/* d_x: DEVICE batch x 269 FP32 inputs; d_y: DEVICE batch x 6 wrench outputs.  Async. */
+sph_status sph_mlp_forward(sph_mlp *m, const float *d_x, int32_t batch, float *d_y);
+
+/* Gradient of the mean squared error on standardised outputs for targets d_t (DEVICE,
+ * batch x 6); h_grad (host, param_count, nullable) and h_loss (nullable).  Synchronises. */
+sph_status sph_mlp_gradients(sph_mlp *m, const float *d_x, const float *d_t, int32_t batch,
+                             float *h_grad, double *h_loss);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss; h_loss nullable (if given,
+ * synchronises and returns the loss before the step). */
+sph_status sph_mlp_train_step(sph_mlp *m, const float *d_x, const float *d_t, int32_t batch,
+                              float lr, double *h_loss);
+
+sph_status sph_mlp_sync(sph_mlp *m);
+const char *sph_mlp_last_error(const sph_mlp *m);
+void sph_mlp_destroy(sph_mlp *m);
+
 /* Counts: particles, fluid particles, grid cells (nx*ny*nz), bodies, substeps run. */
 sph_status sph_get_info(sph_handle *h, int64_t out[5]);
 

@@ -717,6 +717,15 @@ sph_status sph_get_sort(sph_handle *h, uint32_t *h_keys, int32_t *h_ids, uint32_
     return read_status(h);
 }
 
+sph_status sph_get_descriptor(sph_handle *h, float *d_out)
+{
+    if (!h || !d_out) return SPH_ERR_ARG;
+    if (h->grab < 0) return fail(h, SPH_ERR_STATE, "no grabbed body");
+    if (h->substeps == 0) return fail(h, SPH_ERR_STATE, "no substep has run");
+    SPH_CUDA(h, launch_descriptor(h->c, h->stream, h->grab, d_out));
+    return SPH_OK;
+}
+
 sph_status sph_get_diag(sph_handle *h, double out[8])
 {
     if (!h || !out) return SPH_ERR_ARG;

@@ -99,5 +99,6 @@ cudaError_t launch_set_grab(const SimConst &c, cudaStream_t s, int body, int gra
                             const float *pose_vel13, const float *grab_local, int set_pose,
                             int path_n);
 cudaError_t launch_sorted_keys(const SimConst &c, cudaStream_t s, uint32_t *keys, int *ids);
+cudaError_t launch_descriptor(const SimConst &c, cudaStream_t s, int grab_body, float *d_out);
 
 }  // namespace sphgb

@@ -1,0 +1,512 @@
+// sph_mlp.cu -- the learned haptic-rate wrench surrogate: a 269-128-128-128-6 GELU MLP with
+// BF16 weights and FP32 accumulation on tcgen05 tensor cores, trained on the GPU by these
+// kernels (forward, backward, Adam), and the pooled local descriptor it reads from the SPH
+// state.  The exact FP64 coupling reduction of the substep stays the fallback and judge.
+//
+// Parameters (FP32 master copy, logical layout, 68,358 values):
+//   W1[128][269] b1[128] W2[128][128] b2[128] W3[128][128] b3[128] W4[6][128] b4[6]
+// The GEMMs read zero-padded BF16 copies W1b[128][272], W2b, W3b[128][128], W4b[16][128].
+// Inputs are standardised ((x - mean) / std) and outputs de-standardised in the kernels.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+#include "sph_device.cuh"
+#include "tc_gemm.cuh"
+
+namespace sphgb {
+
+constexpr int kIn = 269, kInPad = 272, kHid = 128, kOut = 6, kOutPad = 16;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
+              kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid,
+              kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kOut * kHid, kParams = kOffB4 + kOut;
+static_assert(kParams == 68358, "parameter count");
+
+// ------------------------------------------------------------------ small kernels
+
+__global__ void k_refresh_bf16(const float *master, __nv_bfloat16 *w1, __nv_bfloat16 *w2,
+                               __nv_bfloat16 *w3, __nv_bfloat16 *w4, float *b4pad)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < kHid * kInPad) {
+        int r = t / kInPad, c = t % kInPad;
+        w1[t] = __float2bfloat16_rn(c < kIn ? master[kOffW1 + r * kIn + c] : 0.0f);
+    }
+    if (t < kHid * kHid) {
+        w2[t] = __float2bfloat16_rn(master[kOffW2 + t]);
+        w3[t] = __float2bfloat16_rn(master[kOffW3 + t]);
+    }
+    if (t < kOutPad * kHid) {
+        int r = t / kHid;
+        w4[t] = __float2bfloat16_rn(r < kOut ? master[kOffW4 + t] : 0.0f);
+    }
+    if (t < kOutPad) b4pad[t] = t < kOut ? master[kOffB4 + t] : 0.0f;
+}
+
+__global__ void k_prep_input(const float *x, int B, const float *mean, const float *inv_std,
+                             __nv_bfloat16 *xb)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * kInPad) return;
+    int b = t / kInPad, c = t % kInPad;
+    float v = c < kIn ? (x[(size_t)b * kIn + c] - mean[c]) * inv_std[c] : 0.0f;
+    xb[t] = __float2bfloat16_rn(v);
+}
+
+__global__ void k_output(const float *y, int B, const float *mean, const float *std_, float *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B * kOut) return;
+    int b = t / kOut, j = t % kOut;
+    out[t] = y[(size_t)b * kOutPad + j] * std_[j] + mean[j];
+}
+
+// MSE on standardised outputs: L = mean over B x 6 of (y - tn)^2; dY = 2 (y - tn) / (6 B).
+// One block; the loss is summed in a fixed order (deterministic).
+__global__ void k_loss_grad(const float *y, const float *t, int B, const float *mean,
+                            const float *inv_std, float *dyf, __nv_bfloat16 *dyb, double *loss)
+{
+    __shared__ double s[1024];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < B * kOutPad; i += blockDim.x) {
+        int b = i / kOutPad, j = i % kOutPad;
+        float g = 0.0f;
+        if (j < kOut) {
+            float tn = (t[(size_t)b * kOut + j] - mean[j]) * inv_std[j];
+            float d = y[i] - tn;
+            acc += (double)d * d;
+            g = 2.0f * d / (float)(kOut * B);
+        }
+        dyf[i] = g;
+        dyb[i] = __float2bfloat16_rn(g);
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = s[0] / (double)(kOut * B);
+}
+
+// Column sums of an [B][ld] FP32 matrix (bias gradients), fixed order.
+__global__ void k_colsum(const float *g, int B, int ld, int ncols, float *out)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncols) return;
+    float s = 0.0f;
+    for (int b = 0; b < B; ++b) s += g[(size_t)b * ld + c];
+    out[c] = s;
+}
+
+// Assemble the logical gradient vector from the GEMM outputs.
+__global__ void k_gather_grads(const float *dW1, const float *db1, const float *dW2, const float *db2,
+                               const float *dW3, const float *db3, const float *dW4t, const float *db4,
+                               float *grad)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kParams) return;
+    float v;
+    if (t < kOffB1) { int r = t / kIn, c = t % kIn; v = dW1[r * kInPad + c]; }
+    else if (t < kOffW2) v = db1[t - kOffB1];
+    else if (t < kOffB2) v = dW2[t - kOffW2];
+    else if (t < kOffW3) v = db2[t - kOffB2];
+    else if (t < kOffB3) v = dW3[t - kOffW3];
+    else if (t < kOffW4) v = db3[t - kOffB3];
+    else if (t < kOffB4) { int q = t - kOffW4, j = q / kHid, i = q % kHid; v = dW4t[i * kOutPad + j]; }
+    else v = db4[t - kOffB4];
+    grad[t] = v;
+}
+
+__global__ void k_adam(float *w, float *m, float *v, const float *g, int n, float lr, float b1, float b2,
+                       float eps, float c1, float c2)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float gi = g[t];
+    float mi = b1 * m[t] + (1.0f - b1) * gi;
+    float vi = b2 * v[t] + (1.0f - b2) * gi * gi;
+    m[t] = mi;
+    v[t] = vi;
+    w[t] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+}
+
+// ------------------------------------------------------------- pooled descriptor
+
+// Surrogate input for the grabbed body: pose (x 3, q 4) and velocity (v 3, w 3) of the
+// substep's pose, then a 4 x 4 x 4 grid of cells of edge R = 2h centred on the grab point;
+// per cell (x fastest) the mean density of the fluid particles inside and their
+// mass-weighted mean velocity (zeros for an empty cell).  One thread per descriptor cell
+// scans the grid cells that overlap it in a fixed order (deterministic).
+__global__ void k_descriptor(SimConst c, int grab_body, float *out)
+{
+    const int cell = threadIdx.x;                  // 0..63
+    const DevBody &B = c.body[grab_body];
+    Pose P = body_pose(c, B, c.ctr[0] > 0 ? c.ctr[0] - 1u : 0u);
+    double R9[9], xg[3];
+    grab_point(P, B, xg, R9);
+    const float Rs = 2.0f * c.h;
+    const int ci = cell & 3, cj = (cell >> 2) & 3, ck = cell >> 4;
+    const float lo[3] = {(float)xg[0] + (ci - 2) * Rs, (float)xg[1] + (cj - 2) * Rs, (float)xg[2] + (ck - 2) * Rs};
+    const float hi[3] = {lo[0] + Rs, lo[1] + Rs, lo[2] + Rs};
+    uint32_t bad = 0;
+    int g0[3], g1[3];
+    for (int a = 0; a < 3; ++a) {
+        const int n = a == 0 ? c.nx : (a == 1 ? c.ny : c.nz);
+        g0[a] = cell_axis(lo[a], c.o[a], c.inv_cell, n, bad);
+        g1[a] = cell_axis(hi[a], c.o[a], c.inv_cell, n, bad);
+    }
+    float sr = 0.0f, sm = 0.0f, svx = 0.0f, svy = 0.0f, svz = 0.0f;
+    int cnt = 0;
+    for (int z = g0[2]; z <= g1[2]; ++z)
+        for (int y = g0[1]; y <= g1[1]; ++y) {
+            const int base = (z * c.ny + y) * c.nx;
+            const int s = (int)c.cell_start[base + g0[0]], e = (int)c.cell_start[base + g1[0] + 1];
+            for (int q = s; q < e; ++q) {
+                const float4 x = c.xA[q];
+                const float4 v = c.vA[q];
+                if (__float_as_int(v.w) >= c.nf) continue;          // fluid particles only
+                if (x.x < lo[0] || x.x >= hi[0] || x.y < lo[1] || x.y >= hi[1] || x.z < lo[2] || x.z >= hi[2])
+                    continue;
+                const float m = fabsf(x.w);
+                sr += c.prho[q].x;
+                sm += m;
+                svx += m * v.x; svy += m * v.y; svz += m * v.z;
+                ++cnt;
+            }
+        }
+    float *d = out + 13 + 4 * cell;
+    d[0] = cnt ? sr / (float)cnt : 0.0f;
+    d[1] = sm > 0.0f ? svx / sm : 0.0f;
+    d[2] = sm > 0.0f ? svy / sm : 0.0f;
+    d[3] = sm > 0.0f ? svz / sm : 0.0f;
+    if (cell == 0) {
+        for (int a = 0; a < 3; ++a) { out[a] = P.t[a]; out[7 + a] = P.v[a]; out[10 + a] = P.w[a]; }
+        for (int a = 0; a < 4; ++a) out[3 + a] = P.q[a];
+    }
+}
+
+cudaError_t launch_descriptor(const SimConst &c, cudaStream_t s, int grab_body, float *d_out)
+{
+    k_descriptor<<<1, 64, 0, s>>>(c, grab_body, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace sphgb
+
+using namespace sphgb;
+
+struct sph_mlp {
+    cudaStream_t stream = nullptr;
+    int max_batch = 0;
+    int adam_t = 0;
+    float *master, *m, *v, *grad, *norm;   // norm: xmean[269] xinv[269] ymean[6] ystd[6] yinv[6]
+    __nv_bfloat16 *w1b, *w2b, *w3b, *w4b;
+    float *b4pad;
+    __nv_bfloat16 *xb, *h1, *h2, *h3, *dyb, *dz3, *dz2, *dz1;
+    float *z1, *z2, *z3, *y, *dyf, *dz3f, *dz2f, *dz1f, *out;
+    float *dW1, *dW2, *dW3, *dW4t, *db1, *db2, *db3, *db4;
+    double *loss;
+    unsigned *status;
+    std::string err;
+};
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct MlpLayout {
+    size_t off[48];
+    size_t total;
+};
+
+// Every buffer of the surrogate, in order; sizes in bytes for batch capacity B.
+size_t mlp_sizes(int B, size_t *sz)
+{
+    int i = 0;
+    sz[i++] = 4 * (size_t)kParams;            // master
+    sz[i++] = 4 * (size_t)kParams;            // m
+    sz[i++] = 4 * (size_t)kParams;            // v
+    sz[i++] = 4 * (size_t)kParams;            // grad
+    sz[i++] = 4 * (size_t)(2 * kIn + 3 * kOut);  // norm
+    sz[i++] = 2 * (size_t)kHid * kInPad;      // w1b
+    sz[i++] = 2 * (size_t)kHid * kHid;        // w2b
+    sz[i++] = 2 * (size_t)kHid * kHid;        // w3b
+    sz[i++] = 2 * (size_t)kOutPad * kHid;     // w4b
+    sz[i++] = 4 * (size_t)kOutPad;            // b4pad
+    sz[i++] = 2 * (size_t)B * kInPad;         // xb
+    for (int k = 0; k < 3; ++k) sz[i++] = 2 * (size_t)B * kHid;   // h1 h2 h3
+    sz[i++] = 2 * (size_t)B * kOutPad;        // dyb
+    for (int k = 0; k < 3; ++k) sz[i++] = 2 * (size_t)B * kHid;   // dz3 dz2 dz1
+    for (int k = 0; k < 3; ++k) sz[i++] = 4 * (size_t)B * kHid;   // z1 z2 z3
+    sz[i++] = 4 * (size_t)B * kOutPad;        // y
+    sz[i++] = 4 * (size_t)B * kOutPad;        // dyf
+    for (int k = 0; k < 3; ++k) sz[i++] = 4 * (size_t)B * kHid;   // dz3f dz2f dz1f
+    sz[i++] = 4 * (size_t)B * kOut;           // out
+    sz[i++] = 4 * (size_t)kHid * kInPad;      // dW1
+    sz[i++] = 4 * (size_t)kHid * kHid;        // dW2
+    sz[i++] = 4 * (size_t)kHid * kHid;        // dW3
+    sz[i++] = 4 * (size_t)kHid * kOutPad;     // dW4t
+    sz[i++] = 4 * (size_t)kHid;               // db1
+    sz[i++] = 4 * (size_t)kHid;               // db2
+    sz[i++] = 4 * (size_t)kHid;               // db3
+    sz[i++] = 4 * (size_t)kOutPad;            // db4
+    sz[i++] = 8;                              // loss
+    sz[i++] = 16;                             // status
+    return (size_t)i;
+}
+
+MlpLayout mlp_layout(int B)
+{
+    MlpLayout L;
+    size_t sz[48];
+    size_t n = mlp_sizes(B, sz), off = 0;
+    for (size_t k = 0; k < n; ++k) { L.off[k] = off; off = a256(off + sz[k]); }
+    L.total = off;
+    return L;
+}
+
+sph_status mfail(sph_mlp *m, sph_status s, const std::string &msg)
+{
+    if (m) m->err = msg;
+    return s;
+}
+
+#define MLP_CUDA(m, call)                                                            \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return mfail((m), SPH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+TcGemm gemm(const void *A, int lda, int akc, int af32, const void *B, int ldb, int bkc, int bf32, int M,
+            int N, int K, float *C, int ldc, unsigned *status)
+{
+    TcGemm g;
+    std::memset(&g, 0, sizeof g);
+    g.A = A; g.lda = lda; g.a_kcontig = akc; g.a_f32 = af32;
+    g.B = B; g.ldb = ldb; g.b_kcontig = bkc; g.b_f32 = bf32;
+    g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc;
+    g.epilogue = TC_STORE;
+    g.status = status;
+    return g;
+}
+
+sph_status mlp_forward(sph_mlp *m, const float *d_x, int B)
+{
+    cudaStream_t s = m->stream;
+    const float *xmean = m->norm, *xinv = m->norm + kIn;
+    k_prep_input<<<(B * kInPad + 255) / 256, 256, 0, s>>>(d_x, B, xmean, xinv, m->xb);
+    MLP_CUDA(m, cudaGetLastError());
+    const __nv_bfloat16 *in[3] = {m->xb, m->h1, m->h2};
+    const __nv_bfloat16 *w[3] = {m->w1b, m->w2b, m->w3b};
+    __nv_bfloat16 *hout[3] = {m->h1, m->h2, m->h3};
+    float *z[3] = {m->z1, m->z2, m->z3};
+    const int kdim[3] = {kInPad, kHid, kHid};
+    const int boff[3] = {kOffB1, kOffB2, kOffB3};
+    for (int l = 0; l < 3; ++l) {
+        TcGemm g = gemm(in[l], kdim[l], 1, 0, w[l], kdim[l], 1, 0, B, kHid, kdim[l], z[l], kHid, m->status);
+        g.epilogue = TC_BIAS_GELU;
+        g.bias = m->master + boff[l];
+        g.aux_out = hout[l];
+        g.ldaux = kHid;
+        MLP_CUDA(m, tc_gemm(g, s));
+    }
+    TcGemm g = gemm(m->h3, kHid, 1, 0, m->w4b, kHid, 1, 0, B, kOutPad, kHid, m->y, kOutPad, m->status);
+    g.epilogue = TC_BIAS;
+    g.bias = m->b4pad;
+    MLP_CUDA(m, tc_gemm(g, s));
+    return SPH_OK;
+}
+
+sph_status mlp_backward(sph_mlp *m, const float *d_t, int B)
+{
+    cudaStream_t s = m->stream;
+    const float *ymean = m->norm + 2 * kIn, *yinv = m->norm + 2 * kIn + 2 * kOut;
+    k_loss_grad<<<1, 1024, 0, s>>>(m->y, d_t, B, ymean, yinv, m->dyf, m->dyb, m->loss);
+    MLP_CUDA(m, cudaGetLastError());
+    // layer 4: dW4^T = H3^T dY (rows = 128 inputs, K = batch); db4 = colsum(dY)
+    MLP_CUDA(m, tc_gemm(gemm(m->h3, kHid, 0, 0, m->dyb, kOutPad, 0, 0, kHid, kOutPad, B, m->dW4t, kOutPad,
+                             m->status), s));
+    k_colsum<<<1, 32, 0, s>>>(m->dyf, B, kOutPad, kOutPad, m->db4);
+    // dZ3 = (dY W4) * gelu'(Z3)
+    {
+        TcGemm g = gemm(m->dyb, kOutPad, 1, 0, m->w4b, kHid, 0, 0, B, kHid, kOutPad, m->dz3f, kHid, m->status);
+        g.epilogue = TC_GELU_GRAD; g.aux_in = m->z3; g.aux_out = m->dz3; g.ldaux = kHid;
+        MLP_CUDA(m, tc_gemm(g, s));
+    }
+    // layers 3 and 2: dW = dZ^T H_prev, db = colsum(dZ), dZ_prev = (dZ W) * gelu'(Z_prev)
+    struct L { __nv_bfloat16 *dz; float *dzf; const __nv_bfloat16 *hprev; __nv_bfloat16 *w; float *dW, *db;
+               float *zprev; __nv_bfloat16 *dzprev; float *dzprevf; };
+    L layers[2] = {{m->dz3, m->dz3f, m->h2, m->w3b, m->dW3, m->db3, m->z2, m->dz2, m->dz2f},
+                   {m->dz2, m->dz2f, m->h1, m->w2b, m->dW2, m->db2, m->z1, m->dz1, m->dz1f}};
+    for (const L &l : layers) {
+        MLP_CUDA(m, tc_gemm(gemm(l.dz, kHid, 0, 0, l.hprev, kHid, 0, 0, kHid, kHid, B, l.dW, kHid, m->status), s));
+        k_colsum<<<1, kHid, 0, s>>>(l.dzf, B, kHid, kHid, l.db);
+        TcGemm g = gemm(l.dz, kHid, 1, 0, l.w, kHid, 0, 0, B, kHid, kHid, l.dzprevf, kHid, m->status);
+        g.epilogue = TC_GELU_GRAD; g.aux_in = l.zprev; g.aux_out = l.dzprev; g.ldaux = kHid;
+        MLP_CUDA(m, tc_gemm(g, s));
+    }
+    // layer 1: dW1 = dZ1^T Xb (N = 272 -> two column tiles), db1
+    MLP_CUDA(m, tc_gemm(gemm(m->dz1, kHid, 0, 0, m->xb, kInPad, 0, 0, kHid, kInPad, B, m->dW1, kInPad,
+                             m->status), s));
+    k_colsum<<<1, kHid, 0, s>>>(m->dz1f, B, kHid, kHid, m->db1);
+    k_gather_grads<<<(kParams + 255) / 256, 256, 0, s>>>(m->dW1, m->db1, m->dW2, m->db2, m->dW3, m->db3,
+                                                         m->dW4t, m->db4, m->grad);
+    MLP_CUDA(m, cudaGetLastError());
+    return SPH_OK;
+}
+
+sph_status mlp_status(sph_mlp *m)
+{
+    unsigned st = 0;
+    MLP_CUDA(m, cudaMemcpyAsync(&st, m->status, 4, cudaMemcpyDeviceToHost, m->stream));
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (st) {
+        MLP_CUDA(m, cudaMemsetAsync(m->status, 0, 4, m->stream));
+        return mfail(m, SPH_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+    }
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sph_mlp_param_count(void) { return kParams; }
+
+size_t sph_mlp_workspace_bytes(int32_t max_batch)
+{
+    if (max_batch < 1 || max_batch > (1 << 20)) return 0;
+    return mlp_layout(max_batch).total;
+}
+
+sph_status sph_mlp_create(void *d_workspace, size_t bytes, void *cuda_stream, int32_t max_batch,
+                          sph_mlp **out)
+{
+    if (!out) return SPH_ERR_ARG;
+    *out = nullptr;
+    if (max_batch < 1) return SPH_ERR_ARG;
+    MlpLayout L = mlp_layout(max_batch);
+    if (!d_workspace || bytes < L.total || ((uintptr_t)d_workspace & 255u)) return SPH_ERR_WORKSPACE;
+    sph_mlp *m = new sph_mlp();
+    m->stream = (cudaStream_t)cuda_stream;
+    m->max_batch = max_batch;
+    char *ws = (char *)d_workspace;
+    int i = 0;
+    auto f = [&]() { return reinterpret_cast<float *>(ws + L.off[i++]); };
+    auto h = [&]() { return reinterpret_cast<__nv_bfloat16 *>(ws + L.off[i++]); };
+    m->master = f(); m->m = f(); m->v = f(); m->grad = f(); m->norm = f();
+    m->w1b = h(); m->w2b = h(); m->w3b = h(); m->w4b = h(); m->b4pad = f();
+    m->xb = h(); m->h1 = h(); m->h2 = h(); m->h3 = h(); m->dyb = h();
+    m->dz3 = h(); m->dz2 = h(); m->dz1 = h();
+    m->z1 = f(); m->z2 = f(); m->z3 = f(); m->y = f(); m->dyf = f();
+    m->dz3f = f(); m->dz2f = f(); m->dz1f = f(); m->out = f();
+    m->dW1 = f(); m->dW2 = f(); m->dW3 = f(); m->dW4t = f();
+    m->db1 = f(); m->db2 = f(); m->db3 = f(); m->db4 = f();
+    m->loss = reinterpret_cast<double *>(ws + L.off[i++]);
+    m->status = reinterpret_cast<unsigned *>(ws + L.off[i++]);
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.total, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) { delete m; return SPH_ERR_CUDA; }
+    *out = m;
+    return SPH_OK;
+}
+
+sph_status sph_mlp_set_params(sph_mlp *m, const float *h_params, const float *h_norm)
+{
+    if (!m || !h_params) return SPH_ERR_ARG;
+    MLP_CUDA(m, cudaMemcpyAsync(m->master, h_params, 4 * (size_t)kParams, cudaMemcpyHostToDevice, m->stream));
+    if (h_norm) {
+        // h_norm: xmean[269] xstd[269] ymean[6] ystd[6]; stored with reciprocals
+        std::vector<float> nb(2 * kIn + 3 * kOut);
+        for (int c = 0; c < kIn; ++c) { nb[c] = h_norm[c]; nb[kIn + c] = 1.0f / h_norm[kIn + c]; }
+        for (int j = 0; j < kOut; ++j) {
+            nb[2 * kIn + j] = h_norm[2 * kIn + j];
+            nb[2 * kIn + kOut + j] = h_norm[2 * kIn + kOut + j];
+            nb[2 * kIn + 2 * kOut + j] = 1.0f / h_norm[2 * kIn + kOut + j];
+        }
+        MLP_CUDA(m, cudaMemcpyAsync(m->norm, nb.data(), 4 * nb.size(), cudaMemcpyHostToDevice, m->stream));
+    }
+    MLP_CUDA(m, cudaMemsetAsync(m->m, 0, 4 * (size_t)kParams, m->stream));
+    MLP_CUDA(m, cudaMemsetAsync(m->v, 0, 4 * (size_t)kParams, m->stream));
+    m->adam_t = 0;
+    k_refresh_bf16<<<(kHid * kInPad + 255) / 256, 256, 0, m->stream>>>(m->master, m->w1b, m->w2b, m->w3b,
+                                                                       m->w4b, m->b4pad);
+    MLP_CUDA(m, cudaGetLastError());
+    MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+    return SPH_OK;
+}
+
+sph_status sph_mlp_get_params(sph_mlp *m, float *h_params)
+{
+    if (!m || !h_params) return SPH_ERR_ARG;
+    MLP_CUDA(m, cudaMemcpyAsync(h_params, m->master, 4 * (size_t)kParams, cudaMemcpyDeviceToHost, m->stream));
+    return mlp_status(m);
+}
+
+sph_status sph_mlp_forward(sph_mlp *m, const float *d_x, int32_t batch, float *d_y)
+{
+    if (!m || !d_x || !d_y || batch < 1 || batch > m->max_batch) return SPH_ERR_ARG;
+    sph_status st = mlp_forward(m, d_x, batch);
+    if (st != SPH_OK) return st;
+    const float *ymean = m->norm + 2 * kIn, *ystd = m->norm + 2 * kIn + kOut;
+    k_output<<<(batch * kOut + 255) / 256, 256, 0, m->stream>>>(m->y, batch, ymean, ystd, d_y);
+    MLP_CUDA(m, cudaGetLastError());
+    return SPH_OK;
+}
+
+sph_status sph_mlp_gradients(sph_mlp *m, const float *d_x, const float *d_t, int32_t batch, float *h_grad,
+                             double *h_loss)
+{
+    if (!m || !d_x || !d_t || batch < 1 || batch > m->max_batch) return SPH_ERR_ARG;
+    sph_status st = mlp_forward(m, d_x, batch);
+    if (st == SPH_OK) st = mlp_backward(m, d_t, batch);
+    if (st != SPH_OK) return st;
+    if (h_grad)
+        MLP_CUDA(m, cudaMemcpyAsync(h_grad, m->grad, 4 * (size_t)kParams, cudaMemcpyDeviceToHost, m->stream));
+    if (h_loss) MLP_CUDA(m, cudaMemcpyAsync(h_loss, m->loss, 8, cudaMemcpyDeviceToHost, m->stream));
+    return mlp_status(m);
+}
+
+sph_status sph_mlp_train_step(sph_mlp *m, const float *d_x, const float *d_t, int32_t batch, float lr,
+                              double *h_loss)
+{
+    if (!m || !d_x || !d_t || batch < 1 || batch > m->max_batch || !(lr > 0.0f)) return SPH_ERR_ARG;
+    sph_status st = mlp_forward(m, d_x, batch);
+    if (st == SPH_OK) st = mlp_backward(m, d_t, batch);
+    if (st != SPH_OK) return st;
+    m->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f / (1.0f - std::pow(b1, (float)m->adam_t));
+    const float c2 = 1.0f / (1.0f - std::pow(b2, (float)m->adam_t));
+    k_adam<<<(kParams + 255) / 256, 256, 0, m->stream>>>(m->master, m->m, m->v, m->grad, kParams, lr, b1, b2,
+                                                         1e-8f, c1, c2);
+    k_refresh_bf16<<<(kHid * kInPad + 255) / 256, 256, 0, m->stream>>>(m->master, m->w1b, m->w2b, m->w3b,
+                                                                       m->w4b, m->b4pad);
+    MLP_CUDA(m, cudaGetLastError());
+    if (h_loss) {
+        MLP_CUDA(m, cudaMemcpyAsync(h_loss, m->loss, 8, cudaMemcpyDeviceToHost, m->stream));
+        return mlp_status(m);
+    }
+    return SPH_OK;
+}
+
+sph_status sph_mlp_sync(sph_mlp *m)
+{
+    if (!m) return SPH_ERR_ARG;
+    return mlp_status(m);
+}
+
+const char *sph_mlp_last_error(const sph_mlp *m) { return m ? m->err.c_str() : "null model"; }
+
+void sph_mlp_destroy(sph_mlp *m)
+{
+    if (!m) return;
+    cudaStreamSynchronize(m->stream);
+    delete m;
+}
+
+}  // extern "C"

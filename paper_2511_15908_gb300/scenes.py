@@ -364,3 +364,19 @@ def with_velocity_noise(scene: Scene, seed: int = 0, sigma: float = 0.2) -> Scen
         scene.trajectory = scene.trajectory.copy()
         scene.trajectory[:, 10:13] = rng.normal(0.0, sigma, 3).astype(np.float32)
     return scene
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Seeded initial surrogate parameters in the layout W1[128][269] b1 W2[128][128] b2
+    W3[128][128] b3 W4[6][128] b4: weights uniform in +-1/sqrt(fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    sizes = [(128, 269), (128,), (128, 128), (128,), (128, 128), (128,), (6, 128), (6,)]
+    out = []
+    for s in sizes:
+        out.append(rng.uniform(-1, 1, s) / np.sqrt(s[1]) if len(s) == 2 else np.zeros(s))
+    return np.concatenate([a.ravel() for a in out]).astype(np.float32)
+
+
+def mlp_identity_norm() -> np.ndarray:
+    """Standardisation vectors xmean[269] xstd[269] ymean[6] ystd[6] that leave data as is."""
+    return np.concatenate([np.zeros(269), np.ones(269), np.zeros(6), np.ones(6)]).astype(np.float32)

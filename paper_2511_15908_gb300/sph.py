@@ -30,7 +30,10 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_last_error", "sph_destroy", "sph_set_profiling", "sph_get_kernel_times",
            "sph_batch_workspace_bytes", "sph_batch_create", "sph_batch_configure", "sph_batch_tune",
            "sph_batch_step", "sph_batch_sync", "sph_batch_info", "sph_batch_last_error",
-           "sph_batch_destroy", "sph_batch_test_barrier"]
+           "sph_batch_destroy", "sph_batch_test_barrier", "sph_get_descriptor",
+           "sph_mlp_param_count", "sph_mlp_workspace_bytes", "sph_mlp_create", "sph_mlp_set_params",
+           "sph_mlp_get_params", "sph_mlp_forward", "sph_mlp_gradients", "sph_mlp_train_step",
+           "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -133,6 +136,30 @@ def load(path: str = LIB_PATH):
     L.sph_batch_last_error.argtypes = [_vp]
     L.sph_batch_destroy.restype = None
     L.sph_batch_destroy.argtypes = [_vp]
+    L.sph_get_descriptor.restype = st
+    L.sph_get_descriptor.argtypes = [_vp, _vp]
+    L.sph_mlp_param_count.restype = ctypes.c_int32
+    L.sph_mlp_param_count.argtypes = []
+    L.sph_mlp_workspace_bytes.restype = ctypes.c_size_t
+    L.sph_mlp_workspace_bytes.argtypes = [ctypes.c_int32]
+    L.sph_mlp_create.restype = st
+    L.sph_mlp_create.argtypes = [_vp, ctypes.c_size_t, _vp, ctypes.c_int32, ctypes.POINTER(_vp)]
+    L.sph_mlp_set_params.restype = st
+    L.sph_mlp_set_params.argtypes = [_vp, _f32p, _f32p]
+    L.sph_mlp_get_params.restype = st
+    L.sph_mlp_get_params.argtypes = [_vp, _f32p]
+    L.sph_mlp_forward.restype = st
+    L.sph_mlp_forward.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
+    L.sph_mlp_gradients.restype = st
+    L.sph_mlp_gradients.argtypes = [_vp, _vp, _vp, ctypes.c_int32, _f32p, _f64p]
+    L.sph_mlp_train_step.restype = st
+    L.sph_mlp_train_step.argtypes = [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float, _f64p]
+    L.sph_mlp_sync.restype = st
+    L.sph_mlp_sync.argtypes = [_vp]
+    L.sph_mlp_last_error.restype = ctypes.c_char_p
+    L.sph_mlp_last_error.argtypes = [_vp]
+    L.sph_mlp_destroy.restype = None
+    L.sph_mlp_destroy.argtypes = [_vp]
     L.sph_sync.restype = st
     L.sph_sync.argtypes = [_vp]
     L.sph_last_error.restype = ctypes.c_char_p
@@ -312,6 +339,17 @@ class Simulation:
         self._check(self.L.sph_get_diag(self.h, _ptr(out, ctypes.c_double)))
         return out
 
+    def descriptor_into(self, d_out) -> None:
+        """Write the 269 surrogate inputs of the last substep into a CUDA float tensor."""
+        self._check(self.L.sph_get_descriptor(self.h, d_out.data_ptr()))
+
+    def descriptor(self) -> np.ndarray:
+        import torch
+        d = torch.empty(269, dtype=torch.float32, device=self.device)
+        self.descriptor_into(d)
+        self.stream.synchronize()
+        return d.cpu().numpy()
+
     def set_profiling(self, on: bool = True):
         self._check(self.L.sph_set_profiling(self.h, int(on)))
 
@@ -385,6 +423,79 @@ class Batch:
         if getattr(self, "b", None):
             self.L.sph_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """The 269-128-128-128-6 BF16 tensor-core MLP behind the sph_mlp_* calls."""
+
+    N_IN, N_OUT = 269, 6
+
+    def __init__(self, max_batch: int = 4096, stream=None, device: int = 0):
+        import torch
+        self.L = load()
+        self.max_batch = max_batch
+        self.device = torch.device("cuda", device)
+        nbytes = self.L.sph_mlp_workspace_bytes(max_batch)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        m = _vp()
+        st = self.L.sph_mlp_create(self.workspace.data_ptr(), nbytes, self.stream.cuda_stream, max_batch,
+                                   ctypes.byref(m))
+        if st != OK:
+            raise SphError(st, "sph_mlp_create failed")
+        self.m = m
+        self.n_params = int(self.L.sph_mlp_param_count())
+
+    def _check(self, st):
+        if st != OK:
+            raise SphError(st, self.L.sph_mlp_last_error(self.m).decode())
+
+    def set_params(self, params, norm=None):
+        params = np.ascontiguousarray(params, np.float32)
+        assert params.size == self.n_params
+        norm = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        self._check(self.L.sph_mlp_set_params(self.m, _ptr(params, ctypes.c_float), _ptr(norm, ctypes.c_float)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.n_params, np.float32)
+        self._check(self.L.sph_mlp_get_params(self.m, _ptr(out, ctypes.c_float)))
+        return out
+
+    def forward(self, x_dev, y_dev=None):
+        """x_dev: CUDA float32 tensor (B, 269); returns a (B, 6) CUDA tensor."""
+        import torch
+        B = int(x_dev.shape[0])
+        if y_dev is None:
+            y_dev = torch.empty((B, 6), dtype=torch.float32, device=self.device)
+        self._check(self.L.sph_mlp_forward(self.m, x_dev.data_ptr(), B, y_dev.data_ptr()))
+        return y_dev
+
+    def gradients(self, x_dev, t_dev):
+        g = np.zeros(self.n_params, np.float32)
+        loss = np.zeros(1, np.float64)
+        self._check(self.L.sph_mlp_gradients(self.m, x_dev.data_ptr(), t_dev.data_ptr(), int(x_dev.shape[0]),
+                                             _ptr(g, ctypes.c_float), _ptr(loss, ctypes.c_double)))
+        return g, float(loss[0])
+
+    def train_step(self, x_dev, t_dev, lr: float, want_loss: bool = False):
+        loss = np.zeros(1, np.float64) if want_loss else None
+        self._check(self.L.sph_mlp_train_step(self.m, x_dev.data_ptr(), t_dev.data_ptr(), int(x_dev.shape[0]),
+                                              float(lr), _ptr(loss, ctypes.c_double)))
+        return float(loss[0]) if want_loss else None
+
+    def sync(self):
+        self._check(self.L.sph_mlp_sync(self.m))
+
+    def close(self):
+        if getattr(self, "m", None):
+            self.L.sph_mlp_destroy(self.m)
+            self.m = None
 
     def __del__(self):
         try:

@@ -1,0 +1,111 @@
+"""Form 4: the BF16 tcgen05 MLP surrogate (forward, backward, Adam) and its descriptor,
+against the FP64 oracle with BF16 rounding at the same points."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2511_15908_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15908_gb300 import build, sph as _sph
+    build.build()
+    _sph.load()
+    return _sph
+
+
+def _data(B, seed=0):
+    rng = np.random.default_rng(seed)
+    params = scenes.mlp_init_params(seed)
+    o = 128 * 269
+    params[o:o + 128] = rng.normal(0, 0.1, 128).astype(np.float32)
+    norm = np.concatenate([rng.normal(0, 1, 269), rng.uniform(0.5, 2, 269), rng.normal(0, 1, 6),
+                           rng.uniform(0.5, 2, 6)]).astype(np.float32)
+    X = (norm[:269] + norm[269:538] * rng.normal(0, 1, (B, 269))).astype(np.float32)
+    T = (norm[538:544] + norm[544:550] * rng.normal(0, 1, (B, 6))).astype(np.float32)
+    return params, norm, X, T
+
+
+def test_forward_matches_oracle(sph):
+    import torch
+    params, norm, X, _ = _data(300)          # 3 row tiles, ragged tail
+    m = sph.Surrogate(max_batch=512)
+    m.set_params(params, norm)
+    y = m.forward(torch.tensor(X, device="cuda"))
+    m.sync()
+    ref = omlp.forward(params, norm, X, bf=True)
+    got = y.cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 2e-3 * scale, np.abs(got - ref).max() / scale
+    m.close()
+
+
+def test_gradients_match_oracle(sph):
+    import torch
+    params, norm, X, T = _data(272, seed=1)
+    m = sph.Surrogate(max_batch=512)
+    m.set_params(params, norm)
+    g, loss = m.gradients(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"))
+    lref, gref = omlp.grad(params, norm, X, T, bf=True)
+    assert loss == pytest.approx(lref, rel=1e-4)
+    bounds = [0, 128 * 269, 128 * 270, 128 * 270 + 16384, 128 * 271 + 16384, 128 * 271 + 32768,
+              128 * 272 + 32768, 128 * 272 + 32768 + 768, omlp.param_count()]
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        ga, gb = g[a:b].astype(np.float64), gref[a:b]
+        rel = np.linalg.norm(ga - gb) / np.linalg.norm(gb)
+        assert rel <= 1e-2, (a, b, rel)
+    m.close()
+
+
+def test_adam_training_fits_a_teacher(sph):
+    import torch
+    rng = np.random.default_rng(5)
+    B = 1024
+    teacher = scenes.mlp_init_params(11)
+    norm = scenes.mlp_identity_norm()
+    X = rng.normal(0, 1, (B, 269)).astype(np.float32)
+    T = omlp.forward(teacher, norm, X, bf=False).astype(np.float32)
+    m = sph.Surrogate(max_batch=B)
+    m.set_params(scenes.mlp_init_params(3), norm)
+    x, t = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    first = m.train_step(x, t, 1e-3, want_loss=True)
+    for _ in range(300):
+        m.train_step(x, t, 1e-3)
+    last = m.train_step(x, t, 1e-3, want_loss=True)
+    assert last < 0.1 * first, (first, last)
+    m.close()
+
+
+def test_descriptor_matches_oracle(sph):
+    import torch
+    sc = scenes.with_velocity_noise(
+        scenes.stirring_tank(seed=2, n_fluid=30_000, cols=(50, 50), tank=(0.4, 0.4, 0.3), n_substeps=10,
+                             paddle=(0.02, 0.1, 0.2)), seed=9, sigma=0.2)
+    sim = sph.Simulation(sc)
+    sim.step(1)
+    d = sim.descriptor()
+    ref_sub = oracle.System(sc, mode=1).substep()
+    n = sc.n_total
+    rho = np.empty(n)
+    rho[ref_sub["id"]] = ref_sub["rho"]
+    nf = sc.n_fluid
+    m = np.full(nf, np.float32(1000) * np.float32(np.float32(np.float32(0.008) * np.float32(0.008)) * np.float32(0.008)),
+                np.float64)
+    row = sc.trajectory[0]
+    ref = omlp.descriptor(sc.fluid_x, sc.fluid_v.astype(np.float64), rho[:nf], m, np.ones(nf, np.int32),
+                          row[:3].astype(np.float64), row, np.float32(sc.params["h"]))
+    np.testing.assert_array_equal(d[:13], row)
+    cells = d[13:].reshape(64, 4)
+    rc = ref[13:].reshape(64, 4)
+    assert np.array_equal(cells[:, 0] > 0, rc[:, 0] > 0)
+    assert (rc[:, 0] > 0).sum() >= 8
+    np.testing.assert_allclose(cells[:, 0], rc[:, 0], rtol=2e-6, atol=0)
+    np.testing.assert_allclose(cells[:, 1:], rc[:, 1:], rtol=1e-5, atol=1e-6)
+    sim.close()

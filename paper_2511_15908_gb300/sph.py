@@ -467,26 +467,49 @@ class Surrogate:
         self._check(self.L.sph_mlp_get_params(self.m, _ptr(out, ctypes.c_float)))
         return out
 
+    def _enter(self):
+        # the model's stream waits for work already queued on torch's current stream
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+        return cur
+
+    def _leave(self, cur):
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+
     def forward(self, x_dev, y_dev=None):
         """x_dev: CUDA float32 tensor (B, 269); returns a (B, 6) CUDA tensor."""
         import torch
         B = int(x_dev.shape[0])
+        x_dev = x_dev.contiguous()
         if y_dev is None:
             y_dev = torch.empty((B, 6), dtype=torch.float32, device=self.device)
+        cur = self._enter()
         self._check(self.L.sph_mlp_forward(self.m, x_dev.data_ptr(), B, y_dev.data_ptr()))
+        self._leave(cur)
         return y_dev
 
     def gradients(self, x_dev, t_dev):
         g = np.zeros(self.n_params, np.float32)
         loss = np.zeros(1, np.float64)
+        x_dev, t_dev = x_dev.contiguous(), t_dev.contiguous()
+        self._enter()
         self._check(self.L.sph_mlp_gradients(self.m, x_dev.data_ptr(), t_dev.data_ptr(), int(x_dev.shape[0]),
                                              _ptr(g, ctypes.c_float), _ptr(loss, ctypes.c_double)))
         return g, float(loss[0])
 
     def train_step(self, x_dev, t_dev, lr: float, want_loss: bool = False):
         loss = np.zeros(1, np.float64) if want_loss else None
+        x_dev, t_dev = x_dev.contiguous(), t_dev.contiguous()
+        cur = self._enter()
         self._check(self.L.sph_mlp_train_step(self.m, x_dev.data_ptr(), t_dev.data_ptr(), int(x_dev.shape[0]),
                                               float(lr), _ptr(loss, ctypes.c_double)))
+        # the inputs must stay alive until the model's stream has consumed them
+        x_dev.record_stream(self.stream)
+        t_dev.record_stream(self.stream)
+        self._leave(cur)
         return float(loss[0]) if want_loss else None
 
     def sync(self):

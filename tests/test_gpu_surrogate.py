@@ -109,3 +109,33 @@ def test_descriptor_matches_oracle(sph):
     np.testing.assert_allclose(cells[:, 0], rc[:, 0], rtol=2e-6, atol=0)
     np.testing.assert_allclose(cells[:, 1:], rc[:, 1:], rtol=1e-5, atol=1e-6)
     sim.close()
+
+
+def test_surrogate_beats_the_update_cycle_hold_at_1khz(sph):
+    """What the trained network gains over the method without it: at 1 kHz haptic ticks on
+    held-out substeps of a stirring run, the surrogate (exact wrench of the last ~60 Hz
+    update cycle + learned correction) against holding that exact wrench, and against the
+    paper's rolling average over 20 update cycles."""
+    from paper_2511_15908_gb300 import surrogate
+    n, n_train = 20000, 15000
+    sc = scenes.stirring_tank(seed=4, n_fluid=40_000, cols=(50, 50), tank=(0.4, 0.4, 0.3), n_substeps=n,
+                              paddle=(0.02, 0.1, 0.2))
+    sim = sph.Simulation(sc)
+    desc, wr = surrogate.log_run(sim, n)
+    dt = float(np.float32(sc.params["dt"]))
+    cycle, tick = 33, 2                     # dt 5e-4 s: 16.5 ms update cycle, 1 ms tick
+    x = surrogate.lagged_inputs(desc, cycle, dt)
+    y = surrogate.residual_targets(wr, cycle)
+    model = sph.Surrogate(max_batch=2048)
+    losses = surrogate.fit(model, x[:n_train], y[:n_train], steps=800, batch=1024, lr=1e-3)
+    assert losses[-1][1] < losses[0][1]
+    ev = surrogate.haptic_errors(desc[n_train:], wr[n_train:], model, cycle, tick, dt)
+    print("haptic errors:", ev)
+    assert ev["surrogate"]["force"] < ev["hold"]["force"]
+    assert ev["surrogate"]["force"] < ev["rolling"]["force"]
+    assert ev["surrogate"]["force"] <= 0.05          # the form's 5 % target
+    lat = surrogate.inference_latency_us(sim, model)
+    print("latency per tick us:", lat)
+    assert lat < 1000.0
+    sim.close()
+    model.close()

@@ -33,7 +33,8 @@ METRIC = "particle-steps/s at 1M particles (fluid particles x substeps / s)"
 UNIT = "particle-steps/s"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_2511_15908_gb300", "csrc", "sph_kernels.cu")
+KERNEL_SRC = [os.path.join(ROOT, "paper_2511_15908_gb300", "csrc", f)
+              for f in ("sph_device.cuh", "sph_kernels.cu", "sph_internal.cuh")]
 
 # Algorithmic cost model (documented in the design notes):
 BYTES_PER_PARTICLE_STEP = 168          # HBM bytes of one substep per particle
@@ -52,8 +53,11 @@ def _peaks():
 
 
 def _kernel_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for p in KERNEL_SRC:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def _traffic(kernel):
@@ -258,6 +262,59 @@ def batched_form(args, flush_l2_factory):
     return out
 
 
+def surrogate_form(args):
+    """Form (4): the BF16 tcgen05 MLP surrogate at 1 kHz haptic ticks on the stirring tank
+    (250k fluid), trained on the GPU from logged (descriptor, wrench) pairs: (a) pairs logged
+    from the stirring tank itself (time split), (b) the dam-break pairs of the cube grab
+    (transfer).  Errors are against the exact FP64 coupling reduction at every tick."""
+    import torch
+    from paper_2511_15908_gb300 import scenes, sph, surrogate
+    out = {}
+    n, n_train = args.sur_substeps, int(0.75 * args.sur_substeps)
+    sc = scenes.stirring_tank(seed=0, n_substeps=n)
+    dt = float(np.float32(sc.params["dt"]))
+    cycle, tick = 33, 2
+    sim = sph.Simulation(sc)
+    t0 = time.perf_counter()
+    desc, wr = surrogate.log_run(sim, n)
+    t_log = time.perf_counter() - t0
+    x, y = surrogate.lagged_inputs(desc, cycle, dt), surrogate.residual_targets(wr, cycle)
+    model = sph.Surrogate(max_batch=2048)
+    t0 = time.perf_counter()
+    steps = 800
+    losses = surrogate.fit(model, x[:n_train], y[:n_train], steps=steps, batch=1024, lr=1e-3)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    ev = surrogate.haptic_errors(desc[n_train:], wr[n_train:], model, cycle, tick, dt)
+    lat = surrogate.inference_latency_us(sim, model)
+    out["stirring_logged"] = {"train_pairs": n_train, "eval_ticks": ev["ticks"], "errors": ev,
+                              "train_steps": steps, "train_s": t_fit, "log_s": t_log,
+                              "first_last_loss": [losses[0][1], losses[-1][1]]}
+    out["tick_latency_us"] = lat
+    # (b) dam-break pairs (cube grabbed on a seeded random walk): held-out dam-break substeps
+    # (in distribution) and the stirring tank above (transfer to another body and spacing)
+    nd = args.sur_dam_substeps
+    nd_train = int(0.75 * nd)
+    sd = scenes.dam_break(seed=1, grab=True, n_substeps=nd, cube_pos=(0.4, 0.4, 0.2))
+    sim_d = sph.Simulation(sd, max_path=nd + 16)
+    d_d, w_d = surrogate.log_run(sim_d, nd)
+    dtd = float(np.float32(sd.params["dt"]))
+    cyc_d = 17                                   # dt 1e-3 s: ~60 Hz update cycle
+    model_d = sph.Surrogate(max_batch=2048)
+    xd_, yd_ = surrogate.lagged_inputs(d_d, cyc_d, dtd), surrogate.residual_targets(w_d, cyc_d)
+    surrogate.fit(model_d, xd_[:nd_train], yd_[:nd_train], steps=1500, batch=1024, lr=1e-3)
+    ev_in = surrogate.haptic_errors(d_d[nd_train:], w_d[nd_train:], model_d, cyc_d, 1, dtd)
+    ev_tr = surrogate.haptic_errors(desc[n_train:], wr[n_train:], model_d, cycle, tick, dt)
+    out["dam_break_trained"] = {"train_pairs": nd_train, "held_out_dam_break_1khz": ev_in,
+                                "transfer_to_stirring_1khz": ev_tr}
+    out["target_rel_force_err"] = 0.05
+    for m_ in (model, model_d):
+        m_.close()
+    sim.close()
+    sim_d.close()
+    return out
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -394,6 +451,7 @@ def run_ours(args):
                     flush.fill_(1)
             return f
         forms["batched"] = batched_form(args, factory)
+        forms["surrogate"] = surrogate_form(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -437,6 +495,8 @@ def main():
     ap.add_argument("--workload", default="coupled", choices=["coupled", "stirring", "dam_break"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / surrogate forms")
+    ap.add_argument("--sur-substeps", type=int, default=32000)
+    ap.add_argument("--sur-dam-substeps", type=int, default=40000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

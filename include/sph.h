@@ -347,6 +347,36 @@ const char *sph_batch_last_error(const sph_batch *b);
 /* Free the host-side batch and its graphs (the workspace and the scenes stay). */
 void sph_batch_destroy(sph_batch *b);
 
+/*
+ * Allocation-free spatial hash.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- an engine plugin whose device memory is
+ * owned by the host engine's allocator, a real-time haptic loop that must not allocate
+ * after start-up, or code running while a stream is captured into a CUDA graph (where
+ * cudaMalloc is not permitted).  It computes what a substep's spatial hash computes (cell
+ * key of each sorted slot, stable counting-sort order, cell ranges) for n particles given
+ * as DEVICE float4 (x, y, z, any) records (16-byte aligned), on the grid that sph_create
+ * builds from p (domain_lo/hi, cell; the other fields are ignored).
+ *   d_keys[n]          cell key of each sorted slot
+ *   d_order[n]         input index of the particle in each sorted slot (ties keep input
+ *                      order)
+ *   d_cell_start[C+1]  first sorted slot of each cell, C = grid cells
+ * It allocates nothing: the per-cell counters and per-particle ranks live in one fixed
+ * file-scope device array of about 4.2 MB, reserved on every GPU that loads this library
+ * until the process exits.  Limits: n <= SPH_NOALLOC_MAX_PARTICLES and C <=
+ * SPH_NOALLOC_MAX_CELLS, else SPH_ERR_CAPACITY (nothing is launched).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares the array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race -- serialise
+ * them.  Enqueued on cuda_stream; particles outside the domain are clamped into the border
+ * cells as in sph_step (not reported here).  Errors: SPH_ERR_ARG, SPH_ERR_CAPACITY,
+ * SPH_ERR_CUDA.
+ */
+#define SPH_NOALLOC_MAX_PARTICLES (1 << 18)
+#define SPH_NOALLOC_MAX_CELLS (1 << 18)
+sph_status sph_cell_sort_noalloc(const sph_params *p, const float *d_xyzm, int32_t n,
+                                 uint32_t *d_keys, int32_t *d_order, uint32_t *d_cell_start,
+                                 void *cuda_stream);
+
 /* Wait for the stream and report latched device errors. */
 sph_status sph_sync(sph_handle *h);
 

@@ -33,7 +33,7 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_batch_destroy", "sph_batch_test_barrier", "sph_get_descriptor",
            "sph_mlp_param_count", "sph_mlp_workspace_bytes", "sph_mlp_create", "sph_mlp_set_params",
            "sph_mlp_get_params", "sph_mlp_forward", "sph_mlp_gradients", "sph_mlp_train_step",
-           "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy"]
+           "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -160,6 +160,8 @@ def load(path: str = LIB_PATH):
     L.sph_mlp_last_error.argtypes = [_vp]
     L.sph_mlp_destroy.restype = None
     L.sph_mlp_destroy.argtypes = [_vp]
+    L.sph_cell_sort_noalloc.restype = st
+    L.sph_cell_sort_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
     L.sph_sync.restype = st
     L.sph_sync.argtypes = [_vp]
     L.sph_last_error.restype = ctypes.c_char_p
@@ -525,3 +527,40 @@ class Surrogate:
             self.close()
         except Exception:
             pass
+
+
+NOALLOC_MAX_PARTICLES = 1 << 18
+NOALLOC_MAX_CELLS = 1 << 18
+
+
+def cell_sort_noalloc(params: dict, x_dev, stream=None):
+    """Allocation-free spatial hash of the particles in x_dev (CUDA float32 tensor (n, 4)):
+    returns (keys, order, cell_start) CUDA tensors.  The output tensors are the caller's
+    (allocated here by torch); the library call itself allocates nothing."""
+    import torch
+    L = load()
+    P = make_params(params, 1.0)
+    n = int(x_dev.shape[0])
+    x_dev = x_dev.contiguous()
+    ncell = int(np.prod(grid_dims(params)))
+    keys = torch.empty(max(n, 1), dtype=torch.int32, device=x_dev.device)
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=x_dev.device)
+    cs = torch.empty(ncell + 1, dtype=torch.int32, device=x_dev.device)
+    st = stream if stream is not None else torch.cuda.current_stream(x_dev.device)
+    r = L.sph_cell_sort_noalloc(ctypes.byref(P), x_dev.data_ptr(), n, keys.data_ptr(), order.data_ptr(),
+                                cs.data_ptr(), st.cuda_stream)
+    if r != OK:
+        raise SphError(r, "sph_cell_sort_noalloc failed")
+    return keys[:n], order[:n], cs
+
+
+def grid_dims(params: dict):
+    """Cells per axis of the uniform grid (same FP32 formula as the library)."""
+    cell = np.float32(params["cell"])
+    inv = np.float32(1.0) / cell
+    out = []
+    for a in range(3):
+        o = np.float32(np.float32(params["lo"][a]) - cell)
+        u = np.float32(np.float32(np.float32(params["hi"][a]) - o) * inv)
+        out.append(int(np.floor(u)) + 2)
+    return out

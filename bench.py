@@ -254,7 +254,9 @@ def batched_form(args, flush_l2_factory):
            "speedup_vs_one_by_one": (t_seq / k) / (t_b / args.steps),
            "autotuned": {"blocks_per_sm": bps, "tiles_per_fetch": chunk, "sms": info["sms"]},
            "grab_wrench_rel_diff_vs_single_scene": werr,
-           "gpu_launches_per_step": 1}
+           "gpu_launches_per_step": 8 if info["blocks_per_sm"] == 0 else 1,
+           "launch_structure": "one kernel per phase over all scenes" if info["blocks_per_sm"] == 0
+                               else "one persistent cooperative kernel"}
     for x in sims + solo + ref + chk:
         x.close()
     batch.close()

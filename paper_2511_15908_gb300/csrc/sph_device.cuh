@@ -29,9 +29,6 @@ namespace sphgb {
 constexpr int kTile = 256;     // threads per block = particles per tile
 
 
-#ifndef SPH_FORCE_MINB
-#define SPH_FORCE_MINB 4      // resident 256-thread blocks per SM the force pass is built for
-#endif
 
 constexpr int KIND_STATIC = 1, KIND_RIGID = 2, KIND_SOFT = 3;
 constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u;
@@ -340,6 +337,13 @@ __device__ __forceinline__ void rank_gather_item(const SimConst &c, int blk)
 // q low), the shape is evaluated as (2-q)^3 - 4(1-q)^3 (no cancellation near q = 1), the
 // sum is compensated (Kahan), and rho - rho0 is formed with an FMA against alpha/6 kept
 // as a float pair.
+//
+// Two phases.  The first walks the 9 x-runs with the cheap distance test only and builds
+// each run's neighbour bitmask (kept for the force pass); the second evaluates the kernel
+// on the set bits.  Splitting keeps the candidate loop short and branch-free, so more
+// loads are in flight, and the kernel arithmetic runs only on actual neighbours.  Runs
+// longer than 32 candidates (rare: dense clusters) are summed in the first phase and
+// flagged in novf so the force pass rescans them.
 __device__ __forceinline__ void density_item(const SimConst &c, int blk)
 {
     int p = blk * kTile + threadIdx.x;
@@ -348,37 +352,74 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     float S = 0.0f, C = 0.0f;
     int cnt = 0;
     uint32_t bad = 0, ovf = 0;
-    for_each_run(c, xi, bad, [&](int run, int s0, int e0) {
-        uint32_t m = 0;
-#pragma unroll 2
-        for (int q = s0; q < e0; ++q) {
-            float4 xj = __ldg(c.xA + q);
-            float dx, dy, dz;
-            float r2 = dist2(xi, xj, dx, dy, dz);
-            if (r2 < c.R2) {
-                float r = 0.0f;
-                if (r2 > 0.0f) {              // sqrt: rsqrt + one Newton step (~1 ulp)
-                    float rs = rsqrtf(r2);
-                    r = r2 * rs;
-                    r = __fmaf_rn(0.5f * rs, __fmaf_rn(-r, r, r2), r);
+    auto add = [&](float4 xj, float r2) {
+        // sqrt: rsqrt + one Newton step (~1 ulp); r2 = 0 (the particle itself) gives r = 0
+        float rs = rsqrtf(fmaxf(r2, 1e-30f));
+        float r = r2 * rs;
+        r = __fmaf_rn(0.5f * rs, __fmaf_rn(-r, r, r2), r);
+        // q = r / h with a single rounding of r * (1/h)_hi + r * (1/h)_lo
+        float s = __fmaf_rn(r, c.invh_hi, r * c.invh_lo);
+        // 6 w(q) = (2-q)^3 - 4 (1-q)^3 for q < 1, (2-q)^3 for 1 <= q < 2
+        float t = 2.0f - s, u1 = 1.0f - s;
+        float w6 = t * t * t;
+        if (s < 1.0f) w6 = __fmaf_rn(-4.0f * u1, u1 * u1, w6);
+        float y = __fsub_rn(fabsf(xj.w) * w6, C);
+        float u = __fadd_rn(S, y);
+        C = __fsub_rn(__fsub_rn(u, S), y);
+        S = u;
+        ++cnt;
+    };
+    int cx, cy, cz;
+    uint32_t dummy = 0;
+    cell_of(c, xi, cx, cy, cz, dummy);
+    const int x0 = cx > 0 ? cx - 1 : 0;
+    const int x1 = cx < c.nx - 1 ? cx + 1 : c.nx - 1;
+    uint32_t m[kRuns];      // per-run neighbour bits (bit i: candidate start + i)
+    int st[kRuns];          // per-run first candidate
+#pragma unroll 1
+    for (int r = 0; r < kRuns; ++r) {
+        const int z = cz + r / 3 - 1, y = cy + r % 3 - 1;
+        uint32_t mm = 0u;
+        int s = 0;
+        if (z >= 0 && z < c.nz && y >= 0 && y < c.ny) {
+            const int base = (z * c.ny + y) * c.nx;
+            s = (int)__ldg(c.cell_start + base + x0);
+            int e = (int)__ldg(c.cell_start + base + x1 + 1);
+            if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
+            if (e - s <= 32) {
+                uint32_t bit = 1u;
+#pragma unroll 4
+                for (int q = s; q < e; ++q) {
+                    float4 xj = __ldg(c.xA + q);
+                    float dx, dy, dz;
+                    if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
+                    bit <<= 1;
                 }
-                // q = r / h with a single rounding of r * (1/h)_hi + r * (1/h)_lo
-                float s = __fmaf_rn(r, c.invh_hi, r * c.invh_lo);
-                // 6 w(q) = (2-q)^3 - 4 (1-q)^3 for q < 1, (2-q)^3 for 1 <= q < 2
-                float t = 2.0f - s, u1 = 1.0f - s;
-                float w6 = t * t * t;
-                if (s < 1.0f) w6 = __fmaf_rn(-4.0f * u1, u1 * u1, w6);
-                float y = __fsub_rn(fabsf(xj.w) * w6, C);
-                float u = __fadd_rn(S, y);
-                C = __fsub_rn(__fsub_rn(u, S), y);
-                S = u;
-                ++cnt;
-                m |= 1u << ((q - s0) & 31);
+            } else {
+                ovf |= 1u << r;
+                for (int q = s; q < e; ++q) {
+                    float4 xj = __ldg(c.xA + q);
+                    float dx, dy, dz;
+                    float r2 = dist2(xi, xj, dx, dy, dz);
+                    if (r2 < c.R2) add(xj, r2);
+                }
             }
         }
-        if (e0 - s0 > 32) ovf |= 1u << run;
-        c.nmask[(size_t)run * c.n + p] = m;
-    });
+        m[r] = mm;
+        st[r] = s;
+        c.nmask[(size_t)r * c.n + p] = mm;
+    }
+    int r = 0;
+    uint32_t mm = m[0];
+    for (;;) {
+        while (mm == 0u && r < kRuns - 1) mm = m[++r];
+        if (mm == 0u) break;
+        const int q = st[r] + __ffs(mm) - 1;
+        mm &= mm - 1u;
+        float4 xj = __ldg(c.xA + q);
+        float dx, dy, dz;
+        add(xj, dist2(xi, xj, dx, dy, dz));
+    }
     c.novf[p] = ovf;
     // rho - rho0 = alpha6 * (S - C) - rho0 with alpha6 = hi + lo
     float drho = __fmaf_rn(c.alpha6_hi, S, -c.rho0) +
@@ -445,25 +486,33 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
             };
             const uint32_t ovf = c.novf[p];
             for_each_run(c, xi, bad, [&](int run, int s0, int e0) {
-                if (ovf & (1u << run)) {           // long run: test every candidate again
-                    for (int q = s0; q < e0; ++q) {
-                        float4 xj = __ldg(c.xA + q);
-                        float dx, dy, dz;
-                        float r2 = dist2(xi, xj, dx, dy, dz);
-                        if (r2 < c.R2 && q != p) pair(q, xj, dx, dy, dz, r2);
+                // neighbours recorded by the density pass; a run longer than 32 candidates
+                // is re-tested 32 candidates at a time (one pair evaluation site)
+                const bool long_run = (ovf >> run) & 1u;
+                uint32_t mm = long_run ? 0u : __ldg(c.nmask + (size_t)run * c.n + p);
+                int base = s0, next = s0;
+                do {
+                    if (long_run) {
+                        base = next;
+                        const int end = min(e0, next + 32);
+                        mm = 0u;
+                        for (int q = next; q < end; ++q) {
+                            float4 xj = __ldg(c.xA + q);
+                            float dx, dy, dz;
+                            mm |= (dist2(xi, xj, dx, dy, dz) < c.R2 ? 1u : 0u) << (q - base);
+                        }
+                        next = end;
                     }
-                } else {                           // neighbours recorded by the density pass
-                    uint32_t m = __ldg(c.nmask + (size_t)run * c.n + p);
-                    while (m) {
-                        int q = s0 + __ffs(m) - 1;
-                        m &= m - 1u;
+                    while (mm) {
+                        const int q = base + __ffs(mm) - 1;
+                        mm &= mm - 1u;
                         if (q == p) continue;
                         float4 xj = __ldg(c.xA + q);
                         float dx, dy, dz;
                         float r2 = dist2(xi, xj, dx, dy, dz);
                         pair(q, xj, dx, dy, dz, r2);
                     }
-                }
+                } while (long_run && next < e0);
             });
             ax *= c.alpha_g;
             ay *= c.alpha_g;

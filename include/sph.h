@@ -74,9 +74,10 @@ enum { SPH_BODY_STATIC = 1, SPH_BODY_RIGID = 2, SPH_BODY_SOFT = 3 };
  *   g            gravity, the external force per unit mass (Alg. 1).
  *   dt           substep of the semi-implicit Euler update (Sec. 3.1, Eq. euler).
  *   domain_lo/hi box covered by the uniform grid; one margin cell is added per side.
- *   cell         grid cell edge; must be >= 2h (the 27-cell neighbourhood covers the
- *                support).  A cell slightly above 2h (e.g. 2h * 1.001) guarantees that
- *                FP32 rounding of cell coordinates never hides a neighbour.
+ *   cell         grid cell edge; must be >= h.  The neighbour search visits, per row of
+ *                cells, only the cells that can hold a point within 2h (plus a rounding
+ *                margin) of the particle, so any cell >= h finds every neighbour; about
+ *                h (e.g. h * 1.001) scans the fewest candidates.
  *   visc_eps     regulariser of the viscous term, r^2 + visc_eps h^2.
  *   spring_zeta  damping ratio of soft-body springs.
  *   fluid_spacing lattice spacing of the fluid; fluid SPH mass = rho0 * spacing^3.
@@ -103,9 +104,14 @@ typedef struct {
  *   max_springs    soft-body springs (each counted once)
  *   max_path       entries of the grab path (sph_set_grab_path) and of the per-substep
  *                  wrench log
+ *   max_neighbours neighbour-list slots per particle (0 = 96), 4 bytes each: the density
+ *                  pass records each particle's interaction partners for the force pass;
+ *                  a particle with more partners is re-searched by the force pass
+ *                  (same result, slower)
  */
 typedef struct {
     int32_t max_particles, max_bodies, max_springs, max_path;
+    int32_t max_neighbours;
 } sph_capacity;
 
 /* Bytes of device workspace a scene with these parameters and capacities needs

@@ -186,7 +186,17 @@ typedef struct {
     const uint32_t *key;       /* sorted keys */
     const uint32_t *cell_start;
     float R2;
+    int span;                  /* grid mode: cells searched on each side of the own cell */
 } orc_nbrs;
+
+/* Two particles closer than R lie at most floor(R / cell) + 1 cells apart along an axis
+ * (the small relative slack absorbs FP32 rounding of the cell coordinates), so the grid
+ * search visits that many cells on each side; the brute-force mode is the definition. */
+static int orc_span(const orc_params *P)
+{
+    double R = 2.0 * (double)P->h;
+    return (int)floor(R / (double)P->cell * (1.0 + 1e-5)) + 1;
+}
 
 /* Calls visit(p, q, ctx) for every q != p with the FP32 predicate true, in a fixed order. */
 typedef void (*orc_visit)(int p, int q, void *ctx);
@@ -203,11 +213,12 @@ static void orc_for_neighbours(const orc_nbrs *N, int p, orc_visit visit, void *
     uint32_t k = N->key[p];
     int cx = (int)(k % (uint32_t)nx), cy = (int)((k / (uint32_t)nx) % (uint32_t)ny);
     int cz = (int)(k / ((uint32_t)nx * (uint32_t)ny));
-    for (int z = cz - 1; z <= cz + 1; ++z) {
+    const int S = N->span;
+    for (int z = cz - S; z <= cz + S; ++z) {
         if (z < 0 || z >= nz) continue;
-        for (int y = cy - 1; y <= cy + 1; ++y) {
+        for (int y = cy - S; y <= cy + S; ++y) {
             if (y < 0 || y >= ny) continue;
-            for (int xx = cx - 1; xx <= cx + 1; ++xx) {
+            for (int xx = cx - S; xx <= cx + S; ++xx) {
                 if (xx < 0 || xx >= nx) continue;
                 uint32_t c = (uint32_t)((z * ny + y) * nx + xx);
                 for (uint32_t q = N->cell_start[c]; q < N->cell_start[c + 1]; ++q)
@@ -418,7 +429,7 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
     }
     if (cell_start_out) memcpy(cell_start_out, cs, sizeof(uint32_t) * ((size_t)ncell + 1));
 
-    orc_nbrs N = { mode, n, { dims[0], dims[1], dims[2] }, xs, ks, cs, orc_support2(P) };
+    orc_nbrs N = { mode, n, { dims[0], dims[1], dims[2] }, xs, ks, cs, orc_support2(P), orc_span(P) };
 
     /* a6: density (Eq. density, self term included) and pressure (Eq. pressure). */
 #pragma omp parallel for schedule(dynamic, 256) if (n > 4096)

@@ -24,8 +24,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t xA, vA, xB, vB, prho, key, rank, perm, cnt, cell_start, tile_sum, slot_of_id, locals,
         spring_row, spring_e, fb, xb, acc_dbg, nnbr, body, path, wrench, wrench_part, wblock,
-        diag_part, diag_part2, nmask, novf, diag, wlog, cyc_log, status, ctr, total;
-    int dims[3], ncell, n_scan_tiles, max_wblocks, max_force_blocks;
+        diag_part, diag_part2, nlist, nlist_n, diag, wlog, cyc_log, status, ctr, total;
+    int dims[3], ncell, n_scan_tiles, max_wblocks, max_force_blocks, nl_cap;
 };
 
 // Grid of the FP32 cell hash: origin lo - cell, n = floor((hi - o) / cell) + 2 per axis.
@@ -42,13 +42,13 @@ void grid_dims(const sph_params &p, int dims[3], float o[3], float &inv)
 bool valid_params(const sph_params *p, const sph_capacity *cap)
 {
     if (!p || !cap) return false;
-    if (!(p->h > 0.0f) || !(p->rho0 > 0.0f) || !(p->dt > 0.0f) || !(p->cell >= 2.0f * p->h))
+    if (!(p->h > 0.0f) || !(p->rho0 > 0.0f) || !(p->dt > 0.0f) || !(p->cell >= p->h))
         return false;
     if (!(p->fluid_spacing > 0.0f) || p->k < 0.0f || p->nu < 0.0f) return false;
     for (int a = 0; a < 3; ++a)
         if (!(p->domain_hi[a] > p->domain_lo[a])) return false;
     if (cap->max_particles < 0 || cap->max_bodies < 0 || cap->max_bodies > kMaxBodies ||
-        cap->max_springs < 0 || cap->max_path < 0)
+        cap->max_springs < 0 || cap->max_path < 0 || cap->max_neighbours < 0)
         return false;
     int dims[3];
     float o[3], inv;
@@ -89,8 +89,9 @@ Layout make_layout(const sph_params &p, const sph_capacity &cap)
     L.wblock = take(16 * (size_t)L.max_wblocks);
     L.diag_part = take(8 * 8 * (size_t)L.max_force_blocks);
     L.diag_part2 = take(8 * 8 * (size_t)std::max(L.max_wblocks, kWrenchMinBlocks));
-    L.nmask = take(4 * (size_t)kRuns * N);
-    L.novf = take(4 * N);
+    L.nl_cap = cap.max_neighbours > 0 ? cap.max_neighbours : kDefaultNeighbours;
+    L.nlist = take(4 * (size_t)L.nl_cap * N);
+    L.nlist_n = take(4 * N);
     L.diag = take(8 * 8);
     L.wlog = take(8 * 6 * (size_t)std::max(cap.max_path, 1));
     L.cyc_log = take(8 * 6 * (size_t)W);
@@ -308,6 +309,16 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     grid_dims(*p, L.dims, c.o, c.inv_cell);
     float R = 2.0f * p->h;
     c.R2 = R * R;
+    c.cell = p->cell;
+    {
+        // The search radius exceeds R by a margin far above the FP32 rounding of the
+        // predicate (relative ~1e-6) and of cell bounds (a few ulp of the coordinates).
+        float M = 0.0f;
+        for (int a = 0; a < 3; ++a)
+            M = std::max(M, std::max(std::fabs(c.o[a]), std::fabs(c.o[a] + (float)L.dims[a] * p->cell)));
+        c.margin = std::max(1e-3f * R, 64.0f * M * 1.1920929e-7f);
+        c.Rs = R + c.margin;
+    }
     c.h = p->h;
     c.inv_h = 1.0f / p->h;
     c.rho0 = p->rho0;
@@ -348,8 +359,9 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     c.wblock = at<int4>(h, L.wblock);
     c.diag_part = at<double>(h, L.diag_part);
     c.diag_part2 = at<double>(h, L.diag_part2);
-    c.nmask = at<uint32_t>(h, L.nmask);
-    c.novf = at<uint32_t>(h, L.novf);
+    c.nlist = at<uint32_t>(h, L.nlist);
+    c.nlist_n = at<int>(h, L.nlist_n);
+    c.nl_cap = L.nl_cap;
     c.diag = at<double>(h, L.diag);
     c.wlog = at<double>(h, L.wlog);
     c.cyc_log = at<double>(h, L.cyc_log);

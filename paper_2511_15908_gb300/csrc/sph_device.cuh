@@ -117,55 +117,76 @@ __device__ __forceinline__ float dist2(float4 xi, float4 xj, float &dx, float &d
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Calls f(q) for every particle q of the 27 cells around x (9 contiguous x-runs).
+// Cell index of coordinate x clamped to [0, n) without reporting (NaN -> 0).
+__device__ __forceinline__ int cell_clamp(float x, float o, float inv, int n)
+{
+    const float f = floorf(__fmul_rn(__fsub_rn(x, o), inv));
+    return f >= 0.0f ? (f < (float)(n - 1) ? (int)f : n - 1) : 0;
+}
+
+// Lower bound of |y - y_j| over the particles y_j whose cell index along this axis is j,
+// where cj is the cell of y: the distance from y to cell j's near face, less the margin.
+__device__ __forceinline__ float cell_gap(float y, int j, int cj, float o, float cell, float margin)
+{
+    if (j == cj) return 0.0f;
+    const float g = j > cj ? __fsub_rn(__fmaf_rn((float)j, cell, o), y)
+                           : __fsub_rn(y, __fmaf_rn((float)(j + 1), cell, o));
+    return fmaxf(g - margin, 0.0f);
+}
+
+// Calls f(s, e) for every row of cells (fixed y and z) that can hold a particle within
+// the search radius Rs of x; [s, e) is the range of sorted slots of the row's cells whose
+// x-extent can reach that far (cells along x are consecutive in the key, so the range is
+// contiguous).  Each row is clipped to the chord of the search sphere at the row's
+// nearest y-z distance, so for a cell near h the candidates fill about 2.5 times the
+// sphere's volume instead of the 6.5 times of a 27-cell block of 2h cells.  Every bound
+// is a lower bound on the true distance and FP32 rounding is monotone, so no particle
+// that passes the FP32 predicate is ever outside the visited cells.
 template <class F>
-__device__ __forceinline__ void for_each_candidate(const SimConst &c, float4 x, uint32_t &bad, F &&f)
+__device__ __forceinline__ void for_each_row(const SimConst &c, float4 x, uint32_t &bad, F &&f)
 {
     int cx, cy, cz;
     uint32_t dummy = 0;
     cell_of(c, x, cx, cy, cz, dummy);
-    const int x0 = cx > 0 ? cx - 1 : 0;
-    const int x1 = cx < c.nx - 1 ? cx + 1 : c.nx - 1;
+    const float Rs = c.Rs, Rs2 = Rs * Rs;
+    const int z0 = cell_clamp(x.z - Rs, c.o[2], c.inv_cell, c.nz);
+    const int z1 = cell_clamp(x.z + Rs, c.o[2], c.inv_cell, c.nz);
+    const int y0 = cell_clamp(x.y - Rs, c.o[1], c.inv_cell, c.ny);
+    const int y1 = cell_clamp(x.y + Rs, c.o[1], c.inv_cell, c.ny);
 #pragma unroll 1
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        if (z < 0 || z >= c.nz) continue;
+    for (int z = z0; z <= z1; ++z) {
+        const float gz = cell_gap(x.z, z, cz, c.o[2], c.cell, c.margin);
+        const float rz2 = Rs2 - gz * gz;
 #pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= c.ny) continue;
-            int base = (z * c.ny + y) * c.nx;
-            int s = (int)__ldg(c.cell_start + base + x0);
-            int e = (int)__ldg(c.cell_start + base + x1 + 1);
+        for (int y = y0; y <= y1; ++y) {
+            const float gy = cell_gap(x.y, y, cy, c.o[1], c.cell, c.margin);
+            const float w2 = rz2 - gy * gy;
+            if (!(w2 >= 0.0f)) continue;
+            const float w = sqrtf(w2) + c.margin;
+            const int xa = cell_clamp(x.x - w, c.o[0], c.inv_cell, c.nx);
+            const int xb = cell_clamp(x.x + w, c.o[0], c.inv_cell, c.nx);
+            const int base = (z * c.ny + y) * c.nx;
+            const int s = (int)__ldg(c.cell_start + base + xa);
+            int e = (int)__ldg(c.cell_start + base + xb + 1);
             if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
-#pragma unroll 2
-            for (int q = s; q < e; ++q) f(q);
+            f(s, e);
         }
     }
 }
 
-// Calls f(r, s, e) for each of the 9 x-runs r = 3 (dz+1) + (dy+1) that lie inside the
-// grid; [s, e) is the run's range of sorted slots (cells x-1 .. x+1 are contiguous).
-template <class F>
-__device__ __forceinline__ void for_each_run(const SimConst &c, float4 x, uint32_t &bad, F &&f)
+// Body kind of a particle id and the id range whose pair forces it ignores: a static or
+// rigid particle does not interact with the particles of its own body (their relative
+// positions are fixed); fluid and soft particles ignore nobody (range empty).
+__device__ __forceinline__ void pair_scope(const SimConst &c, int id, int &kind, int &excl_lo,
+                                           int &excl_n)
 {
-    int cx, cy, cz;
-    uint32_t dummy = 0;
-    cell_of(c, x, cx, cy, cz, dummy);
-    const int x0 = cx > 0 ? cx - 1 : 0;
-    const int x1 = cx < c.nx - 1 ? cx + 1 : c.nx - 1;
-#pragma unroll 1
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-#pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (z < 0 || z >= c.nz || y < 0 || y >= c.ny) continue;
-            int base = (z * c.ny + y) * c.nx;
-            int s = (int)__ldg(c.cell_start + base + x0);
-            int e = (int)__ldg(c.cell_start + base + x1 + 1);
-            if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
-            f(3 * (dz + 1) + (dy + 1), s, e);
+    kind = 0; excl_lo = 0; excl_n = 0;
+    if (id >= c.nf) {
+        const int b = body_of(c, id);
+        kind = c.body_kind[b];
+        if (kind != KIND_SOFT) {
+            excl_lo = b == 0 ? c.nf : c.body_end[b - 1];
+            excl_n = c.body_end[b] - excl_lo;
         }
     }
 }
@@ -338,20 +359,24 @@ __device__ __forceinline__ void rank_gather_item(const SimConst &c, int blk)
 // sum is compensated (Kahan), and rho - rho0 is formed with an FMA against alpha/6 kept
 // as a float pair.
 //
-// Two phases.  The first walks the 9 x-runs with the cheap distance test only and builds
-// each run's neighbour bitmask (kept for the force pass); the second evaluates the kernel
-// on the set bits.  Splitting keeps the candidate loop short and branch-free, so more
-// loads are in flight, and the kernel arithmetic runs only on actual neighbours.  Runs
-// longer than 32 candidates (rare: dense clusters) are summed in the first phase and
-// flagged in novf so the force pass rescans them.
+// Each row of candidates is taken 32 at a time in two phases: a branch-free distance test
+// that sets one bit per neighbour, then the kernel on the set bits.  The pass also records
+// the particle's interaction partners (neighbours other than itself and, for a static or
+// rigid particle, other than its own body's particles) in the slot-major neighbour list
+// the force pass reads.  Static particles take no force, so they record nothing unless
+// the debug record is on.
 __device__ __forceinline__ void density_item(const SimConst &c, int blk)
 {
-    int p = blk * kTile + threadIdx.x;
+    const int p = blk * kTile + threadIdx.x;
     if (p >= c.n) return;
     const float4 xi = c.xA[p];
     float S = 0.0f, C = 0.0f;
-    int cnt = 0;
-    uint32_t bad = 0, ovf = 0;
+    int cnt = 0, nl = 0;
+    uint32_t bad = 0;
+    int kind = 0, excl_lo = 0, excl_n = 0;
+    if (xi.w < 0.0f) pair_scope(c, __float_as_int(c.vA[p].w), kind, excl_lo, excl_n);
+    const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
+    const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
     auto add = [&](float4 xj, float r2) {
         // sqrt: rsqrt + one Newton step (~1 ulp); r2 = 0 (the particle itself) gives r = 0
         float rs = rsqrtf(fmaxf(r2, 1e-30f));
@@ -369,58 +394,34 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
         S = u;
         ++cnt;
     };
-    int cx, cy, cz;
-    uint32_t dummy = 0;
-    cell_of(c, xi, cx, cy, cz, dummy);
-    const int x0 = cx > 0 ? cx - 1 : 0;
-    const int x1 = cx < c.nx - 1 ? cx + 1 : c.nx - 1;
-    uint32_t m[kRuns];      // per-run neighbour bits (bit i: candidate start + i)
-    int st[kRuns];          // per-run first candidate
+    for_each_row(c, xi, bad, [&](int s0, int e0) {
 #pragma unroll 1
-    for (int r = 0; r < kRuns; ++r) {
-        const int z = cz + r / 3 - 1, y = cy + r % 3 - 1;
-        uint32_t mm = 0u;
-        int s = 0;
-        if (z >= 0 && z < c.nz && y >= 0 && y < c.ny) {
-            const int base = (z * c.ny + y) * c.nx;
-            s = (int)__ldg(c.cell_start + base + x0);
-            int e = (int)__ldg(c.cell_start + base + x1 + 1);
-            if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
-            if (e - s <= 32) {
-                uint32_t bit = 1u;
+        for (int b = s0; b < e0; b += 32) {
+            const int end = min(e0, b + 32);
+            uint32_t mm = 0u, bit = 1u;
 #pragma unroll 4
-                for (int q = s; q < e; ++q) {
-                    float4 xj = __ldg(c.xA + q);
-                    float dx, dy, dz;
-                    if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
-                    bit <<= 1;
-                }
-            } else {
-                ovf |= 1u << r;
-                for (int q = s; q < e; ++q) {
-                    float4 xj = __ldg(c.xA + q);
-                    float dx, dy, dz;
-                    float r2 = dist2(xi, xj, dx, dy, dz);
-                    if (r2 < c.R2) add(xj, r2);
-                }
+            for (int q = b; q < end; ++q) {
+                const float4 xj = __ldg(c.xA + q);
+                float dx, dy, dz;
+                if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
+                bit <<= 1;
+            }
+            while (mm) {
+                const int q = b + __ffs(mm) - 1;
+                mm &= mm - 1u;
+                const float4 xj = __ldg(c.xA + q);
+                float dx, dy, dz;
+                add(xj, dist2(xi, xj, dx, dy, dz));
+                if (q == p || !keep_list) continue;
+                if (excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) <
+                                  (unsigned)excl_n)
+                    continue;
+                if (nl < c.nl_cap) c.nlist[(size_t)nl * c.n + p] = (uint32_t)q;
+                ++nl;
             }
         }
-        m[r] = mm;
-        st[r] = s;
-        c.nmask[(size_t)r * c.n + p] = mm;
-    }
-    int r = 0;
-    uint32_t mm = m[0];
-    for (;;) {
-        while (mm == 0u && r < kRuns - 1) mm = m[++r];
-        if (mm == 0u) break;
-        const int q = st[r] + __ffs(mm) - 1;
-        mm &= mm - 1u;
-        float4 xj = __ldg(c.xA + q);
-        float dx, dy, dz;
-        add(xj, dist2(xi, xj, dx, dy, dz));
-    }
-    c.novf[p] = ovf;
+    });
+    c.nlist_n[p] = nl;
     // rho - rho0 = alpha6 * (S - C) - rho0 with alpha6 = hi + lo
     float drho = __fmaf_rn(c.alpha6_hi, S, -c.rho0) +
                  __fmaf_rn(c.alpha6_lo, S, -c.alpha6_hi * C);
@@ -449,15 +450,8 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
         const float2 pi = c.prho[p];
         const int id = __float_as_int(vi.w);
         const float mi = fabsf(xi.w);
-        int kind = 0, excl_lo = 0, excl_n = 0, b = -1;
-        if (id >= c.nf) {
-            b = body_of(c, id);
-            kind = c.body_kind[b];
-            if (kind != KIND_SOFT) {
-                excl_lo = b == 0 ? c.nf : c.body_end[b - 1];
-                excl_n = c.body_end[b] - excl_lo;
-            }
-        }
+        int kind, excl_lo, excl_n;
+        pair_scope(c, id, kind, excl_lo, excl_n);
         const bool skip = (kind == KIND_STATIC) && !(c.flags & FLAG_RECORD);
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
         if (!skip) {
@@ -484,36 +478,29 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
                 ay -= coef * dy;
                 az -= coef * dz;
             };
-            const uint32_t ovf = c.novf[p];
-            for_each_run(c, xi, bad, [&](int run, int s0, int e0) {
-                // neighbours recorded by the density pass; a run longer than 32 candidates
-                // is re-tested 32 candidates at a time (one pair evaluation site)
-                const bool long_run = (ovf >> run) & 1u;
-                uint32_t mm = long_run ? 0u : __ldg(c.nmask + (size_t)run * c.n + p);
-                int base = s0, next = s0;
-                do {
-                    if (long_run) {
-                        base = next;
-                        const int end = min(e0, next + 32);
-                        mm = 0u;
-                        for (int q = next; q < end; ++q) {
-                            float4 xj = __ldg(c.xA + q);
-                            float dx, dy, dz;
-                            mm |= (dist2(xi, xj, dx, dy, dz) < c.R2 ? 1u : 0u) << (q - base);
-                        }
-                        next = end;
-                    }
-                    while (mm) {
-                        const int q = base + __ffs(mm) - 1;
-                        mm &= mm - 1u;
+            const int nl = __ldg(c.nlist_n + p);
+            if (nl <= c.nl_cap) {
+                // the partners the density pass recorded (independent index loads)
+#pragma unroll 2
+                for (int k = 0; k < nl; ++k) {
+                    const int q = (int)__ldg(c.nlist + (size_t)k * c.n + p);
+                    const float4 xj = __ldg(c.xA + q);
+                    float dx, dy, dz;
+                    const float r2 = dist2(xi, xj, dx, dy, dz);
+                    pair(q, xj, dx, dy, dz, r2);
+                }
+            } else {
+                // more partners than list slots: search again
+                for_each_row(c, xi, bad, [&](int s0, int e0) {
+                    for (int q = s0; q < e0; ++q) {
                         if (q == p) continue;
-                        float4 xj = __ldg(c.xA + q);
+                        const float4 xj = __ldg(c.xA + q);
                         float dx, dy, dz;
-                        float r2 = dist2(xi, xj, dx, dy, dz);
-                        pair(q, xj, dx, dy, dz, r2);
+                        const float r2 = dist2(xi, xj, dx, dy, dz);
+                        if (r2 < c.R2) pair(q, xj, dx, dy, dz, r2);
                     }
-                } while (long_run && next < e0);
-            });
+                });
+            }
             ax *= c.alpha_g;
             ay *= c.alpha_g;
             az *= c.alpha_g;

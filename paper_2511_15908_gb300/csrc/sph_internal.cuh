@@ -12,13 +12,14 @@
 namespace sphgb {
 
 constexpr int kMaxBodies = 64;
-constexpr int kMaxCellRun = 1536;   // particles scanned per x-run of 3 cells before the
+constexpr int kMaxCellRun = 1536;   // particles scanned per x-run of cells before the
                                     // status word reports SPH_ERR_CAPACITY
 constexpr int kMaxCell = 512;       // particles per cell for the deterministic rank
 constexpr int kScanTile = 2048;     // cells per scan block (256 threads x 8)
 constexpr int kReduceChunk = 256;   // body particles per wrench-reduction block
 constexpr int kWrenchMinBlocks = 128; // the FP64 reduction is spread over at least this many
-constexpr int kRuns = 9;            // x-runs of 3 cells covering the 27-cell neighbourhood
+constexpr int kDefaultNeighbours = 96; // neighbour-list slots per particle when the
+                                       // capacity leaves it 0
 
 // status word bits (mirrors sph_status codes as bit positions)
 enum : uint32_t {
@@ -42,8 +43,10 @@ struct DevBody {
 struct __align__(16) SimConst {
     int n, nf, nb, n_body_particles;
     int nx, ny, nz, ncell;
-    float o[3], inv_cell;
+    float o[3], inv_cell, cell;
     float R2, h, inv_h;
+    float Rs, margin;          // search radius R + margin; margin covers FP32 rounding of
+                               // cell bounds and of the neighbour predicate
     float rho0, k, nu20;       // nu20 = 2 (d + 2) nu * 2 with d = 3 (the 2 from rho_bar)
     float eps_h2;
     float alpha6_hi, alpha6_lo; // alpha / 6 = 1 / (4 pi h^3) as an unevaluated float pair
@@ -57,6 +60,7 @@ struct __align__(16) SimConst {
     int n_wblocks;
     int n_wgrid;               // wrench kernel grid = max(n_wblocks, kWrenchMinBlocks)
     int smooth_window;
+    int nl_cap;                // neighbour-list slots per particle
     int body_end[kMaxBodies];  // exclusive id end of each body (ids ascending)
     int body_kind[kMaxBodies];
     int wfirst[kMaxBodies];    // first reduction block of each body
@@ -79,8 +83,9 @@ struct __align__(16) SimConst {
     int4 *wblock;              // (body, l0, l1, 0) per reduction block
     double *diag_part;         // n_force_blocks x 8
     double *diag_part2;        // wrench grid x 8 (second level)
-    uint32_t *nmask;           // kRuns x n: neighbour bits of each run (density -> force)
-    uint32_t *novf;            // per particle: runs longer than 32 candidates (re-tested)
+    uint32_t *nlist;           // nl_cap x n, slot-major: neighbours kept by the density
+                               // pass for the force pass (nlist[k * n + p], k < nlist_n[p])
+    int *nlist_n;              // per particle: neighbours found (> nl_cap: force rescans)
     double *diag;              // 8
     double *wlog;              // max_path x 6
     double *cyc_log;           // smooth_window x 6

@@ -20,9 +20,9 @@ Scene recipes (all lengths in metres, z is up, gravity -9.81 along z):
 
 Smoothing length h equals the fluid spacing, so the kernel support 2h is twice the
 spacing; the pressure constant is k = c^2 with c = 0.4 h / dt (an acoustic CFL of 0.4);
-kinematic viscosity 1e-3 m^2/s.  The grid cell edge is the support radius enlarged by
-0.1 % so that FP32 rounding of cell coordinates can never separate two particles
-closer than the support radius by more than one cell.
+kinematic viscosity 1e-3 m^2/s.  The grid cell edge is h enlarged by 0.1 % (half the
+support radius): the neighbour search clips each row of cells to the support sphere, and
+cells near h leave the fewest candidates to test (any cell >= h is valid).
 """
 from __future__ import annotations
 
@@ -81,13 +81,13 @@ class Scene:
 
 
 def make_params(spacing, dt, lo, hi, *, rho0=1000.0, nu=1e-3, flags=FLAG_CLAMP_PRESSURE,
-                cfl=0.4, smooth_window=20):
+                cfl=0.4, smooth_window=20, cell_over_h=1.001):
     h = float(spacing)
     c = cfl * h / dt
     return dict(h=h, rho0=float(rho0), k=float(c * c), nu=float(nu),
                 g=(0.0, 0.0, -9.81), dt=float(dt),
                 lo=tuple(float(a) for a in lo), hi=tuple(float(a) for a in hi),
-                cell=float(np.float32(2.0 * h * 1.001)), flags=int(flags),
+                cell=float(np.float32(cell_over_h * h)), flags=int(flags),
                 visc_eps=0.01, spring_zeta=0.1, smooth_window=int(smooth_window))
 
 

@@ -55,7 +55,8 @@ class Params(ctypes.Structure):
 
 class Capacity(ctypes.Structure):
     _fields_ = [("max_particles", ctypes.c_int32), ("max_bodies", ctypes.c_int32),
-                ("max_springs", ctypes.c_int32), ("max_path", ctypes.c_int32)]
+                ("max_springs", ctypes.c_int32), ("max_path", ctypes.c_int32),
+                ("max_neighbours", ctypes.c_int32)]
 
 
 _lib = None
@@ -197,7 +198,7 @@ class Simulation:
     """One scene on one GPU behind the C ABI.  The workspace is a torch CUDA tensor."""
 
     def __init__(self, scene: _scenes.Scene, flags: Optional[int] = None, max_path: Optional[int] = None,
-                 device: int = 0, stream=None):
+                 device: int = 0, stream=None, max_neighbours: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the SPH library needs a CUDA device")
@@ -208,7 +209,8 @@ class Simulation:
         n_springs = sum(0 if b.springs is None else int(b.springs.shape[0]) for b in scene.bodies)
         traj_n = 0 if scene.trajectory is None else int(scene.trajectory.shape[0])
         self.cap = Capacity(scene.n_total, max(1, len(scene.bodies)), n_springs,
-                            max_path if max_path is not None else max(traj_n, 4096))
+                            max_path if max_path is not None else max(traj_n, 4096),
+                            int(max_neighbours))
         nbytes = self.L.sph_workspace_bytes(ctypes.byref(self.params), ctypes.byref(self.cap))
         if nbytes == 0:
             raise SphError(ERR_ARG, "invalid parameters or capacities")

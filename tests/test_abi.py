@@ -42,7 +42,7 @@ def test_workspace_size_and_argument_checks(lib):
     n = L.sph_workspace_bytes(ctypes.byref(P), ctypes.byref(cap))
     assert n > 160 * sc.n_total
     bad = sph.make_params(sc.params, sc.fluid_spacing)
-    bad.cell = 0.5 * bad.h          # cell smaller than the support radius
+    bad.cell = 0.5 * bad.h          # cell below h
     assert L.sph_workspace_bytes(ctypes.byref(bad), ctypes.byref(cap)) == 0
     cap_bad = sph.Capacity(sc.n_total, 65, 0, 100)
     assert L.sph_workspace_bytes(ctypes.byref(P), ctypes.byref(cap_bad)) == 0

@@ -52,10 +52,10 @@ def _kinds(sc):
     return kinds
 
 
-def check_one_substep(sph, sc, mode, record=True):
+def check_one_substep(sph, sc, mode, record=True, max_neighbours=0):
     """Run one substep on the GPU and in the oracle; assert the parity bar."""
     flags = sc.params["flags"] | (sph.FLAG_RECORD if record else 0)
-    sim = sph.Simulation(sc, flags=flags)
+    sim = sph.Simulation(sc, flags=flags, max_neighbours=max_neighbours)
     n = sc.n_total
     v0 = None
     if not record:
@@ -167,6 +167,32 @@ def test_stirring_tank_full_size_bench_config(sph):
 def test_coupled_full_size_bench_config(sph):
     sc = scenes.with_velocity_noise(scenes.coupled(seed=0, n_substeps=10), seed=6, sigma=0.2)
     check_one_substep(sph, sc, mode=1, record=False)
+
+
+@pytest.mark.parametrize("cell_over_h", [1.0, 1.37, 2.002])
+def test_cell_edges_from_h_to_2h(sph, cell_over_h):
+    # the clipped row search must find every neighbour for any cell >= h; h exactly puts
+    # neighbours up to 2 cells away, 2.002 h reduces to the 27-cell block
+    sc = scenes.dam_break(seed=3, grab=True, cube_pos=(0.4, 0.4, 0.2))
+    sc.params = dict(sc.params, cell=float(np.float32(cell_over_h * sc.params["h"])))
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_neighbour_list_overflow_takes_the_rescan(sph):
+    # 6 list slots: almost every particle has more partners, so the force pass searches
+    # again; it visits the partners in the list's order, so the state is bit-identical
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=3, grab=True, cube_pos=(0.4, 0.4, 0.2)),
+                                    seed=9, sigma=0.3)
+    check_one_substep(sph, sc, mode=0, max_neighbours=6)
+    out = []
+    for cap in (0, 6):
+        sim = sph.Simulation(sc, max_neighbours=cap)
+        sim.step(5)
+        st = sim.state()
+        out.append((st["x"], st["v"], sim.body(1), sim.body_wrench(1)))
+        sim.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
 
 
 # ------------------------------------------------------------ properties, edge cases

@@ -104,7 +104,8 @@ typedef struct {
  *   max_springs    soft-body springs (each counted once)
  *   max_path       entries of the grab path (sph_set_grab_path) and of the per-substep
  *                  wrench log
- *   max_neighbours neighbour-list slots per particle (0 = 96), 4 bytes each: the density
+ *   max_neighbours neighbour-list slots per particle (0 = 96; rounded up to a multiple of
+ *                  4), 4 bytes each: the density
  *                  pass records each particle's interaction partners for the force pass;
  *                  a particle with more partners is re-searched by the force pass
  *                  (same result, slower)

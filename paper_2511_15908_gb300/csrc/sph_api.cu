@@ -89,7 +89,7 @@ Layout make_layout(const sph_params &p, const sph_capacity &cap)
     L.wblock = take(16 * (size_t)L.max_wblocks);
     L.diag_part = take(8 * 8 * (size_t)L.max_force_blocks);
     L.diag_part2 = take(8 * 8 * (size_t)std::max(L.max_wblocks, kWrenchMinBlocks));
-    L.nl_cap = cap.max_neighbours > 0 ? cap.max_neighbours : kDefaultNeighbours;
+    L.nl_cap = ((cap.max_neighbours > 0 ? cap.max_neighbours : kDefaultNeighbours) + 3) & ~3;
     L.nlist = take(4 * (size_t)L.nl_cap * N);
     L.nlist_n = take(4 * N);
     L.diag = take(8 * 8);
@@ -359,7 +359,7 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     c.wblock = at<int4>(h, L.wblock);
     c.diag_part = at<double>(h, L.diag_part);
     c.diag_part2 = at<double>(h, L.diag_part2);
-    c.nlist = at<uint32_t>(h, L.nlist);
+    c.nlist4 = at<uint4>(h, L.nlist);
     c.nlist_n = at<int>(h, L.nlist_n);
     c.nl_cap = L.nl_cap;
     c.diag = at<double>(h, L.diag);

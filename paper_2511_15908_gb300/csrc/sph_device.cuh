@@ -117,11 +117,12 @@ __device__ __forceinline__ float dist2(float4 xi, float4 xj, float &dx, float &d
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Cell index of coordinate x clamped to [0, n) without reporting (NaN -> 0).
+// Cell index of coordinate x clamped to [0, n) without reporting.  Rounds toward -inf
+// like the hash's floor; out-of-range and non-finite inputs land on a valid cell.
 __device__ __forceinline__ int cell_clamp(float x, float o, float inv, int n)
 {
-    const float f = floorf(__fmul_rn(__fsub_rn(x, o), inv));
-    return f >= 0.0f ? (f < (float)(n - 1) ? (int)f : n - 1) : 0;
+    const int i = __float2int_rd(__fmul_rn(__fsub_rn(x, o), inv));
+    return min(max(i, 0), n - 1);
 }
 
 // Lower bound of |y - y_j| over the particles y_j whose cell index along this axis is j,
@@ -162,7 +163,8 @@ __device__ __forceinline__ void for_each_row(const SimConst &c, float4 x, uint32
             const float gy = cell_gap(x.y, y, cy, c.o[1], c.cell, c.margin);
             const float w2 = rz2 - gy * gy;
             if (!(w2 >= 0.0f)) continue;
-            const float w = sqrtf(w2) + c.margin;
+            // chord half-width; the rsqrt error (~1e-7 relative) is far inside the margin
+            const float w = w2 * rsqrtf(fmaxf(w2, 1e-30f)) + c.margin;
             const int xa = cell_clamp(x.x - w, c.o[0], c.inv_cell, c.nx);
             const int xb = cell_clamp(x.x + w, c.o[0], c.inv_cell, c.nx);
             const int base = (z * c.ny + y) * c.nx;
@@ -282,14 +284,23 @@ __device__ __forceinline__ void scan_apply_item(const SimConst &c, int blk)
         s_pre = t;
     }
     __syncthreads();
-    // 8 consecutive cells per thread
+    // 8 consecutive cells per thread, moved as two 16-byte vectors when all 8 exist and
+    // both arrays are 16-byte aligned (the workspace's are; a caller's array may not be)
     const int base = blk * kScanTile + threadIdx.x * 8;
+    const bool full = base + 8 <= c.ncell &&
+                      (((uintptr_t)c.cnt | (uintptr_t)c.cell_start) & 15u) == 0;
     uint32_t v[8], tot = 0;
+    if (full) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(c.cnt + base);
+        const uint4 b = *reinterpret_cast<const uint4 *>(c.cnt + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        v[i] = (base + i < c.ncell) ? c.cnt[base + i] : 0u;
-        tot += v[i];
+        for (int i = 0; i < 8; ++i) v[i] = (base + i < c.ncell) ? c.cnt[base + i] : 0u;
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tot += v[i];
     // inclusive warp scan of the thread totals
     uint32_t inc = tot;
 #pragma unroll
@@ -303,6 +314,18 @@ __device__ __forceinline__ void scan_apply_item(const SimConst &c, int blk)
     uint32_t wpre = 0;
     for (int w = 0; w < wid; ++w) wpre += ws[w];
     uint32_t run = s_pre + wpre + inc - tot;
+    if (full) {
+        uint32_t st[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { st[i] = run; run += v[i]; }
+        *reinterpret_cast<uint4 *>(c.cell_start + base) = make_uint4(st[0], st[1], st[2], st[3]);
+        *reinterpret_cast<uint4 *>(c.cell_start + base + 4) = make_uint4(st[4], st[5], st[6], st[7]);
+        // counts ready for the next substep's hash
+        *reinterpret_cast<uint4 *>(c.cnt + base) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(c.cnt + base + 4) = make_uint4(0u, 0u, 0u, 0u);
+        if (base + 8 == c.ncell) c.cell_start[c.ncell] = run;
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         int ci = base + i;
@@ -352,32 +375,12 @@ __device__ __forceinline__ void rank_gather_item(const SimConst &c, int blk)
 
 // ------------------------------------------------------------------- density pass
 
-// Density to a few 1e-8: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000 into a
-// pressure change that moves free-surface accelerations by ~1e-4 m/s^2, so every term is
-// unbiased (q = r/h from the float pair 1/h with one rounding -- r * fl(1/h) alone biases
-// q low), the shape is evaluated as (2-q)^3 - 4(1-q)^3 (no cancellation near q = 1), the
-// sum is compensated (Kahan), and rho - rho0 is formed with an FMA against alpha/6 kept
-// as a float pair.
-//
-// Each row of candidates is taken 32 at a time in two phases: a branch-free distance test
-// that sets one bit per neighbour, then the kernel on the set bits.  The pass also records
-// the particle's interaction partners (neighbours other than itself and, for a static or
-// rigid particle, other than its own body's particles) in the slot-major neighbour list
-// the force pass reads.  Static particles take no force, so they record nothing unless
-// the debug record is on.
-__device__ __forceinline__ void density_item(const SimConst &c, int blk)
-{
-    const int p = blk * kTile + threadIdx.x;
-    if (p >= c.n) return;
-    const float4 xi = c.xA[p];
+// Compensated sum of m_j * 6 w(q_ij) over a particle's neighbours (see below).
+struct DensitySum {
     float S = 0.0f, C = 0.0f;
-    int cnt = 0, nl = 0;
-    uint32_t bad = 0;
-    int kind = 0, excl_lo = 0, excl_n = 0;
-    if (xi.w < 0.0f) pair_scope(c, __float_as_int(c.vA[p].w), kind, excl_lo, excl_n);
-    const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
-    const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
-    auto add = [&](float4 xj, float r2) {
+    int cnt = 0;
+    __device__ __forceinline__ void add(const SimConst &c, float4 xj, float r2)
+    {
         // sqrt: rsqrt + one Newton step (~1 ulp); r2 = 0 (the particle itself) gives r = 0
         float rs = rsqrtf(fmaxf(r2, 1e-30f));
         float r = r2 * rs;
@@ -393,7 +396,61 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
         C = __fsub_rn(__fsub_rn(u, S), y);
         S = u;
         ++cnt;
-    };
+    }
+};
+
+// Appends slots to a particle's neighbour list four at a time: the entries wait in a
+// register quad and leave as one 16-byte store, so a warp issues a quarter of the
+// stores.  Entries beyond the capacity are counted, not stored.
+struct ListWriter {
+    uint4 *dst;                // this particle's group 0; group g at dst[g * n]
+    size_t n;
+    int cap, nl = 0;
+    uint4 quad;
+    __device__ __forceinline__ void push(uint32_t q)
+    {
+        const int slot = nl & 3;
+        quad.x = slot == 0 ? q : quad.x;
+        quad.y = slot == 1 ? q : quad.y;
+        quad.z = slot == 2 ? q : quad.z;
+        quad.w = q;
+        ++nl;
+        if (slot == 3 && nl <= cap) dst[(size_t)(nl / 4 - 1) * n] = quad;
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if ((nl & 3) && nl <= cap) dst[(size_t)(nl / 4) * n] = quad;
+    }
+};
+
+// Density to a few 1e-8: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000 into a
+// pressure change that moves free-surface accelerations by ~1e-4 m/s^2, so every term is
+// unbiased (q = r/h from the float pair 1/h with one rounding -- r * fl(1/h) alone biases
+// q low), the shape is evaluated as (2-q)^3 - 4(1-q)^3 (no cancellation near q = 1), the
+// sum is compensated (Kahan), and rho - rho0 is formed with an FMA against alpha/6 kept
+// as a float pair.
+//
+// Each row of candidates is taken 32 at a time in two phases: a branch-free distance test
+// that sets one bit per neighbour, then the kernel on the set bits.  The pass also records
+// the particle's interaction partners (neighbours other than itself and, for a static or
+// rigid particle, other than its own body's particles) in the neighbour list the force
+// pass reads.  Static particles take no force, so they record nothing unless the debug
+// record is on.
+__device__ __forceinline__ void density_item(const SimConst &c, int blk)
+{
+    const int p = blk * kTile + threadIdx.x;
+    if (p >= c.n) return;
+    const float4 xi = c.xA[p];
+    uint32_t bad = 0;
+    int kind = 0, excl_lo = 0, excl_n = 0;
+    if (xi.w < 0.0f) pair_scope(c, __float_as_int(c.vA[p].w), kind, excl_lo, excl_n);
+    const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
+    const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
+    DensitySum acc;
+    ListWriter list;
+    list.dst = c.nlist4 + p;
+    list.n = (size_t)c.n;
+    list.cap = c.nl_cap;
     for_each_row(c, xi, bad, [&](int s0, int e0) {
 #pragma unroll 1
         for (int b = s0; b < e0; b += 32) {
@@ -411,25 +468,25 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
                 mm &= mm - 1u;
                 const float4 xj = __ldg(c.xA + q);
                 float dx, dy, dz;
-                add(xj, dist2(xi, xj, dx, dy, dz));
+                acc.add(c, xj, dist2(xi, xj, dx, dy, dz));
                 if (q == p || !keep_list) continue;
                 if (excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) <
                                   (unsigned)excl_n)
                     continue;
-                if (nl < c.nl_cap) c.nlist[(size_t)nl * c.n + p] = (uint32_t)q;
-                ++nl;
+                list.push((uint32_t)q);
             }
         }
     });
-    c.nlist_n[p] = nl;
+    list.flush();
+    c.nlist_n[p] = list.nl;
     // rho - rho0 = alpha6 * (S - C) - rho0 with alpha6 = hi + lo
-    float drho = __fmaf_rn(c.alpha6_hi, S, -c.rho0) +
-                 __fmaf_rn(c.alpha6_lo, S, -c.alpha6_hi * C);
+    float drho = __fmaf_rn(c.alpha6_hi, acc.S, -c.rho0) +
+                 __fmaf_rn(c.alpha6_lo, acc.S, -c.alpha6_hi * acc.C);
     float rho = c.rho0 + drho;
     float pr = c.k * drho;
     if ((c.flags & FLAG_CLAMP) && pr < 0.0f) pr = 0.0f;
     c.prho[p] = make_float2(rho, pr / (rho * rho));
-    if (c.flags & FLAG_RECORD) c.nnbr[p] = cnt - 1;
+    if (c.flags & FLAG_RECORD) c.nnbr[p] = acc.cnt - 1;
     report(c, bad);
 }
 
@@ -480,14 +537,19 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
             };
             const int nl = __ldg(c.nlist_n + p);
             if (nl <= c.nl_cap) {
-                // the partners the density pass recorded (independent index loads)
-#pragma unroll 2
-                for (int k = 0; k < nl; ++k) {
-                    const int q = (int)__ldg(c.nlist + (size_t)k * c.n + p);
-                    const float4 xj = __ldg(c.xA + q);
-                    float dx, dy, dz;
-                    const float r2 = dist2(xi, xj, dx, dy, dz);
-                    pair(q, xj, dx, dy, dz, r2);
+                // the partners the density pass recorded, four per 16-byte load
+                for (int g = 0; 4 * g < nl; ++g) {
+                    const uint4 e = __ldg(c.nlist4 + (size_t)g * c.n + p);
+                    const int m = min(4, nl - 4 * g);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (j >= m) break;
+                        const int q = (int)(j == 0 ? e.x : j == 1 ? e.y : j == 2 ? e.z : e.w);
+                        const float4 xj = __ldg(c.xA + q);
+                        float dx, dy, dz;
+                        const float r2 = dist2(xi, xj, dx, dy, dz);
+                        pair(q, xj, dx, dy, dz, r2);
+                    }
                 }
             } else {
                 // more partners than list slots: search again

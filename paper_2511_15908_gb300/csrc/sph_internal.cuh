@@ -60,7 +60,7 @@ struct __align__(16) SimConst {
     int n_wblocks;
     int n_wgrid;               // wrench kernel grid = max(n_wblocks, kWrenchMinBlocks)
     int smooth_window;
-    int nl_cap;                // neighbour-list slots per particle
+    int nl_cap;                // neighbour-list slots per particle (a multiple of 4)
     int body_end[kMaxBodies];  // exclusive id end of each body (ids ascending)
     int body_kind[kMaxBodies];
     int wfirst[kMaxBodies];    // first reduction block of each body
@@ -83,8 +83,9 @@ struct __align__(16) SimConst {
     int4 *wblock;              // (body, l0, l1, 0) per reduction block
     double *diag_part;         // n_force_blocks x 8
     double *diag_part2;        // wrench grid x 8 (second level)
-    uint32_t *nlist;           // nl_cap x n, slot-major: neighbours kept by the density
-                               // pass for the force pass (nlist[k * n + p], k < nlist_n[p])
+    uint4 *nlist4;             // (nl_cap / 4) x n quads: the neighbours the density pass
+                               // keeps for the force pass; entry k of particle p is
+                               // component k % 4 of nlist4[(k / 4) * n + p], k < nlist_n[p]
     int *nlist_n;              // per particle: neighbours found (> nl_cap: force rescans)
     double *diag;              // 8
     double *wlog;              // max_path x 6

@@ -2,6 +2,9 @@
 // (captured once into a CUDA graph).  The arithmetic lives in sph_device.cuh.
 #include "sph_device.cuh"
 
+#ifndef SPH_DENSITY_MINB
+#define SPH_DENSITY_MINB 6    // resident 256-thread blocks per SM the density pass is built for
+#endif
 #ifndef SPH_FORCE_MINB
 #define SPH_FORCE_MINB 4      // resident 256-thread blocks per SM the force pass is built for
 #endif
@@ -13,7 +16,7 @@ __global__ void __launch_bounds__(kTile) k_scan_tiles(SimConst c) { scan_tiles_i
 __global__ void __launch_bounds__(kTile) k_scan_apply(SimConst c) { scan_apply_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_scatter(SimConst c) { scatter_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_rank_gather(SimConst c) { rank_gather_item(c, blockIdx.x); }
-__global__ void __launch_bounds__(kTile) k_density(SimConst c) { density_item(c, blockIdx.x); }
+__global__ void __launch_bounds__(kTile, SPH_DENSITY_MINB) k_density(SimConst c) { density_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force(SimConst c) { force_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_wrench(SimConst c) { wrench_item(c, blockIdx.x); }
 __global__ void k_cycle_end(SimConst c) { cycle_end_item(c); }

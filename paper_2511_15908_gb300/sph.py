@@ -535,19 +535,25 @@ NOALLOC_MAX_PARTICLES = 1 << 18
 NOALLOC_MAX_CELLS = 1 << 18
 
 
-def cell_sort_noalloc(params: dict, x_dev, stream=None):
+def cell_sort_noalloc(params: dict, x_dev, stream=None, out=None):
     """Allocation-free spatial hash of the particles in x_dev (CUDA float32 tensor (n, 4)):
-    returns (keys, order, cell_start) CUDA tensors.  The output tensors are the caller's
-    (allocated here by torch); the library call itself allocates nothing."""
+    returns (keys, order, cell_start) CUDA tensors.  The output tensors are the caller's:
+    `out` = (keys[n], order[n], cell_start[cells + 1]) int32 tensors, or allocated here by
+    torch when None; the library call itself allocates nothing."""
     import torch
     L = load()
     P = make_params(params, 1.0)
     n = int(x_dev.shape[0])
     x_dev = x_dev.contiguous()
     ncell = int(np.prod(grid_dims(params)))
-    keys = torch.empty(max(n, 1), dtype=torch.int32, device=x_dev.device)
-    order = torch.empty(max(n, 1), dtype=torch.int32, device=x_dev.device)
-    cs = torch.empty(ncell + 1, dtype=torch.int32, device=x_dev.device)
+    if out is not None:
+        keys, order, cs = out
+        if keys.numel() < n or order.numel() < n or cs.numel() < ncell + 1:
+            raise ValueError("output tensors too small")
+    else:
+        keys = torch.empty(max(n, 1), dtype=torch.int32, device=x_dev.device)
+        order = torch.empty(max(n, 1), dtype=torch.int32, device=x_dev.device)
+        cs = torch.empty(ncell + 1, dtype=torch.int32, device=x_dev.device)
     st = stream if stream is not None else torch.cuda.current_stream(x_dev.device)
     r = L.sph_cell_sort_noalloc(ctypes.byref(P), x_dev.data_ptr(), n, keys.data_ptr(), order.data_ptr(),
                                 cs.data_ptr(), st.cuda_stream)

@@ -66,3 +66,23 @@ def test_noalloc_rejects_sizes_beyond_the_limit(sph):
     with pytest.raises(sph.SphError) as e:
         sph.cell_sort_noalloc(big, torch.zeros((16, 4), dtype=torch.float32, device="cuda"))
     assert e.value.status == sph.ERR_CAPACITY
+
+
+def test_noalloc_cell_start_only_4_byte_aligned(sph):
+    # a caller's cell_start that is only 4-byte aligned takes the scalar path of the scan
+    import torch
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=2), seed=2, sigma=0.3)
+    x0, keys, ids, cs = _reference(sph, sc)
+    x4 = np.zeros((x0.shape[0], 4), np.float32)
+    x4[:, :3] = x0
+    xd = torch.tensor(x4, device="cuda")
+    n = x0.shape[0]
+    buf = torch.zeros(cs.size + 1, dtype=torch.int32, device="cuda")
+    assert (buf.data_ptr() + 4) % 16 != 0
+    out = (torch.empty(n, dtype=torch.int32, device="cuda"),
+           torch.empty(n, dtype=torch.int32, device="cuda"), buf[1:])
+    k, o, c = sph.cell_sort_noalloc(sc.params, xd, out=out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(k.cpu().numpy().astype(np.uint32), keys)
+    np.testing.assert_array_equal(o.cpu().numpy(), ids)
+    np.testing.assert_array_equal(c.cpu().numpy().astype(np.uint32), cs)

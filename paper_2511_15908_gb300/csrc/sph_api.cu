@@ -309,15 +309,15 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     grid_dims(*p, L.dims, c.o, c.inv_cell);
     float R = 2.0f * p->h;
     c.R2 = R * R;
-    c.cell = p->cell;
     {
         // The search radius exceeds R by a margin far above the FP32 rounding of the
-        // predicate (relative ~1e-6) and of cell bounds (a few ulp of the coordinates).
+        // predicate (relative ~1e-6) and of cell coordinates (a few ulp of the coordinates).
         float M = 0.0f;
         for (int a = 0; a < 3; ++a)
             M = std::max(M, std::max(std::fabs(c.o[a]), std::fabs(c.o[a] + (float)L.dims[a] * p->cell)));
-        c.margin = std::max(1e-3f * R, 64.0f * M * 1.1920929e-7f);
-        c.Rs = R + c.margin;
+        const float margin = std::max(1e-3f * R, 64.0f * M * 1.1920929e-7f);
+        c.Rc = (R + margin) / p->cell;
+        c.mc = margin / p->cell;
     }
     c.h = p->h;
     c.inv_h = 1.0f / p->h;

@@ -117,56 +117,55 @@ __device__ __forceinline__ float dist2(float4 xi, float4 xj, float &dx, float &d
     return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
 }
 
-// Cell index of coordinate x clamped to [0, n) without reporting.  Rounds toward -inf
-// like the hash's floor; out-of-range and non-finite inputs land on a valid cell.
-__device__ __forceinline__ int cell_clamp(float x, float o, float inv, int n)
+// Floor of a cell coordinate clamped to [0, n): out-of-range and non-finite inputs land on
+// a valid cell.
+__device__ __forceinline__ int cell_floor(float u, int n)
 {
-    const int i = __float2int_rd(__fmul_rn(__fsub_rn(x, o), inv));
-    return min(max(i, 0), n - 1);
+    return min(max(__float2int_rd(u), 0), n - 1);
 }
 
-// Lower bound of |y - y_j| over the particles y_j whose cell index along this axis is j,
-// where cj is the cell of y: the distance from y to cell j's near face, less the margin.
-__device__ __forceinline__ float cell_gap(float y, int j, int cj, float o, float cell, float margin)
+// Lower bound, in cell units, of the distance along one axis from cell coordinate u (own
+// cell cu) to any particle whose cell index along that axis is j: the distance to cell
+// j's near face, less the margin.
+__device__ __forceinline__ float cell_gap(float u, int j, int cu, float mc)
 {
-    if (j == cj) return 0.0f;
-    const float g = j > cj ? __fsub_rn(__fmaf_rn((float)j, cell, o), y)
-                           : __fsub_rn(y, __fmaf_rn((float)(j + 1), cell, o));
-    return fmaxf(g - margin, 0.0f);
+    if (j == cu) return 0.0f;
+    const float g = j > cu ? (float)j - u : u - (float)(j + 1);
+    return fmaxf(g - mc, 0.0f);
 }
 
 // Calls f(s, e) for every row of cells (fixed y and z) that can hold a particle within
-// the search radius Rs of x; [s, e) is the range of sorted slots of the row's cells whose
+// the search radius of x; [s, e) is the range of sorted slots of the row's cells whose
 // x-extent can reach that far (cells along x are consecutive in the key, so the range is
 // contiguous).  Each row is clipped to the chord of the search sphere at the row's
 // nearest y-z distance, so for a cell near h the candidates fill about 2.5 times the
-// sphere's volume instead of the 6.5 times of a 27-cell block of 2h cells.  Every bound
-// is a lower bound on the true distance and FP32 rounding is monotone, so no particle
-// that passes the FP32 predicate is ever outside the visited cells.
+// sphere's volume instead of the 6.5 times of a 27-cell block of 2h cells.  The bounds
+// work in cell coordinates u = (x - o) / cell, rounded exactly as the hash rounds them;
+// every bound is a lower bound on the distance and rounding is monotone, so no particle
+// that passes the FP32 predicate is ever outside the visited cells (the margin, ~2e-3
+// cells, is far above the rounding of u).
 template <class F>
 __device__ __forceinline__ void for_each_row(const SimConst &c, float4 x, uint32_t &bad, F &&f)
 {
-    int cx, cy, cz;
-    uint32_t dummy = 0;
-    cell_of(c, x, cx, cy, cz, dummy);
-    const float Rs = c.Rs, Rs2 = Rs * Rs;
-    const int z0 = cell_clamp(x.z - Rs, c.o[2], c.inv_cell, c.nz);
-    const int z1 = cell_clamp(x.z + Rs, c.o[2], c.inv_cell, c.nz);
-    const int y0 = cell_clamp(x.y - Rs, c.o[1], c.inv_cell, c.ny);
-    const int y1 = cell_clamp(x.y + Rs, c.o[1], c.inv_cell, c.ny);
+    const float ux = __fmul_rn(__fsub_rn(x.x, c.o[0]), c.inv_cell);
+    const float uy = __fmul_rn(__fsub_rn(x.y, c.o[1]), c.inv_cell);
+    const float uz = __fmul_rn(__fsub_rn(x.z, c.o[2]), c.inv_cell);
+    const float Rc = c.Rc, Rc2 = Rc * Rc, mc = c.mc;
+    const int cy = cell_floor(uy, c.ny), cz = cell_floor(uz, c.nz);
+    const int z0 = cell_floor(uz - Rc, c.nz), z1 = cell_floor(uz + Rc, c.nz);
+    const int y0 = cell_floor(uy - Rc, c.ny), y1 = cell_floor(uy + Rc, c.ny);
 #pragma unroll 1
     for (int z = z0; z <= z1; ++z) {
-        const float gz = cell_gap(x.z, z, cz, c.o[2], c.cell, c.margin);
-        const float rz2 = Rs2 - gz * gz;
+        const float gz = cell_gap(uz, z, cz, mc);
+        const float rz2 = Rc2 - gz * gz;
 #pragma unroll 1
         for (int y = y0; y <= y1; ++y) {
-            const float gy = cell_gap(x.y, y, cy, c.o[1], c.cell, c.margin);
+            const float gy = cell_gap(uy, y, cy, mc);
             const float w2 = rz2 - gy * gy;
             if (!(w2 >= 0.0f)) continue;
             // chord half-width; the rsqrt error (~1e-7 relative) is far inside the margin
-            const float w = w2 * rsqrtf(fmaxf(w2, 1e-30f)) + c.margin;
-            const int xa = cell_clamp(x.x - w, c.o[0], c.inv_cell, c.nx);
-            const int xb = cell_clamp(x.x + w, c.o[0], c.inv_cell, c.nx);
+            const float w = w2 * rsqrtf(fmaxf(w2, 1e-30f)) + mc;
+            const int xa = cell_floor(ux - w, c.nx), xb = cell_floor(ux + w, c.nx);
             const int base = (z * c.ny + y) * c.nx;
             const int s = (int)__ldg(c.cell_start + base + xa);
             int e = (int)__ldg(c.cell_start + base + xb + 1);
@@ -399,27 +398,34 @@ struct DensitySum {
     }
 };
 
-// Appends slots to a particle's neighbour list four at a time: the entries wait in a
-// register quad and leave as one 16-byte store, so a warp issues a quarter of the
-// stores.  Entries beyond the capacity are counted, not stored.
+// Appends slots to a particle's neighbour list four at a time: entries shift into a
+// register quad and leave as one 16-byte store, so a warp issues a quarter of the stores.
+// Entries beyond the capacity are counted, not stored.
 struct ListWriter {
-    uint4 *dst;                // this particle's group 0; group g at dst[g * n]
+    uint4 *dst;                // this particle's quad 0; quad g at dst[g * n]
     size_t n;
     int cap, nl = 0;
     uint4 quad;
     __device__ __forceinline__ void push(uint32_t q)
     {
-        const int slot = nl & 3;
-        quad.x = slot == 0 ? q : quad.x;
-        quad.y = slot == 1 ? q : quad.y;
-        quad.z = slot == 2 ? q : quad.z;
-        quad.w = q;
+        quad = make_uint4(quad.y, quad.z, quad.w, q);
         ++nl;
-        if (slot == 3 && nl <= cap) dst[(size_t)(nl / 4 - 1) * n] = quad;
+        if ((nl & 3) == 0 && nl <= cap) dst[(size_t)(nl / 4 - 1) * n] = quad;
     }
     __device__ __forceinline__ void flush()
     {
-        if ((nl & 3) && nl <= cap) dst[(size_t)(nl / 4) * n] = quad;
+        const int r = nl & 3;
+        if (r == 0 || nl > cap) return;
+        // the last r entries sit in the top r components; move them to the bottom
+        uint4 o = quad;
+        if (r == 1) {
+            o.x = quad.w;
+        } else if (r == 2) {
+            o.x = quad.z; o.y = quad.w;
+        } else {
+            o.x = quad.y; o.y = quad.z; o.z = quad.w;
+        }
+        dst[(size_t)(nl / 4) * n] = o;
     }
 };
 
@@ -447,6 +453,7 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
     const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
     DensitySum acc;
+    acc.add(c, xi, 0.0f);                               // self term
     ListWriter list;
     list.dst = c.nlist4 + p;
     list.n = (size_t)c.n;
@@ -463,13 +470,14 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
                 if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
                 bit <<= 1;
             }
+            if ((unsigned)(p - b) < 32u) mm &= ~(1u << (p - b));   // self: summed above
             while (mm) {
                 const int q = b + __ffs(mm) - 1;
                 mm &= mm - 1u;
                 const float4 xj = __ldg(c.xA + q);
                 float dx, dy, dz;
                 acc.add(c, xj, dist2(xi, xj, dx, dy, dz));
-                if (q == p || !keep_list) continue;
+                if (!keep_list) continue;
                 if (excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) <
                                   (unsigned)excl_n)
                     continue;
@@ -537,9 +545,13 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
             };
             const int nl = __ldg(c.nlist_n + p);
             if (nl <= c.nl_cap) {
-                // the partners the density pass recorded, four per 16-byte load
+                // the partners the density pass recorded, four per 16-byte load; the next
+                // quad is fetched while this one is evaluated
+                const uint4 *lq = c.nlist4 + p;
+                uint4 nxt = nl > 0 ? __ldg(lq) : make_uint4(0u, 0u, 0u, 0u);
                 for (int g = 0; 4 * g < nl; ++g) {
-                    const uint4 e = __ldg(c.nlist4 + (size_t)g * c.n + p);
+                    const uint4 e = nxt;
+                    if (4 * (g + 1) < nl) nxt = __ldg(lq + (size_t)(g + 1) * c.n);
                     const int m = min(4, nl - 4 * g);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {

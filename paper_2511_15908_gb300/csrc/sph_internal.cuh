@@ -43,10 +43,11 @@ struct DevBody {
 struct __align__(16) SimConst {
     int n, nf, nb, n_body_particles;
     int nx, ny, nz, ncell;
-    float o[3], inv_cell, cell;
+    float o[3], inv_cell;
     float R2, h, inv_h;
-    float Rs, margin;          // search radius R + margin; margin covers FP32 rounding of
-                               // cell bounds and of the neighbour predicate
+    float Rc, mc;              // search radius R + margin and the margin, in cell units;
+                               // the margin covers FP32 rounding of cell coordinates and
+                               // of the neighbour predicate
     float rho0, k, nu20;       // nu20 = 2 (d + 2) nu * 2 with d = 3 (the 2 from rho_bar)
     float eps_h2;
     float alpha6_hi, alpha6_lo; // alpha / 6 = 1 / (4 pi h^3) as an unevaluated float pair

@@ -89,7 +89,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -264,6 +264,39 @@ def batched_form(args, flush_l2_factory):
     return out
 
 
+def tait_variant(args, sc, flush_l2_factory):
+    """The Tait equation of state (Sec. 3.1's named alternative) on the same workload:
+    ms per substep and the density pass, timed like the plain path."""
+    import torch
+    from paper_2511_15908_gb300 import sph
+    sim = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_TAIT)
+    sim.set_profiling(True)
+    flush = flush_l2_factory(sim.stream)
+    domain = [0]
+    for _ in range(max(3, args.warmup)):
+        flush()
+        sim.step(1)
+    _reported(sim.sync, domain, sph)
+    n = max(5, args.steps)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    kt = np.zeros((n, len(sph.KERNELS)))
+    for i in range(n):
+        flush()
+        ev0[i].record(sim.stream)
+        sim.step(1)
+        ev1[i].record(sim.stream)
+        kt[i] = _reported(sim.kernel_times, domain, sph)
+    _reported(sim.sync, domain, sph)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)]))
+    km = kt.mean(axis=0)
+    sim.close()
+    return {"ms_per_substep": ms, "value": sc.n_fluid / (ms / 1e3), "unit": UNIT,
+            "density_ms": float(km[sph.KERNELS.index("density")]),
+            "force_ms": float(km[sph.KERNELS.index("force")]), "out_of_domain_reports": domain[0],
+            "what": "same workload with SPH_FLAG_TAIT (p = B((rho/rho0)^7 - 1), B = k rho0 / 7)"}
+
+
 def surrogate_form(args):
     """Form (4): the BF16 tcgen05 MLP surrogate at 1 kHz haptic ticks on the stirring tank
     (250k fluid), trained on the GPU from logged (descriptor, wrench) pairs: (a) pairs logged
@@ -317,6 +350,19 @@ def surrogate_form(args):
     return out
 
 
+def _reported(fn, counter, sph):
+    """Call fn(); a latched out-of-domain report (particles that splashed over the tank
+    walls are clamped into border cells) is counted and the read repeated -- the status
+    clears once reported and the data is unchanged."""
+    try:
+        return fn()
+    except sph.SphError as e:
+        if e.status != sph.ERR_DOMAIN:
+            raise
+        counter[0] += 1
+        return fn()
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -328,20 +374,6 @@ def run_ours(args):
     build.build()
     sc = _workload(args.workload)
     peaks, peak_kind = _peaks()
-
-    # CPU baseline (rank 0, N = 1): the oracle as it stands, one substep, host cores;
-    # its first-substep wrench is also the FP64 reference of the grab-wrench error.
-    cpu = None
-    ref_wrench = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        t_cpu, out = _oracle_substep_time(sc)
-        ref_wrench = out["wrench"][sc.grab_body]
-        cpu = {"value": sc.n_fluid / t_cpu, "unit": UNIT, "cores": os.cpu_count(),
-               "kind": "oracle",
-               "sample": f"1 substep of the full coupled scene ({sc.n_total} particles), "
-                         f"FP64 uniform-grid oracle, {t_cpu:.1f} s"}
 
     # neighbour statistics of the first substep (record run) for the algorithmic flop count
     rec = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_RECORD)
@@ -357,11 +389,6 @@ def run_ours(args):
     # first substep: grab-wrench error against the FP64 oracle
     sim.step(1)
     w_gpu = sim.grab_wrench()
-    wrench_err = None
-    if ref_wrench is not None:
-        fe = np.linalg.norm(w_gpu[:3] - ref_wrench[:3]) / max(np.linalg.norm(ref_wrench[:3]), 1e-30)
-        te = np.linalg.norm(w_gpu[3:] - ref_wrench[3:]) / max(np.linalg.norm(ref_wrench[3:]), 1e-30)
-        wrench_err = {"force_rel": float(fe), "torque_rel": float(te)}
 
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     stream = sim.stream
@@ -370,10 +397,11 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             flush.fill_(1)
 
+    domain = [0]
     for _ in range(args.warmup):
         flush_l2()
         sim.step(1)
-    sim.sync()
+    _reported(sim.sync, domain, sph)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -386,9 +414,9 @@ def run_ours(args):
             ev0[i].record(stream)
             sim.step(1)
             ev1[i].record(stream)
-            ktimes[i] = sim.kernel_times()          # synchronises the stream
+            ktimes[i] = _reported(sim.kernel_times, domain, sph)   # synchronises the stream
         torch.cuda.synchronize()
-    sim.sync()
+    _reported(sim.sync, domain, sph)
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
     total_s = float(step_ms.sum()) / 1e3
     if world > 1:
@@ -440,10 +468,28 @@ def run_ours(args):
         pose_h[:] = row
         sim.set_grab_pose(sim.body_ids[sc.grab_body], pose_h[:7], pose_h[7:])
         sim.step(1)
-        w = sim.grab_wrench()
+        w = _reported(sim.grab_wrench, domain, sph)
         e2e_s += time.perf_counter() - t0
     e2e_value = world * sc.n_fluid * args.steps / e2e_s
     sim.close()
+
+    # CPU baseline (rank 0, N = 1), after every GPU timing so that the host's OpenMP
+    # threads run alone: the oracle as it stands, one substep, host cores; its wrench is
+    # also the FP64 reference of the first substep's grab wrench.
+    cpu = None
+    wrench_err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t_cpu, out = _oracle_substep_time(sc)
+        ref_wrench = out["wrench"][sc.grab_body]
+        cpu = {"value": sc.n_fluid / t_cpu, "unit": UNIT, "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": f"1 substep of the full coupled scene ({sc.n_total} particles), "
+                         f"FP64 uniform-grid oracle, {t_cpu:.2f} s"}
+        fe = np.linalg.norm(w_gpu[:3] - ref_wrench[:3]) / max(np.linalg.norm(ref_wrench[:3]), 1e-30)
+        te = np.linalg.norm(w_gpu[3:] - ref_wrench[3:]) / max(np.linalg.norm(ref_wrench[3:]), 1e-30)
+        wrench_err = {"force_rel": float(fe), "torque_rel": float(te)}
 
     forms = {}
     if not args.no_forms:
@@ -454,6 +500,7 @@ def run_ours(args):
             return f
         forms["batched"] = batched_form(args, factory)
         forms["surrogate"] = surrogate_form(args)
+        forms["tait_eos"] = tait_variant(args, sc, factory)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -465,7 +512,8 @@ def run_ours(args):
                                        f"{sc.params['dt']}", "particles_all": n_all,
                            "particles_fluid": sc.n_fluid, "l2": "flushed between steps",
                            "parallelism": f"replicas x{world}",
-                           "all_particle_steps_per_s": value * n_all / sc.n_fluid},
+                           "all_particle_steps_per_s": value * n_all / sc.n_fluid,
+                           "out_of_domain_reports": domain[0]},
                 "gpu_launches": 8 * args.steps,
                 "kernel_ms": {k: float(v) for k, v in zip(sph.KERNELS, kmean)},
                 "kernel_share": shares,
@@ -491,7 +539,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="coupled", choices=["coupled", "stirring", "dam_break"])

@@ -57,8 +57,12 @@ enum {
     SPH_FLAG_CLAMP_PRESSURE = 1u << 0, /* negative pressures from the linear EOS become 0 */
     SPH_FLAG_RECORD = 1u << 1,         /* keep per-particle acceleration, neighbour
                                           counts and static-body wrenches (test hook) */
-    SPH_FLAG_NO_GRAPH = 1u << 2        /* launch kernels directly instead of replaying a
+    SPH_FLAG_NO_GRAPH = 1u << 2,       /* launch kernels directly instead of replaying a
                                           captured CUDA graph */
+    SPH_FLAG_TAIT = 1u << 3            /* Tait variation of the equation of state, which
+                                          Sec. 3.1 names as the alternative to Eq. pressure:
+                                          p = B ((rho / rho0)^7 - 1), B = k rho0 / 7 (the
+                                          same slope as k (rho - rho0) at rest) */
 };
 
 /* Body kinds (Sec. 3.2 particle types). */
@@ -104,11 +108,12 @@ typedef struct {
  *   max_springs    soft-body springs (each counted once)
  *   max_path       entries of the grab path (sph_set_grab_path) and of the per-substep
  *                  wrench log
- *   max_neighbours neighbour-list slots per particle (0 = 96; rounded up to a multiple of
- *                  4), 4 bytes each: the density
- *                  pass records each particle's interaction partners for the force pass;
- *                  a particle with more partners is re-searched by the force pass
- *                  (same result, slower)
+ *   max_neighbours neighbour-list slots per particle (0 = 288; rounded up to a multiple
+ *                  of 4), 4 bytes each: the density pass records each particle's
+ *                  interaction partners for the force pass; a particle with more partners
+ *                  is re-searched by the force pass (same result, slower).  288 covers a
+ *                  fluid particle among boundary particles sampled at half its spacing
+ *                  (about 270 partners); slots a particle does not use are never touched
  */
 typedef struct {
     int32_t max_particles, max_bodies, max_springs, max_path;

@@ -10,7 +10,8 @@
  *   Sec. 3.1, Alg. 1      density pass, force pass, integrate pass
  *   Sec. 3.1, Eq. kernel  cubic-spline W(r,h) with support 2h
  *   Sec. 3.1, Eq. density rho_i = sum_j m_j W(|x_i - x_j|, h)
- *   Sec. 3.1, Eq. pressure p_i = k (rho_i - rho_0)
+ *   Sec. 3.1, Eq. pressure p_i = k (rho_i - rho_0); with the Tait flag the variation the
+ *                         same passage names instead (see readings)
  *   Sec. 3.1, Eq. euler   v += a dt;  x += v(t+dt) dt
  *   Sec. 3.1 (uniform-grid spatial hash) and Alg. 2 (cell, count, cumulative sum,
  *                         sorted index)
@@ -31,6 +32,9 @@
  *   - the cell of a particle, the neighbour predicate and the boundary positions fed
  *     to them are fixed FP32 operation sequences (below), so integer results are
  *     bit-defined; all physics is FP64 from the FP32 state;
+ *   - the Tait variation of the equation of state (named in Sec. 3.1, form not given) is
+ *     the weakly compressible form p = B ((rho / rho_0)^gamma - 1), gamma = 7, with
+ *     B = k rho_0 / gamma so that dp/drho at rest equals the linear form's k;
  *   - the grab wrench is the sum of pair forces on the body's particles (gravity
  *     excluded) with torque about the grab point; rigid bodies are updated every
  *     substep.
@@ -45,6 +49,8 @@
 #define ORC_SOFT 3
 
 #define ORC_CLAMP_PRESSURE 1
+#define ORC_TAIT 8
+#define ORC_TAIT_GAMMA 7.0
 
 #define ORC_PI 3.14159265358979323846
 
@@ -442,6 +448,8 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
         rho[p] = c.rho_sum;
         nnbr[p] = c.count;
         double pr = P->k * (c.rho_sum - P->rho0);
+        if (P->flags & ORC_TAIT)
+            pr = P->k * P->rho0 / ORC_TAIT_GAMMA * (pow(c.rho_sum / P->rho0, ORC_TAIT_GAMMA) - 1.0);
         if ((P->flags & ORC_CLAMP_PRESSURE) && pr < 0.0) pr = 0.0;
         pres[p] = pr;
     }

@@ -323,6 +323,7 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     c.inv_h = 1.0f / p->h;
     c.rho0 = p->rho0;
     c.k = p->k;
+    c.tait_B = (float)((double)p->k * (double)p->rho0 / 7.0);
     c.nu20 = 20.0f * p->nu;
     c.eps_h2 = p->visc_eps * p->h * p->h;
     {

@@ -31,7 +31,7 @@ constexpr int kTile = 256;     // threads per block = particles per tile
 
 
 constexpr int KIND_STATIC = 1, KIND_RIGID = 2, KIND_SOFT = 3;
-constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u;
+constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u, FLAG_TAIT = 8u;
 
 // ------------------------------------------------------------------ small helpers
 
@@ -491,7 +491,15 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     float drho = __fmaf_rn(c.alpha6_hi, acc.S, -c.rho0) +
                  __fmaf_rn(c.alpha6_lo, acc.S, -c.alpha6_hi * acc.C);
     float rho = c.rho0 + drho;
-    float pr = c.k * drho;
+    float pr;
+    if (c.flags & FLAG_TAIT) {
+        // Tait variation (Sec. 3.1): B ((rho/rho0)^7 - 1), B = k rho0 / 7; (1+x)^7 - 1 by its
+        // binomial expansion, which has no cancellation near rest (x = drho / rho0 ~ 1e-3)
+        const float x = drho / c.rho0;
+        pr = c.tait_B * (x * (7.0f + x * (21.0f + x * (35.0f + x * (35.0f + x * (21.0f + x * (7.0f + x)))))));
+    } else {
+        pr = c.k * drho;
+    }
     if ((c.flags & FLAG_CLAMP) && pr < 0.0f) pr = 0.0f;
     c.prho[p] = make_float2(rho, pr / (rho * rho));
     if (c.flags & FLAG_RECORD) c.nnbr[p] = acc.cnt - 1;

@@ -18,7 +18,7 @@ constexpr int kMaxCell = 512;       // particles per cell for the deterministic 
 constexpr int kScanTile = 2048;     // cells per scan block (256 threads x 8)
 constexpr int kReduceChunk = 256;   // body particles per wrench-reduction block
 constexpr int kWrenchMinBlocks = 128; // the FP64 reduction is spread over at least this many
-constexpr int kDefaultNeighbours = 96; // neighbour-list slots per particle when the
+constexpr int kDefaultNeighbours = 288; // neighbour-list slots per particle when the
                                        // capacity leaves it 0
 
 // status word bits (mirrors sph_status codes as bit positions)
@@ -49,6 +49,7 @@ struct __align__(16) SimConst {
                                // the margin covers FP32 rounding of cell coordinates and
                                // of the neighbour predicate
     float rho0, k, nu20;       // nu20 = 2 (d + 2) nu * 2 with d = 3 (the 2 from rho_bar)
+    float tait_B;              // k rho0 / 7: the Tait form's scale (same slope at rest)
     float eps_h2;
     float alpha6_hi, alpha6_lo; // alpha / 6 = 1 / (4 pi h^3) as an unevaluated float pair
     float invh_hi, invh_lo;     // 1 / h as an unevaluated float pair

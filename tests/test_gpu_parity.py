@@ -94,6 +94,9 @@ def check_one_substep(sph, sc, mode, record=True, max_neighbours=0):
     err = dif / scale
     cond = _by_id(ref, "cond", n)
     k = float(np.float32(sc.params["k"]))
+    if sc.params["flags"] & scenes.FLAG_TAIT:
+        # the Tait form's slope dp/drho = k (rho / rho0)^6 takes the place of k
+        k = k * np.maximum(1.0, (rho_ref / float(np.float32(sc.params["rho0"]))) ** 6)
     fp32_bound = EPS32 * (8.0 * k * cond[:, 0] / rho_ref + 4.0 * cond[:, 1])
     ok = dif <= ACC_TOL * scale + fp32_bound
     frac = float(np.mean(err[sel] <= ACC_TOL))
@@ -167,6 +170,27 @@ def test_stirring_tank_full_size_bench_config(sph):
 def test_coupled_full_size_bench_config(sph):
     sc = scenes.with_velocity_noise(scenes.coupled(seed=0, n_substeps=10), seed=6, sigma=0.2)
     check_one_substep(sph, sc, mode=1, record=False)
+
+
+def test_tait_eos_dam_break_grabbed_cube(sph):
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=3, grab=True, cube_pos=(0.4, 0.4, 0.2)),
+                                    seed=10, sigma=0.3)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_TAIT)
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_tait_eos_unclamped_tiny(sph):
+    sc = scenes.with_velocity_noise(scenes.tiny(seed=11, n=(7, 6, 5)), seed=11, sigma=0.5)
+    sc.params = dict(sc.params, flags=scenes.FLAG_TAIT)
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_tait_eos_coupled_reduced(sph):
+    sc = scenes.with_velocity_noise(
+        scenes.coupled(seed=1, n_fluid=60_000, cols=(60, 40), tank=(0.6, 0.4, 0.4), n_substeps=10,
+                       probe_r=0.04, soft_n=8), seed=12, sigma=0.2)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_TAIT)
+    check_one_substep(sph, sc, mode=1)
 
 
 @pytest.mark.parametrize("cell_over_h", [1.0, 1.37, 2.002])

@@ -304,11 +304,15 @@ def test_two_particle_pressure_force_is_repulsive_and_symmetric():
 
 
 @pytest.mark.slow
-def test_hydrostatic_column_settles_to_rho0_g_depth():
+@pytest.mark.parametrize("tait", [False, True])
+def test_hydrostatic_column_settles_to_rho0_g_depth(tait):
     # settled column: interior pressure p(d) ~ rho0 g d (this fails for a gradient that
-    # is off by a factor of two); run the grid oracle for 1.5 s of simulated time
+    # is off by a factor of two); run the grid oracle for 1.5 s of simulated time; the
+    # hydrostatic law does not depend on the equation of state (Tait as well as linear)
     sc = scenes.column(seed=0, n=(5, 5, 16))
     sc.params["nu"] = 5e-3
+    if tait:
+        sc.params["flags"] = sc.params["flags"] | scenes.FLAG_TAIT
     s = oracle.System(sc, mode=1)
     for _ in range(1500):
         out = s.substep()
@@ -411,3 +415,48 @@ def test_boxcar_smoothing():
     expect = [step[max(0, t - 19):t + 1, 0].mean() for t in range(40)]
     np.testing.assert_allclose(out[:, 0], expect, rtol=1e-15)
     np.testing.assert_allclose(out[29:, 0], 1.0)
+
+
+# ------------------------------------------------- Tait equation of state (Sec. 3.1)
+
+def _tait_pair(seed=6, unclamped=True):
+    sc = scenes.with_velocity_noise(scenes.tiny(seed=seed, n=(7, 7, 7)), seed=seed, sigma=0.3)
+    base = 0 if unclamped else scenes.FLAG_CLAMP_PRESSURE
+    lin = oracle.System(dict_scene(sc, base), mode=0).substep()
+    tait = oracle.System(dict_scene(sc, base | scenes.FLAG_TAIT), mode=0).substep()
+    return sc, lin, tait
+
+
+def dict_scene(sc, flags):
+    import copy
+    out = copy.copy(sc)
+    out.params = dict(sc.params, flags=flags)
+    return out
+
+
+def test_tait_matches_linear_eos_to_first_order_with_curvature_3k_rho0():
+    # (rho0 (1+x))^7 expansion: B ((1+x)^7 - 1) = k rho0 x + 3 k rho0 x^2 + O(x^3) with
+    # B = k rho0 / 7, so p_tait - p_lin - 3 k rho0 x^2 is third order in x; the linear term
+    # fixes B, the quadratic term (gamma - 1) / 2 = 3 fixes gamma = 7
+    sc, lin, tait = _tait_pair()
+    p = sc.params
+    k, rho0 = float(np.float32(p["k"])), float(np.float32(p["rho0"]))
+    np.testing.assert_array_equal(lin["rho"], tait["rho"])
+    x = lin["rho"] / rho0 - 1.0
+    near = np.abs(x) < 2e-2
+    assert near.sum() > 20
+    resid = tait["pres"][near] - lin["pres"][near] - 3.0 * k * rho0 * x[near] ** 2
+    assert np.all(np.abs(resid) <= 6.0 * k * rho0 * np.abs(x[near]) ** 3 + 1e-9 * k * rho0)
+
+
+def test_tait_is_convex_above_its_tangent_and_increasing():
+    # convex with the linear EOS as its tangent at rest: p_tait >= p_lin for every density,
+    # equality only at rho0; and pressure increases with density
+    sc, lin, tait = _tait_pair(seed=7)
+    assert np.all(tait["pres"] >= lin["pres"] - 1e-9 * np.abs(lin["pres"]).max())
+    o = np.argsort(lin["rho"])
+    assert np.all(np.diff(tait["pres"][o]) >= 0.0)
+    # a free-surface particle (rho ~ rho0 / 2) keeps only the tension floor -B
+    rho0 = float(np.float32(sc.params["rho0"]))
+    B = float(np.float32(sc.params["k"])) * rho0 / 7.0
+    assert tait["pres"].min() >= -B

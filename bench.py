@@ -297,6 +297,40 @@ def tait_variant(args, sc, flush_l2_factory):
             "what": "same workload with SPH_FLAG_TAIT (p = B((rho/rho0)^7 - 1), B = k rho0 / 7)"}
 
 
+def isosurface_form(args, sc):
+    """Alg. 2's isosurface kernels on the same workload after 20 substeps: the corner density
+    field (hash of the current state + field pass) and marching cubes, cube = h,
+    isovalue rho0 / 2, device time with CUDA events on the simulation's stream."""
+    import torch
+    from paper_2511_15908_gb300 import sph
+    sim = sph.Simulation(sc)
+    domain = [0]
+    sim.step(20)
+    _reported(sim.sync, domain, sph)
+    cube = float(np.float32(sc.params["h"]))
+    iso = float(np.float32(0.5 * sc.params["rho0"]))
+    dims, origin = sph.iso_grid(sc.params, cube)
+    s = sim.stream
+    field_ms, mc_ms, n_tris = [], [], 0
+    for rep in range(6):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(s)
+        f = sim.iso_field(cube)
+        e1.record(s)
+        tris = sph.iso_polygonize(f, dims, origin, cube, iso, max_tris=4 << 20, stream=s)
+        e2.record(s)
+        e2.synchronize()
+        if rep > 0:
+            field_ms.append(e0.elapsed_time(e1))
+            mc_ms.append(e1.elapsed_time(e2))
+        n_tris = int(tris.shape[0])
+    sim.close()
+    return {"field_ms": float(np.median(field_ms)), "polygonize_ms": float(np.median(mc_ms)),
+            "triangles": n_tris, "corners": int(np.prod(dims)), "cube": cube, "isovalue": iso,
+            "what": "sph_iso_field (hash of the current state + fluid density at every corner) "
+                    "and sph_iso_polygonize (count, scan, write) after 20 substeps"}
+
+
 def surrogate_form(args):
     """Form (4): the BF16 tcgen05 MLP surrogate at 1 kHz haptic ticks on the stirring tank
     (250k fluid), trained on the GPU from logged (descriptor, wrench) pairs: (a) pairs logged
@@ -501,6 +535,7 @@ def run_ours(args):
         forms["batched"] = batched_form(args, factory)
         forms["surrogate"] = surrogate_form(args)
         forms["tait_eos"] = tait_variant(args, sc, factory)
+        forms["isosurface"] = isosurface_form(args, sc)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

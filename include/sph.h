@@ -360,6 +360,69 @@ const char *sph_batch_last_error(const sph_batch *b);
 void sph_batch_destroy(sph_batch *b);
 
 /*
+ * Isosurface of the fluid (Alg. 2's isosurface compute kernels; Sec. 3.4).  The fluid's
+ * surface is the isosurface of a density field that the fluid particles generate through
+ * the smoothing kernel, sampled at the corners of a uniform grid of cubes offset from the
+ * hash grid and polygonised by marching cubes.
+ *
+ * Corner grid of edge `cube` over the scene's domain: corner (i, j, k) sits at
+ * origin + (i, j, k) cube with origin = domain_lo + cube / 2 (half a cube off the domain
+ * corner) and dims[a] = floor((domain_hi[a] - domain_lo[a]) / cube) corners per axis
+ * (>= 2 each).  Errors: SPH_ERR_ARG.
+ */
+sph_status sph_iso_grid(const sph_params *p, float cube, int32_t dims[3], float origin[3]);
+
+/*
+ * Density field of the fluid particles at every corner of that grid:
+ * phi(c) = sum over fluid particles j with |c - x_j| < 2h of m_j W(|c - x_j|, h)
+ * (Eq. density without the boundary and soft-body particles), from the current state.
+ *   d_field  device, dims[0] * dims[1] * dims[2] floats, x fastest; written.
+ * The spatial hash and reorder of the current state run first (the grid is reused for the
+ * corner search, as Sec. 3.4 says); the next substep redoes the same hash from the same
+ * state, so the simulation is unaffected, but sph_get_sort afterwards reports this hash.
+ * Enqueued on the handle's stream after a synchronisation.  Errors: SPH_ERR_ARG,
+ * SPH_ERR_CUDA, and the handle's pending status.
+ */
+sph_status sph_iso_field(sph_handle *h, float cube, float *d_field);
+
+/* Device workspace of sph_iso_polygonize for a corner grid of dims (0 if dims are invalid:
+ * each >= 2 and fewer than 2^28 cubes). */
+size_t sph_iso_workspace_bytes(const int32_t dims[3]);
+
+/*
+ * Marching cubes over a corner field (any field; sph_iso_field's or the caller's).
+ *   d_field      device, dims[0] * dims[1] * dims[2] floats, x fastest.
+ *   origin, cube corner (0,0,0) and cube edge, as sph_iso_grid returns them.
+ *   iso          isovalue; a corner is inside the surface when its value exceeds it.
+ *   d_ws         device workspace, 256-byte aligned, >= sph_iso_workspace_bytes(dims).
+ *   d_tris       device output, max_tris x 9 floats: the three vertices (x, y, z) of each
+ *                triangle, ordered by cube (x fastest) and within a cube by the rule
+ *                below; vertex on the edge from corner a to b at
+ *                p_a + (iso - phi_a) / (phi_b - phi_a) (p_b - p_a); the triangle's
+ *                normal (v1 - v0) x (v2 - v0) points out of the surface (toward lower
+ *                field values).
+ *   h_n_tris     host: the number of triangles of the whole surface.
+ * Rule per cube: on each face, two cut edges are joined by a segment, four cut edges by one
+ * segment around each inside corner (the face decides alone, so neighbouring cubes agree and
+ * the surface is closed); the segments form loops through the cut edges, taken in the
+ * order of their smallest edge, each starting there (first step to the smaller of its two
+ * neighbours) and running so that its normal (Newell's formula over the edge midpoints)
+ * points from the inside corners to the outside ones; a loop is split into a fan from its
+ * first vertex, or -- when a fan diagonal would join two vertices on a common cube face --
+ * into a fan from its centre (the mean of its vertices, one triangle per side, the centre
+ * first).  At most 7 triangles per cube.  Edges are numbered 0-3 along x
+ * (corners 0-1, 2-3, 4-5, 6-7), 4-7 along y (0-2, 1-3, 4-6, 5-7), 8-11 along z (0-4, 1-5,
+ * 2-6, 3-7), corner v at offset (v & 1, v >> 1 & 1, v >> 2 & 1).
+ * Synchronises the stream.  Returns SPH_ERR_CAPACITY (with *h_n_tris set) when the surface
+ * has more than max_tris triangles; only the first max_tris are written.  Errors:
+ * SPH_ERR_ARG, SPH_ERR_WORKSPACE, SPH_ERR_CAPACITY, SPH_ERR_CUDA.  The paper's own grid
+ * spacing and isovalue are not given; callers choose them.
+ */
+sph_status sph_iso_polygonize(const float *d_field, const int32_t dims[3], const float origin[3],
+                              float cube, float iso, void *d_ws, size_t ws_bytes, float *d_tris,
+                              int64_t max_tris, int64_t *h_n_tris, void *cuda_stream);
+
+/*
  * Allocation-free spatial hash.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- an engine plugin whose device memory is
  * owned by the host engine's allocator, a real-time haptic loop that must not allocate

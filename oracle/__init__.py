@@ -18,7 +18,8 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = [os.path.join(_HERE, "sph_oracle.c"), os.path.join(_HERE, "mlp_oracle.c")]
+_SRC = [os.path.join(_HERE, "sph_oracle.c"), os.path.join(_HERE, "mlp_oracle.c"),
+        os.path.join(_HERE, "iso_oracle.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 KIND_STATIC, KIND_RIGID, KIND_SOFT = 1, 2, 3
@@ -104,6 +105,9 @@ def _declare(L):
     if hasattr(L, "orc_mlp_forward"):
         from . import mlp as _mlp
         _mlp.declare(L)
+    if hasattr(L, "orc_iso_polygonize"):
+        from . import iso as _iso
+        _iso.declare(L)
 
 
 def _f32(x) -> float:
@@ -198,6 +202,12 @@ def boxcar(wrenches: np.ndarray, window: int) -> np.ndarray:
     return out
 
 
+def particle_mass(rho0, spacing) -> np.float32:
+    """SPH mass rho0 * s^3 as the FP32 value the method stores (each product rounded)."""
+    s32 = np.float32(spacing)
+    return np.float32(np.float32(rho0) * np.float32(np.float32(s32 * s32) * s32))
+
+
 class System:
     """Particles in the current slot order plus body states, advanced by `substep`.
 
@@ -214,9 +224,7 @@ class System:
         nf = scene.n_fluid
 
         def pmass(spacing):
-            # SPH mass rho0 * s^3 as the FP32 value the method stores (each product rounded)
-            s32 = np.float32(spacing)
-            return np.float32(rho0 * np.float32(np.float32(s32 * s32) * s32))
+            return particle_mass(rho0, spacing)
 
         xs = [np.asarray(scene.fluid_x, np.float32)]
         vs = [np.asarray(scene.fluid_v, np.float32)]

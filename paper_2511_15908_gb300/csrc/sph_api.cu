@@ -276,6 +276,10 @@ sph_status scene_for_batch(sph_handle *h, SimConst *out)
 // Batch support: the batch advanced this scene by n substeps (one update cycle).
 void scene_advanced(sph_handle *h, int n) { h->substeps += n; }
 
+// Isosurface support: the handle's stream and parameters.
+cudaStream_t scene_stream(sph_handle *h) { return h->stream; }
+const sph_params *scene_params(sph_handle *h) { return &h->p; }
+
 }  // namespace sphgb
 
 extern "C" {

@@ -102,6 +102,8 @@ constexpr int kSubstepKernels = 8;
 // them as graph nodes when the stream is being captured.
 cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev = nullptr,
                            bool external = false);
+// the first five substep kernels only: hash, scan, reorder of the current state
+cudaError_t launch_sort(const SimConst &c, cudaStream_t s);
 cudaError_t launch_cycle_end(const SimConst &c, cudaStream_t s);
 cudaError_t launch_set_grab(const SimConst &c, cudaStream_t s, int body, int grab,
                             const float *pose_vel13, const float *grab_local, int set_pose,

@@ -89,6 +89,17 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     return cudaGetLastError();
 }
 
+cudaError_t launch_sort(const SimConst &c, cudaStream_t s)
+{
+    const int nb = blocks_for(c.n, 256);
+    k_hash<<<nb, kTile, 0, s>>>(c);
+    k_scan_tiles<<<c.n_scan_tiles, kTile, 0, s>>>(c);
+    k_scan_apply<<<c.n_scan_tiles, kTile, 0, s>>>(c);
+    k_scatter<<<nb, kTile, 0, s>>>(c);
+    k_rank_gather<<<nb, kTile, 0, s>>>(c);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cycle_end(const SimConst &c, cudaStream_t s)
 {
     k_cycle_end<<<1, 1, 0, s>>>(c);

@@ -33,7 +33,8 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_batch_destroy", "sph_batch_test_barrier", "sph_get_descriptor",
            "sph_mlp_param_count", "sph_mlp_workspace_bytes", "sph_mlp_create", "sph_mlp_set_params",
            "sph_mlp_get_params", "sph_mlp_forward", "sph_mlp_gradients", "sph_mlp_train_step",
-           "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc"]
+           "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc",
+           "sph_iso_grid", "sph_iso_field", "sph_iso_workspace_bytes", "sph_iso_polygonize"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -163,6 +164,15 @@ def load(path: str = LIB_PATH):
     L.sph_mlp_destroy.argtypes = [_vp]
     L.sph_cell_sort_noalloc.restype = st
     L.sph_cell_sort_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.sph_iso_grid.restype = st
+    L.sph_iso_grid.argtypes = [ctypes.POINTER(Params), ctypes.c_float, _i32p, _f32p]
+    L.sph_iso_field.restype = st
+    L.sph_iso_field.argtypes = [_vp, ctypes.c_float, _vp]
+    L.sph_iso_workspace_bytes.restype = ctypes.c_size_t
+    L.sph_iso_workspace_bytes.argtypes = [_i32p]
+    L.sph_iso_polygonize.restype = st
+    L.sph_iso_polygonize.argtypes = [_vp, _i32p, _f32p, ctypes.c_float, ctypes.c_float, _vp,
+                                     ctypes.c_size_t, _vp, ctypes.c_int64, _i64p, _vp]
     L.sph_sync.restype = st
     L.sph_sync.argtypes = [_vp]
     L.sph_last_error.restype = ctypes.c_char_p
@@ -346,6 +356,22 @@ class Simulation:
     def descriptor_into(self, d_out) -> None:
         """Write the 269 surrogate inputs of the last substep into a CUDA float tensor."""
         self._check(self.L.sph_get_descriptor(self.h, d_out.data_ptr()))
+
+    def iso_field(self, cube: float):
+        """Fluid density field at the corners of the isosurface grid of edge `cube`
+        (CUDA float tensor (nz, ny, nx)); see iso_grid for the corner positions."""
+        import torch
+        dims, _ = iso_grid(self.scene.params, cube)
+        f = torch.empty((dims[2], dims[1], dims[0]), dtype=torch.float32, device=self.device)
+        self._check(self.L.sph_iso_field(self.h, ctypes.c_float(cube), f.data_ptr()))
+        torch.cuda.current_stream(self.device).wait_stream(self.stream)
+        f.record_stream(self.stream)
+        return f
+
+    def isosurface(self, cube: float, iso: float, max_tris: int = 1 << 20):
+        """Triangles (n, 3, 3) of the fluid surface phi = iso on the grid of edge `cube`."""
+        dims, origin = iso_grid(self.scene.params, cube)
+        return iso_polygonize(self.iso_field(cube), dims, origin, cube, iso, max_tris)
 
     def descriptor(self) -> np.ndarray:
         import torch
@@ -560,6 +586,44 @@ def cell_sort_noalloc(params: dict, x_dev, stream=None, out=None):
     if r != OK:
         raise SphError(r, "sph_cell_sort_noalloc failed")
     return keys[:n], order[:n], cs
+
+
+def iso_grid(params: dict, cube: float):
+    """Corner counts (nx, ny, nz) and corner (0,0,0) of the isosurface grid of edge cube."""
+    L = load()
+    P = make_params(params, 1.0)
+    dims = np.zeros(3, np.int32)
+    org = np.zeros(3, np.float32)
+    r = L.sph_iso_grid(ctypes.byref(P), ctypes.c_float(cube), _ptr(dims, ctypes.c_int32),
+                       _ptr(org, ctypes.c_float))
+    if r != OK:
+        raise SphError(r, "sph_iso_grid failed")
+    return [int(d) for d in dims], org
+
+
+def iso_polygonize(field_dev, dims, origin, cube: float, iso: float, max_tris: int = 1 << 20,
+                   stream=None):
+    """Marching cubes over a CUDA float field (nz, ny, nx); returns the triangles as a CUDA
+    tensor (n, 3, 3).  Raises SphError(ERR_CAPACITY) when there are more than max_tris."""
+    import torch
+    L = load()
+    field_dev = field_dev.contiguous()
+    d = np.asarray(dims, np.int32)
+    o = np.asarray(origin, np.float32)
+    nbytes = L.sph_iso_workspace_bytes(_ptr(d, ctypes.c_int32))
+    if nbytes == 0:
+        raise SphError(ERR_ARG, "invalid isosurface grid")
+    ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=field_dev.device)
+    off = (-ws.data_ptr()) % 256
+    tris = torch.empty((max(max_tris, 1), 3, 3), dtype=torch.float32, device=field_dev.device)
+    n = np.zeros(1, np.int64)
+    st = stream if stream is not None else torch.cuda.current_stream(field_dev.device)
+    r = L.sph_iso_polygonize(field_dev.data_ptr(), _ptr(d, ctypes.c_int32), _ptr(o, ctypes.c_float),
+                             ctypes.c_float(cube), ctypes.c_float(iso), ws.data_ptr() + off, nbytes,
+                             tris.data_ptr(), int(max_tris), _ptr(n, ctypes.c_int64), st.cuda_stream)
+    if r != OK:
+        raise SphError(r, f"sph_iso_polygonize failed ({int(n[0])} triangles)")
+    return tris[:int(n[0])]
 
 
 def grid_dims(params: dict):

@@ -132,6 +132,23 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x: float, device: str = "cuda") -> float:
+    """The largest of each rank's x (the job's time is its slowest rank's); x itself when
+    no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _workload(name):
     from paper_2511_15908_gb300 import scenes
     if name == "coupled":
@@ -160,6 +177,19 @@ def _reference_sample(seed=0):
                           n_substeps=16)
 
 
+def _workload_name(name, sc):
+    return (f"{name} scene: {sc.n_fluid} fluid + {sc.n_total - sc.n_fluid} boundary/soft "
+            f"particles, dt {sc.params['dt']}")
+
+
+def _reference_config(args):
+    """The same workload line as the CUDA arm's; the oracle times a bounded sample of it."""
+    full = _workload(args.workload)
+    return {"workload": _workload_name(args.workload, full), "particles_all": full.n_total,
+            "particles_fluid": full.n_fluid, "parallelism": "host cores (oracle)",
+            "sample": "250k-fluid slab of the same tank (same spacing, probe, soft cube)"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands, on this host's cores."""
     world, rank, _ = _dist()
@@ -181,8 +211,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "coupled scene sample: 250k fluid slab of the 1M tank, "
-                                   "FP64 uniform-grid oracle", "particles": sc.n_total},
+            "config": _reference_config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} substeps of a 250k-fluid slab "
                                        f"({sc.n_total} particles) of the coupled scene"},
@@ -452,13 +481,10 @@ def run_ours(args):
         torch.cuda.synchronize()
     _reported(sim.sync, domain, sph)
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
-    total_s = float(step_ms.sum()) / 1e3
+    total_s = max_over_ranks(float(step_ms.sum()) / 1e3)
     if world > 1:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
         torch.distributed.barrier()
-    value = world * sc.n_fluid * args.steps / total_s
+    value = job_rate(sc.n_fluid * args.steps, world, total_s)
     ms_per_step = 1e3 * total_s / args.steps
 
     kmean = ktimes.mean(axis=0)
@@ -504,7 +530,8 @@ def run_ours(args):
         sim.step(1)
         w = _reported(sim.grab_wrench, domain, sph)
         e2e_s += time.perf_counter() - t0
-    e2e_value = world * sc.n_fluid * args.steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s)
+    e2e_value = job_rate(sc.n_fluid * args.steps, world, e2e_s)
     sim.close()
 
     # CPU baseline (rank 0, N = 1), after every GPU timing so that the host's OpenMP
@@ -542,9 +569,7 @@ def run_ours(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32 (f64 wrench/momentum reductions)", "data": "synthetic",
-                "config": {"workload": f"{args.workload} scene: {sc.n_fluid} fluid + "
-                                       f"{n_all - sc.n_fluid} boundary/soft particles, dt "
-                                       f"{sc.params['dt']}", "particles_all": n_all,
+                "config": {"workload": _workload_name(args.workload, sc), "particles_all": n_all,
                            "particles_fluid": sc.n_fluid, "l2": "flushed between steps",
                            "parallelism": f"replicas x{world}",
                            "all_particle_steps_per_s": value * n_all / sc.n_fluid,

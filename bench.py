@@ -293,12 +293,12 @@ def batched_form(args, flush_l2_factory):
     return out
 
 
-def tait_variant(args, sc, flush_l2_factory):
-    """The Tait equation of state (Sec. 3.1's named alternative) on the same workload:
-    ms per substep and the density pass, timed like the plain path."""
+def variant_form(args, sc, flush_l2_factory, flag, what):
+    """A variant of the method (a flag) on the same workload: ms per substep and the density
+    and force passes, timed like the plain path."""
     import torch
     from paper_2511_15908_gb300 import sph
-    sim = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_TAIT)
+    sim = sph.Simulation(sc, flags=sc.params["flags"] | flag)
     sim.set_profiling(True)
     flush = flush_l2_factory(sim.stream)
     domain = [0]
@@ -323,7 +323,7 @@ def tait_variant(args, sc, flush_l2_factory):
     return {"ms_per_substep": ms, "value": sc.n_fluid / (ms / 1e3), "unit": UNIT,
             "density_ms": float(km[sph.KERNELS.index("density")]),
             "force_ms": float(km[sph.KERNELS.index("force")]), "out_of_domain_reports": domain[0],
-            "what": "same workload with SPH_FLAG_TAIT (p = B((rho/rho0)^7 - 1), B = k rho0 / 7)"}
+            "what": what}
 
 
 def isosurface_form(args, sc):
@@ -561,7 +561,14 @@ def run_ours(args):
             return f
         forms["batched"] = batched_form(args, factory)
         forms["surrogate"] = surrogate_form(args)
-        forms["tait_eos"] = tait_variant(args, sc, factory)
+        from paper_2511_15908_gb300 import sph as _sph
+        forms["tait_eos"] = variant_form(
+            args, sc, factory, _sph.FLAG_TAIT,
+            "same workload with SPH_FLAG_TAIT (p = B((rho/rho0)^7 - 1), B = k rho0 / 7)")
+        forms["volume_boundary"] = variant_form(
+            args, sc, factory, _sph.FLAG_VOLUME_BOUNDARY,
+            "same workload with SPH_FLAG_VOLUME_BOUNDARY (boundary weights psi = rho0 / "
+            "sum_boundary W; the density interval includes the psi pass)")
         forms["isosurface"] = isosurface_form(args, sc)
 
     if rank == 0:

@@ -59,10 +59,20 @@ enum {
                                           counts and static-body wrenches (test hook) */
     SPH_FLAG_NO_GRAPH = 1u << 2,       /* launch kernels directly instead of replaying a
                                           captured CUDA graph */
-    SPH_FLAG_TAIT = 1u << 3            /* Tait variation of the equation of state, which
+    SPH_FLAG_TAIT = 1u << 3,           /* Tait variation of the equation of state, which
                                           Sec. 3.1 names as the alternative to Eq. pressure:
                                           p = B ((rho / rho0)^7 - 1), B = k rho0 / 7 (the
                                           same slope as k (rho - rho0) at rest) */
+    SPH_FLAG_VOLUME_BOUNDARY = 1u << 4 /* volume-based boundary particles (Akinci et al., whose
+                                          coupling Sec. 2.1 cites): a static or rigid
+                                          particle b weighs psi_b = rho0 / sum_{k boundary}
+                                          W_bk instead of its mass in the density of fluid
+                                          and soft particles; a fluid or soft particle i
+                                          feels psi_b (-p_i / rho_i^2 + viscosity with
+                                          rho_bar = rho_i) grad W from b and b the opposite
+                                          force; boundary particles exert no SPH force on
+                                          each other; sph_get_state reports psi_b as a
+                                          boundary particle's density */
 };
 
 /* Body kinds (Sec. 3.2 particle types). */

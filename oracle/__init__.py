@@ -25,6 +25,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 KIND_STATIC, KIND_RIGID, KIND_SOFT = 1, 2, 3
 CLAMP_PRESSURE = 1
 TAIT = 8
+VOLUME_BOUNDARY = 16
 
 
 def build(force: bool = False) -> str:
@@ -124,7 +125,7 @@ def params(p: dict) -> Params:
         P.hi[a] = p["hi"][a]
     P.dt, P.visc_eps, P.spring_zeta = _f32(p["dt"]), _f32(p["visc_eps"]), _f32(p["spring_zeta"])
     P.cell = p["cell"]
-    P.flags = int(p["flags"]) & (CLAMP_PRESSURE | TAIT)
+    P.flags = int(p["flags"]) & (CLAMP_PRESSURE | TAIT | VOLUME_BOUNDARY)
     return P
 
 

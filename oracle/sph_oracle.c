@@ -35,6 +35,13 @@
  *   - the Tait variation of the equation of state (named in Sec. 3.1, form not given) is
  *     the weakly compressible form p = B ((rho / rho_0)^gamma - 1), gamma = 7, with
  *     B = k rho_0 / gamma so that dp/drho at rest equals the linear form's k;
+ *   - the volume-based boundary variant (Akinci et al., cited in Sec. 2.1; the flag
+ *     ORC_VOLUME_BOUNDARY): each static or rigid particle b carries the weight
+ *     psi_b = rho_0 / sum_{k boundary} W_bk (self included) in place of its mass in the
+ *     density of fluid and soft particles; a fluid or soft particle i feels
+ *     psi_b (-p_i / rho_i^2 + viscosity with rho_bar = rho_i) grad W from b, b feels the
+ *     opposite force, and two boundary particles exert no SPH force on each other;
+ *     the density reported for a boundary particle is its psi_b;
  *   - the grab wrench is the sum of pair forces on the body's particles (gravity
  *     excluded) with torque about the grab point; rigid bodies are updated every
  *     substep.
@@ -50,6 +57,7 @@
 
 #define ORC_CLAMP_PRESSURE 1
 #define ORC_TAIT 8
+#define ORC_VOLUME_BOUNDARY 16
 #define ORC_TAIT_GAMMA 7.0
 
 #define ORC_PI 3.14159265358979323846
@@ -297,6 +305,8 @@ void orc_soft_setup(int n_springs, const int *pairs, const float *rest_xyz, doub
 typedef struct {
     const orc_params *P;
     const double *xd, *vd, *m, *rho, *pres;
+    const double *psi;          /* volume-boundary weights (NULL: mass-based boundaries) */
+    int weight_boundary;        /* density: weigh boundary neighbours by psi */
     const int *body_of;         /* sorted slot -> body index or -1 (fluid) */
     const int *kind_of;         /* sorted slot -> kind (0 fluid) */
     double h;
@@ -311,8 +321,20 @@ static void visit_density(int p, int q, void *vctx)
     double d0 = c->xd[3 * p] - c->xd[3 * q], d1 = c->xd[3 * p + 1] - c->xd[3 * q + 1];
     double d2 = c->xd[3 * p + 2] - c->xd[3 * q + 2];
     double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-    c->rho_sum += c->m[q] * orc_W(r, c->h);
+    int qb = c->kind_of && (c->kind_of[q] == ORC_STATIC || c->kind_of[q] == ORC_RIGID);
+    c->rho_sum += (c->weight_boundary && qb ? c->psi[q] : c->m[q]) * orc_W(r, c->h);
     c->count++;
+}
+
+/* Volume-boundary weight sum: W to every boundary neighbour (the self term is added by
+ * the caller). */
+static void visit_boundary_sum(int p, int q, void *vctx)
+{
+    orc_pair_ctx *c = (orc_pair_ctx *)vctx;
+    if (!(c->kind_of[q] == ORC_STATIC || c->kind_of[q] == ORC_RIGID)) return;
+    double d0 = c->xd[3 * p] - c->xd[3 * q], d1 = c->xd[3 * p + 1] - c->xd[3 * q + 1];
+    double d2 = c->xd[3 * p + 2] - c->xd[3 * q + 2];
+    c->rho_sum += orc_W(sqrt(d0 * d0 + d1 * d1 + d2 * d2), c->h);
 }
 
 /* Pair force on p from q divided by m_p (pressure and viscosity of Alg. 1). */
@@ -332,12 +354,25 @@ static void visit_force(int p, int q, void *vctx)
     double r = sqrt(r2);
     double gw = orc_gradW_coef(r, c->h);             /* grad_p W = gw * x */
     double rp = c->rho[p], rq = c->rho[q];
-    double fp = -c->m[q] * (c->pres[p] / (rp * rp) + c->pres[q] / (rq * rq));
     double vx = v[0] * x[0] + v[1] * x[1] + v[2] * x[2];
-    double fv = 2.0 * (3 + 2) * P->nu * c->m[q] * (2.0 / (rp + rq)) * vx
-                / (r2 + P->visc_eps * c->h * c->h);
+    double fp, fv;
+    int pb = kp == ORC_STATIC || kp == ORC_RIGID;
+    int qb = c->kind_of[q] == ORC_STATIC || c->kind_of[q] == ORC_RIGID;
+    if (c->psi && (pb || qb)) {
+        /* volume-based boundary: the fluid side's own pressure and density only */
+        if (pb && qb) return;
+        double rf = pb ? rq : rp, pf = pb ? c->pres[q] : c->pres[p];
+        double w = pb ? c->m[q] * c->psi[p] / c->m[p] : c->psi[q];
+        fp = -w * pf / (rf * rf);
+        fv = 2.0 * (3 + 2) * P->nu * w * (1.0 / rf) * vx / (r2 + P->visc_eps * c->h * c->h);
+        c->gabs += w * fabs(gw) * r;
+    } else {
+        fp = -c->m[q] * (c->pres[p] / (rp * rp) + c->pres[q] / (rq * rq));
+        fv = 2.0 * (3 + 2) * P->nu * c->m[q] * (2.0 / (rp + rq)) * vx
+             / (r2 + P->visc_eps * c->h * c->h);
+        c->gabs += c->m[q] * fabs(gw) * r;
+    }
     for (int a = 0; a < 3; ++a) c->acc[a] += (fp + fv) * gw * x[a];
-    c->gabs += c->m[q] * fabs(gw) * r;
     c->fabs_sum += fabs(fp + fv) * fabs(gw) * r;
     c->count++;
 }
@@ -437,16 +472,38 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
 
     orc_nbrs N = { mode, n, { dims[0], dims[1], dims[2] }, xs, ks, cs, orc_support2(P), orc_span(P) };
 
+    /* volume-based boundaries: psi_b = rho_0 / sum_{k boundary} W_bk (self included) */
+    const int vol = (P->flags & ORC_VOLUME_BOUNDARY) != 0;
+    double *psi = vol ? (double *)calloc((size_t)n, sizeof(double)) : NULL;
+    if (vol) {
+#pragma omp parallel for schedule(dynamic, 256) if (n > 4096)
+        for (int p = 0; p < n; ++p) {
+            if (!(kind_of[p] == ORC_STATIC || kind_of[p] == ORC_RIGID)) continue;
+            orc_pair_ctx c;
+            memset(&c, 0, sizeof c);
+            c.xd = xd; c.h = h; c.kind_of = kind_of;
+            c.rho_sum = orc_W(0.0, h);
+            orc_for_neighbours(&N, p, visit_boundary_sum, &c);
+            psi[p] = P->rho0 / c.rho_sum;
+        }
+    }
+
     /* a6: density (Eq. density, self term included) and pressure (Eq. pressure). */
 #pragma omp parallel for schedule(dynamic, 256) if (n > 4096)
     for (int p = 0; p < n; ++p) {
         orc_pair_ctx c;
         memset(&c, 0, sizeof c);
         c.xd = xd; c.m = ms; c.h = h;
+        c.kind_of = kind_of; c.psi = psi; c.weight_boundary = vol;
         c.rho_sum = ms[p] * orc_W(0.0, h);
         orc_for_neighbours(&N, p, visit_density, &c);
         rho[p] = c.rho_sum;
         nnbr[p] = c.count;
+        if (vol && (kind_of[p] == ORC_STATIC || kind_of[p] == ORC_RIGID)) {
+            rho[p] = psi[p];                   /* reported in place of a density */
+            pres[p] = 0.0;
+            continue;
+        }
         double pr = P->k * (c.rho_sum - P->rho0);
         if (P->flags & ORC_TAIT)
             pr = P->k * P->rho0 / ORC_TAIT_GAMMA * (pow(c.rho_sum / P->rho0, ORC_TAIT_GAMMA) - 1.0);
@@ -484,7 +541,7 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
         orc_pair_ctx c;
         memset(&c, 0, sizeof c);
         c.P = P; c.xd = xd; c.vd = vd; c.m = ms; c.rho = rho; c.pres = pres;
-        c.body_of = body_of; c.kind_of = kind_of; c.h = h;
+        c.body_of = body_of; c.kind_of = kind_of; c.h = h; c.psi = psi;
         orc_for_neighbours(&N, p, visit_force, &c);
         if (cond) { cond[2 * p] = c.gabs; cond[2 * p + 1] = c.fabs_sum; }
         int kp = kind_of[p];
@@ -604,6 +661,7 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
     }
 
     free(Rf); free(fs); free(xf); free(vcur); free(body_of_id); free(key); free(cs); free(src);
+    free(psi);
     free(xs); free(xd); free(vd); free(ms); free(ks); free(ids); free(body_of); free(kind_of);
     free(slot_of_id);
     return clamped;

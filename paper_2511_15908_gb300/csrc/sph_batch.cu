@@ -19,7 +19,8 @@
 
 namespace sphgb {
 
-enum Phase { P_HASH, P_SCAN_T, P_SCAN_A, P_SCATTER, P_GATHER, P_DENSITY, P_FORCE, P_WRENCH, kPhases };
+enum Phase { P_HASH, P_SCAN_T, P_SCAN_A, P_SCATTER, P_GATHER, P_VOLUME, P_DENSITY, P_FORCE, P_WRENCH,
+             kPhases };
 
 constexpr unsigned kBarrierSpin = 1u << 22;   // x 64 ns sleep: the barrier gives up after ~0.3 s
 
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
                     case P_SCAN_A: scan_apply_item(c, blk); break;
                     case P_SCATTER: scatter_item(c, blk); break;
                     case P_GATHER: rank_gather_item(c, blk); break;
+                    case P_VOLUME: boundary_volume_item(c, blk); break;
                     case P_DENSITY: density_item(c, blk); break;
                     case P_FORCE: force_item(c, blk); break;
                     default: wrench_item(c, blk); break;
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(kTile) k_batch_phase(BatchConst b)
     case P_SCAN_A: scan_apply_item(c, blk); break;
     case P_SCATTER: scatter_item(c, blk); break;
     case P_GATHER: rank_gather_item(c, blk); break;
+    case P_VOLUME: boundary_volume_item(c, blk); break;
     case P_DENSITY: density_item(c, blk); break;
     case P_FORCE: force_item(c, blk); break;
     default: wrench_item(c, blk); break;
@@ -241,6 +244,7 @@ cudaError_t launch_phases(sph_batch *b, int n_substeps, int cycle_end)
         if (bc.total[P_SCAN_A]) k_batch_phase<P_SCAN_A><<<bc.total[P_SCAN_A], kTile, 0, b->stream>>>(bc);
         if (bc.total[P_SCATTER]) k_batch_phase<P_SCATTER><<<bc.total[P_SCATTER], kTile, 0, b->stream>>>(bc);
         if (bc.total[P_GATHER]) k_batch_phase<P_GATHER><<<bc.total[P_GATHER], kTile, 0, b->stream>>>(bc);
+        if (bc.total[P_VOLUME]) k_batch_phase<P_VOLUME><<<bc.total[P_VOLUME], kTile, 0, b->stream>>>(bc);
         if (bc.total[P_DENSITY]) k_batch_phase<P_DENSITY><<<bc.total[P_DENSITY], kTile, 0, b->stream>>>(bc);
         if (bc.total[P_FORCE]) k_batch_phase<P_FORCE><<<bc.total[P_FORCE], kTile, 0, b->stream>>>(bc);
         if (bc.total[P_WRENCH]) k_batch_phase<P_WRENCH><<<bc.total[P_WRENCH], kTile, 0, b->stream>>>(bc);
@@ -349,7 +353,9 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
             prefix[(size_t)ph * (n_scenes + 1) + s] = run;
             const SimConst &c = table[s];
             int tiles = (ph == P_SCAN_T || ph == P_SCAN_A) ? c.n_scan_tiles
-                        : (ph == P_WRENCH) ? c.n_wgrid : (c.n + kTile - 1) / kTile;
+                        : (ph == P_WRENCH) ? c.n_wgrid
+                        : (ph == P_VOLUME && !(c.flags & FLAG_VOLUME)) ? 0
+                        : (c.n + kTile - 1) / kTile;
             run += tiles;
         }
         prefix[(size_t)ph * (n_scenes + 1) + n_scenes] = run;

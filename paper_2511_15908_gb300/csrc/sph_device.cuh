@@ -31,7 +31,7 @@ constexpr int kTile = 256;     // threads per block = particles per tile
 
 
 constexpr int KIND_STATIC = 1, KIND_RIGID = 2, KIND_SOFT = 3;
-constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u, FLAG_TAIT = 8u;
+constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u, FLAG_TAIT = 8u, FLAG_VOLUME = 16u;
 
 // ------------------------------------------------------------------ small helpers
 
@@ -380,6 +380,11 @@ struct DensitySum {
     int cnt = 0;
     __device__ __forceinline__ void add(const SimConst &c, float4 xj, float r2)
     {
+        add_m(c, fabsf(xj.w), r2);
+    }
+    // the same with the neighbour's weight given (its mass, or a boundary volume weight)
+    __device__ __forceinline__ void add_m(const SimConst &c, float mj, float r2)
+    {
         // sqrt: rsqrt + one Newton step (~1 ulp); r2 = 0 (the particle itself) gives r = 0
         float rs = rsqrtf(fmaxf(r2, 1e-30f));
         float r = r2 * rs;
@@ -390,7 +395,7 @@ struct DensitySum {
         float t = 2.0f - s, u1 = 1.0f - s;
         float w6 = t * t * t;
         if (s < 1.0f) w6 = __fmaf_rn(-4.0f * u1, u1 * u1, w6);
-        float y = __fsub_rn(fabsf(xj.w) * w6, C);
+        float y = __fsub_rn(mj * w6, C);
         float u = __fadd_rn(S, y);
         C = __fsub_rn(__fsub_rn(u, S), y);
         S = u;
@@ -451,6 +456,10 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     int kind = 0, excl_lo = 0, excl_n = 0;
     if (xi.w < 0.0f) pair_scope(c, __float_as_int(c.vA[p].w), kind, excl_lo, excl_n);
     const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
+    // volume-based boundaries: boundary neighbours weigh psi (in their (rho, P) slot) and
+    // a boundary particle interacts with none of them
+    const bool vol = (c.flags & FLAG_VOLUME) != 0;
+    const bool vol_boundary = vol && xi.w < 0.0f;
     const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
     DensitySum acc;
     acc.add(c, xi, 0.0f);                               // self term
@@ -476,7 +485,14 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
                 mm &= mm - 1u;
                 const float4 xj = __ldg(c.xA + q);
                 float dx, dy, dz;
-                acc.add(c, xj, dist2(xi, xj, dx, dy, dz));
+                const float r2 = dist2(xi, xj, dx, dy, dz);
+                if (vol && xj.w < 0.0f) {
+                    if (!vol_boundary) acc.add_m(c, __ldg(&c.prho[q].x), r2);
+                    else ++acc.cnt;
+                    if (vol_boundary) continue;
+                } else {
+                    acc.add(c, xj, r2);
+                }
                 if (!keep_list) continue;
                 if (excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) <
                                   (unsigned)excl_n)
@@ -501,8 +517,35 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
         pr = c.k * drho;
     }
     if ((c.flags & FLAG_CLAMP) && pr < 0.0f) pr = 0.0f;
-    c.prho[p] = make_float2(rho, pr / (rho * rho));
+    if (!vol_boundary) c.prho[p] = make_float2(rho, pr / (rho * rho));   // else psi stays
     if (c.flags & FLAG_RECORD) c.nnbr[p] = acc.cnt - 1;
+    report(c, bad);
+}
+
+// Volume-based boundaries (Akinci et al.): each static or rigid particle's weight
+// psi_b = rho0 / sum_{k boundary} W_bk (self included), stored in its (rho, P) slot as
+// (psi_b, 0) before the density pass reads it.
+__device__ __forceinline__ void boundary_volume_item(const SimConst &c, int blk)
+{
+    const int p = blk * kTile + threadIdx.x;
+    if (p >= c.n) return;
+    const float4 xi = c.xA[p];
+    if (!(xi.w < 0.0f)) return;
+    DensitySum acc;
+    acc.add_m(c, 1.0f, 0.0f);                            // self
+    uint32_t bad = 0;
+    for_each_row(c, xi, bad, [&](int s0, int e0) {
+        for (int q = s0; q < e0; ++q) {
+            const float4 xj = __ldg(c.xA + q);
+            if (q == p || !(xj.w < 0.0f)) continue;
+            float dx, dy, dz;
+            const float r2 = dist2(xi, xj, dx, dy, dz);
+            if (r2 < c.R2) acc.add_m(c, 1.0f, r2);
+        }
+    });
+    // sum W = alpha6 (S - C), alpha6 = hi + lo
+    const float sumW = __fmaf_rn(c.alpha6_hi, acc.S, __fmaf_rn(c.alpha6_lo, acc.S, -c.alpha6_hi * acc.C));
+    c.prho[p] = make_float2(c.rho0 / sumW, 0.0f);
     report(c, bad);
 }
 
@@ -526,6 +569,8 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
         int kind, excl_lo, excl_n;
         pair_scope(c, id, kind, excl_lo, excl_n);
         const bool skip = (kind == KIND_STATIC) && !(c.flags & FLAG_RECORD);
+        const bool vol = (c.flags & FLAG_VOLUME) != 0;
+        const float inv_mi = 1.0f / mi;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
         if (!skip) {
             auto pair = [&](int q, float4 xj, float dx, float dy, float dz, float r2) {
@@ -533,6 +578,8 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
                 int jd = __float_as_int(vj.w);
                 if ((unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
                 float2 pj = __ldg(c.prho + q);
+                const bool bi = xi.w < 0.0f, bj = xj.w < 0.0f;
+                if (vol && bi && bj) return;       // volume boundaries: no boundary pairs
                 float rinv = 0.0f;                 // coincident particles: no force
                 if (r2 > 0.0f) {
                     rinv = rsqrtf(r2);
@@ -545,8 +592,18 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
                 float gq = s < 1.0f ? (-2.0f + 1.5f * s) : (-0.5f * t * t * c.h * rinv);
                 // v_ij . x_ij with x_ij = -d
                 float vx = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
-                float visc = __fdividef(c.nu20 * vx, (pi.x + pj.x) * (r2 + c.eps_h2));
-                float coef = fabsf(xj.w) * (visc - (pi.y + pj.y)) * gq;
+                float coef;
+                if (vol && (bi || bj)) {
+                    // the fluid side's density and pressure only; the boundary side
+                    // weighs psi (its (rho, P) slot holds (psi, 0))
+                    const float rf = bi ? pj.x : pi.x, Pf = bi ? pj.y : pi.y;
+                    const float w = bi ? fabsf(xj.w) * pi.x * inv_mi : pj.x;
+                    const float visc = __fdividef(c.nu20 * vx, (rf + rf) * (r2 + c.eps_h2));
+                    coef = w * (visc - Pf) * gq;
+                } else {
+                    float visc = __fdividef(c.nu20 * vx, (pi.x + pj.x) * (r2 + c.eps_h2));
+                    coef = fabsf(xj.w) * (visc - (pi.y + pj.y)) * gq;
+                }
                 ax -= coef * dx;
                 ay -= coef * dy;
                 az -= coef * dz;

@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(kTile) k_scan_apply(SimConst c) { scan_apply_i
 __global__ void __launch_bounds__(kTile) k_scatter(SimConst c) { scatter_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_rank_gather(SimConst c) { rank_gather_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile, SPH_DENSITY_MINB) k_density(SimConst c) { density_item(c, blockIdx.x); }
+__global__ void __launch_bounds__(kTile) k_boundary_volume(SimConst c) { boundary_volume_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force(SimConst c) { force_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_wrench(SimConst c) { wrench_item(c, blockIdx.x); }
 __global__ void k_cycle_end(SimConst c) { cycle_end_item(c); }
@@ -80,6 +81,8 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     mark();
     k_rank_gather<<<nb, kTile, 0, s>>>(c);
     mark();
+    // volume-based boundaries: their weights first (timed with the density pass)
+    if (c.flags & FLAG_VOLUME) k_boundary_volume<<<nb, kTile, 0, s>>>(c);
     k_density<<<nb, kTile, 0, s>>>(c);
     mark();
     k_force<<<c.n_force_blocks, kTile, 0, s>>>(c);

@@ -38,6 +38,7 @@ KIND_SOFT = 3
 FLAG_CLAMP_PRESSURE = 1 << 0   # negative pressures are clamped to zero
 FLAG_RECORD = 1 << 1           # keep per-particle acceleration and neighbour counts
 FLAG_TAIT = 1 << 3             # Tait equation of state instead of the linear one
+FLAG_VOLUME_BOUNDARY = 1 << 4  # boundary particles weighted by volume (psi) instead of mass
 
 
 @dataclass

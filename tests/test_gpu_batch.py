@@ -65,6 +65,28 @@ def test_batched_substeps_bit_identical_to_single_scene(sph):
     batch.close()
 
 
+def test_batched_volume_boundaries_bit_identical_and_mixed(sph):
+    # the boundary-volume phase runs only for scenes that set the flag; a batch mixing
+    # both kinds must step each scene exactly as it steps alone, in both launch structures
+    scs = _scene_set()[3:6]
+    for i in (0, 2):
+        scs[i].params = dict(scs[i].params, flags=scs[i].params["flags"] | scenes.FLAG_VOLUME_BOUNDARY)
+    solo = [sph.Simulation(sc) for sc in scs]
+    for s in solo:
+        s.step(4)
+    for bps in (0, 1):
+        bsims = [sph.Simulation(sc) for sc in scs]
+        batch = sph.Batch(bsims)
+        batch.configure(bps, 1)
+        batch.step(4)
+        batch.sync()
+        for a, b in zip(solo, bsims):
+            xa, va, ra, ba, _ = _snapshot(a)
+            xb, vb, rb, bb, _ = _snapshot(b)
+            assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
+        batch.close()
+
+
 def test_batched_one_substep_matches_oracle(sph):
     # the parity checks of the plain path, with the substep run by the batched launch
     scs = _scene_set()[3:6]

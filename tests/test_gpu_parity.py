@@ -193,6 +193,27 @@ def test_tait_eos_coupled_reduced(sph):
     check_one_substep(sph, sc, mode=1)
 
 
+def test_volume_boundaries_dam_break_grabbed_cube(sph):
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=3, grab=True, cube_pos=(0.4, 0.4, 0.2)),
+                                    seed=13, sigma=0.3)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_VOLUME_BOUNDARY)
+    check_one_substep(sph, sc, mode=0)
+
+
+def test_volume_boundaries_coupled_reduced(sph):
+    sc = scenes.with_velocity_noise(
+        scenes.coupled(seed=3, n_fluid=60_000, cols=(60, 40), tank=(0.6, 0.4, 0.4), n_substeps=10,
+                       probe_r=0.04, soft_n=8), seed=14, sigma=0.2)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_VOLUME_BOUNDARY)
+    check_one_substep(sph, sc, mode=1)
+
+
+def test_volume_boundaries_full_size_bench_config(sph):
+    sc = scenes.with_velocity_noise(scenes.coupled(seed=0, n_substeps=10), seed=15, sigma=0.2)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_VOLUME_BOUNDARY)
+    check_one_substep(sph, sc, mode=1, record=False)
+
+
 @pytest.mark.parametrize("cell_over_h", [1.0, 1.37, 2.002])
 def test_cell_edges_from_h_to_2h(sph, cell_over_h):
     # the clipped row search must find every neighbour for any cell >= h; h exactly puts

@@ -460,3 +460,82 @@ def test_tait_is_convex_above_its_tangent_and_increasing():
     rho0 = float(np.float32(sc.params["rho0"]))
     B = float(np.float32(sc.params["k"])) * rho0 / 7.0
     assert tait["pres"].min() >= -B
+
+
+# ------------------------------------- volume-based boundary variant (Akinci, Sec. 2.1)
+
+def _plane_layer_scene(d_over_h, h=0.02, sb=0.01):
+    """One fluid particle at height d above a single plane layer of boundary particles
+    (spacing sb), no gravity; the layer is wide enough to cover the kernel support."""
+    p = _params(h=h, dt=1e-4, lo=(-0.3, -0.3, -0.3), hi=(0.3, 0.3, 0.3))
+    p["g"] = (0.0, 0.0, 0.0)
+    p["flags"] = scenes.FLAG_VOLUME_BOUNDARY
+    n = np.arange(-12, 13)
+    X, Y = np.meshgrid(n * sb, n * sb, indexing="ij")
+    layer = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], 1).astype(np.float32)
+    fx = np.array([[0.0, 0.0, d_over_h * h]], np.float32)
+    sc = scenes.Scene("layer", p, fx, np.zeros_like(fx), h, [scenes.Body(scenes.KIND_STATIC, layer, sb)])
+    return sc, layer
+
+
+def _plane_integral(d, h):
+    # F(d) = integral over the plane of W(sqrt(r^2 + d^2)): the kernel's mass per area
+    from scipy import integrate as it
+    f = lambda r: 2.0 * np.pi * r * oracle.W(np.sqrt(r * r + d * d), h)
+    return it.quad(f, 0.0, 2.0 * h, points=[h], epsabs=0, epsrel=1e-11)[0]
+
+
+@pytest.mark.parametrize("d_over_h", [0.0, 0.5, 1.0, 1.5])
+def test_volume_boundary_plane_layer_weights(d_over_h):
+    # psi_b = rho0 / sum_k W_bk over the layer ~ rho0 sb^2 / F(0) (a lattice Riemann sum of
+    # the plane integral), and the layer adds rho0 F(d) / F(0) to a fluid particle at
+    # height d: the layer stands in for a half-space of rest-density material
+    h, sb = 0.02, 0.01
+    sc, layer = _plane_layer_scene(d_over_h, h, sb)
+    out = oracle.System(sc, mode=0).substep()
+    ids = out["id"]
+    rho0 = float(np.float32(sc.params["rho0"]))
+    h32 = float(np.float32(h))
+    F0, Fd = _plane_integral(0.0, h32), _plane_integral(d_over_h * h32, h32)
+    centre = 1 + int(np.argmin(np.linalg.norm(layer, axis=1)))   # id of the layer's middle
+    psi_c = out["rho"][ids == centre][0]
+    assert psi_c == pytest.approx(rho0 * float(np.float32(sb)) ** 2 / F0, rel=2e-3)
+    m_f = float(oracle.particle_mass(rho0, h))
+    boundary_part = out["rho"][ids == 0][0] - m_f * oracle.W(0.0, h32)
+    assert boundary_part == pytest.approx(rho0 * Fd / F0, rel=5e-3, abs=1e-6 * rho0)
+
+
+def test_volume_boundary_pair_forces_cancel():
+    sc = _random_scene(seed=9)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_VOLUME_BOUNDARY)
+    out = oracle.System(sc, mode=0).substep()
+    diag = out["diag"]
+    assert np.linalg.norm(diag[0:3]) <= 1e-12 * diag[3]
+
+
+def test_volume_boundary_no_force_between_boundary_particles():
+    # two static bodies overlapping: with volume boundaries they exert no SPH force on each
+    # other, so with no fluid every acceleration is zero
+    h = 0.02
+    p = _params(h=h, lo=(-0.2, -0.2, -0.2), hi=(0.2, 0.2, 0.2))
+    p["flags"] = scenes.FLAG_VOLUME_BOUNDARY
+    a = (np.random.default_rng(1).uniform(-0.03, 0.03, (40, 3))).astype(np.float32)
+    b = (a + 0.004).astype(np.float32)
+    sc = scenes.Scene("bb", p, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), h,
+                      [scenes.Body(scenes.KIND_STATIC, a, h / 2), scenes.Body(scenes.KIND_STATIC, b, h / 2)])
+    out = oracle.System(sc, mode=0).substep()
+    assert np.all(out["acc"] == 0.0)
+
+
+def test_volume_boundary_hydrostatic_floor_carries_the_weight():
+    sc = scenes.column(seed=0, n=(5, 5, 16))
+    sc.params["nu"] = 5e-3
+    sc.params["flags"] = sc.params["flags"] | scenes.FLAG_VOLUME_BOUNDARY
+    s = oracle.System(sc, mode=1)
+    for _ in range(1500):
+        out = s.substep()
+    fluid = out["id"] < sc.n_fluid
+    assert np.abs(out["v_new"][fluid]).max() < 0.05
+    m_f = sc.params["rho0"] * sc.fluid_spacing ** 3
+    weight = sc.n_fluid * m_f * sc.params["g"][2]
+    assert out["wrench"][0, 2] == pytest.approx(weight, rel=0.03)

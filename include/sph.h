@@ -370,6 +370,30 @@ const char *sph_batch_last_error(const sph_batch *b);
 void sph_batch_destroy(sph_batch *b);
 
 /*
+ * Cloth anchors (Sec. 4: a soft-body cloth plane with definable anchor points).  The listed
+ * particles of soft body `body` (local indices 0..n_body-1) keep their position and stay
+ * at rest; they still exert and feel SPH and spring forces (their acceleration is reported
+ * under SPH_FLAG_RECORD).  Only before the first sph_step.  Errors: SPH_ERR_ARG,
+ * SPH_ERR_STATE.
+ */
+sph_status sph_set_anchors(sph_handle *h, int32_t body, int32_t n, const int32_t *h_local);
+
+/*
+ * Incision (Sec. 4: a scalpel cutting the skin of a soft body): every active spring of every
+ * soft body whose segment between its two particles' current positions meets the closed
+ * triangle tri (host, v0 v1 v2, 9 floats) is cut: its stiffness and damping become 0 for
+ * the rest of the run.  A stroke of the blade between two frames is two such triangles.
+ * The test is Moller and Trumbore's in FP32 (segment parameter in [0, 1]; a segment
+ * parallel to the triangle within |det| <= 1e-7 |e1|_1 |d x e2|_1 does not meet it), taken
+ * with the spring's lower particle id as the segment start.  The current state is sorted
+ * first, as the next substep's hash would (the simulation is unaffected).  *h_n_cut
+ * receives the number of springs cut by this call.  Synchronises.  Errors: SPH_ERR_ARG,
+ * SPH_ERR_CUDA and the handle's pending status.  The paper's cutting model is not given;
+ * this is the build's reading of it.
+ */
+sph_status sph_cut_springs(sph_handle *h, const float tri[9], int64_t *h_n_cut);
+
+/*
  * Isosurface of the fluid (Alg. 2's isosurface compute kernels; Sec. 3.4).  The fluid's
  * surface is the isosurface of a density field that the fluid particles generate through
  * the smoothing kernel, sampled at the corners of a uniform grid of cubes offset from the

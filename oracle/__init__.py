@@ -70,7 +70,8 @@ class BodyC(ctypes.Structure):
                 ("n_springs", ctypes.c_int), ("springs", ctypes.POINTER(ctypes.c_int)),
                 ("spring_L0", ctypes.POINTER(ctypes.c_double)),
                 ("spring_k", ctypes.POINTER(ctypes.c_double)),
-                ("spring_c", ctypes.POINTER(ctypes.c_double))]
+                ("spring_c", ctypes.POINTER(ctypes.c_double)),
+                ("anchored", ctypes.POINTER(ctypes.c_int))]
 
 
 _P = ctypes.POINTER
@@ -233,6 +234,7 @@ class System:
         self.bodies = []
         first = nf
         self._keep = []
+        self._springs = []          # (body index, pairs, k_s, c_d) of every soft body
         for b in scene.bodies:
             n = b.n
             bc = BodyC()
@@ -264,6 +266,12 @@ class System:
                 bc.spring_L0 = L0.ctypes.data_as(_P(ctypes.c_double))
                 bc.spring_k = ks.ctypes.data_as(_P(ctypes.c_double))
                 bc.spring_c = cd.ctypes.data_as(_P(ctypes.c_double))
+                self._springs.append((len(self.bodies), pairs, ks, cd))
+                if b.anchors is not None and len(b.anchors):
+                    anc = np.zeros(n, np.int32)
+                    anc[np.asarray(b.anchors)] = 1
+                    self._keep.append(anc)
+                    bc.anchored = anc.ctypes.data_as(_P(ctypes.c_int))
             xs.append(local if b.kind != KIND_RIGID else np.zeros((n, 3), np.float32))
             vs.append(np.zeros((n, 3), np.float32))
             ms.append(np.full(n, pm, np.float32))
@@ -338,6 +346,48 @@ class System:
                     bc.q[a] = st[3 + a]
         self.step_index += 1
         return out
+
+    def cut_springs(self, tri, margin: float = 1e-5):
+        """Incision: cut (k_s = c_d = 0) every active spring whose segment between its
+        particles' current positions (lower id first) meets the closed triangle tri, by
+        Moller and Trumbore's test in FP64 with the segment parameter in [0, 1] and
+        |det| <= 1e-7 |e1|_1 |d x e2|_1 counted as parallel.  Returns (number cut, per body
+        the boolean arrays cut and near -- `near`: the decision is within `margin` of one
+        of the test's bounds, where FP32 may decide otherwise)."""
+        t = np.asarray(tri, np.float64).reshape(3, 3)
+        xid = self.by_id(self.x.astype(np.float64))
+        total, out = 0, []
+        for bi, pairs, ks, cd in self._springs:
+            first = self.bodies[bi].first
+            ia = first + pairs[:, 0].astype(np.int64)
+            ib = first + pairs[:, 1].astype(np.int64)
+            lo, hi = np.minimum(ia, ib), np.maximum(ia, ib)
+            a, b = xid[lo], xid[hi]
+            e1, e2 = t[1] - t[0], t[2] - t[0]
+            d = b - a
+            pv = np.cross(d, e2)
+            det = pv @ e1
+            scale = np.abs(e1).sum() * np.abs(pv).sum(1)
+            ok = np.abs(det) > 1e-7 * scale
+            inv = np.where(ok, 1.0 / np.where(ok, det, 1.0), 0.0)
+            tv = a - t[0]
+            u = np.einsum("ij,ij->i", tv, pv) * inv
+            qv = np.cross(tv, e1)
+            v = np.einsum("ij,ij->i", d, qv) * inv
+            w = 1.0 - u - v
+            sp = (qv @ e2) * inv
+            hit = ok & (u >= 0) & (u <= 1) & (v >= 0) & (w >= 0) & (sp >= 0) & (sp <= 1)
+            active = ~((ks == 0.0) & (cd == 0.0))
+            cut = hit & active
+            near = active & ok & (np.minimum.reduce([np.abs(u), np.abs(1 - u), np.abs(v), np.abs(w),
+                                                     np.abs(sp), np.abs(1 - sp)]) < margin)
+            # the parallel threshold itself: within a factor 1.5 of it either side
+            near |= active & (np.abs(det) > 1e-7 / 1.5 * scale) & (np.abs(det) < 1.5e-7 * scale)
+            ks[cut] = 0.0
+            cd[cut] = 0.0
+            total += int(cut.sum())
+            out.append((cut, near))
+        return total, out
 
     def by_id(self, arr: np.ndarray) -> np.ndarray:
         """Reorder a per-particle array of the current (sorted) order into id order."""

@@ -77,7 +77,9 @@ typedef struct {
     const float *local;     /* n x 3: rigid body-frame offsets; static world positions */
     int n_springs;
     const int *springs;     /* n_springs x 2 local indices (soft) */
-    const double *spring_L0, *spring_k, *spring_c;   /* per spring (soft) */
+    const double *spring_L0, *spring_k, *spring_c;   /* per spring (soft); a cut spring has
+                                                        k = c = 0 and acts no more */
+    const int *anchored;        /* soft, per local particle (may be NULL): pinned at rest */
 } orc_body;
 
 /* ---------------------------------------------------------------- kernel (Eq. kernel) */
@@ -516,6 +518,7 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
     for (int b = 0; b < nb; ++b) {
         if (B[b].kind != ORC_SOFT) continue;
         for (int s = 0; s < B[b].n_springs; ++s) {
+            if (B[b].spring_k[s] == 0.0 && B[b].spring_c[s] == 0.0) continue;   /* cut */
             int pa = slot_of_id[B[b].first + B[b].springs[2 * s]];
             int pb = slot_of_id[B[b].first + B[b].springs[2 * s + 1]];
             double d[3], dv[3], L = 0.0, vd_ = 0.0;
@@ -550,7 +553,17 @@ int orc_substep(const orc_params *P, int n, int nf, const float *x, const float 
             if (kp == 0 || kp == ORC_SOFT) ap += P->g[a];
             acc[3 * p + a] = ap;
         }
-        if (kp == 0 || kp == ORC_SOFT) {
+        int pinned = 0;                  /* cloth anchor (Sec. 4): keeps its place, at rest */
+        if (kp == ORC_SOFT) {
+            const orc_body *bb = &B[body_of[p]];
+            pinned = bb->anchored && bb->anchored[ids[p] - bb->first];
+        }
+        if (pinned) {
+            for (int a = 0; a < 3; ++a) {
+                v_new[3 * p + a] = 0.0;
+                x_new[3 * p + a] = xd[3 * p + a];
+            }
+        } else if (kp == 0 || kp == ORC_SOFT) {
             for (int a = 0; a < 3; ++a) {
                 v_new[3 * p + a] = vd[3 * p + a] + acc[3 * p + a] * dt;
                 x_new[3 * p + a] = xd[3 * p + a] + v_new[3 * p + a] * dt;

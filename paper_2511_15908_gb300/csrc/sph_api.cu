@@ -24,7 +24,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layout {
     size_t xA, vA, xB, vB, prho, key, rank, perm, cnt, cell_start, tile_sum, slot_of_id, locals,
         spring_row, spring_e, fb, xb, acc_dbg, nnbr, body, path, wrench, wrench_part, wblock,
-        diag_part, diag_part2, nlist, nlist_n, diag, wlog, cyc_log, status, ctr, total;
+        diag_part, diag_part2, nlist, nlist_n, cut, diag, wlog, cyc_log, status, ctr, total;
     int dims[3], ncell, n_scan_tiles, max_wblocks, max_force_blocks, nl_cap;
 };
 
@@ -92,6 +92,7 @@ Layout make_layout(const sph_params &p, const sph_capacity &cap)
     L.nl_cap = ((cap.max_neighbours > 0 ? cap.max_neighbours : kDefaultNeighbours) + 3) & ~3;
     L.nlist = take(4 * (size_t)L.nl_cap * N);
     L.nlist_n = take(4 * N);
+    L.cut = take(16);
     L.diag = take(8 * 8);
     L.wlog = take(8 * 6 * (size_t)std::max(cap.max_path, 1));
     L.cyc_log = take(8 * 6 * (size_t)W);
@@ -731,6 +732,39 @@ sph_status sph_get_sort(sph_handle *h, uint32_t *h_keys, int32_t *h_ids, uint32_
     if (h_cell_start)
         SPH_CUDA(h, cudaMemcpyAsync(h_cell_start, h->c.cell_start, 4 * ((size_t)h->c.ncell + 1),
                                     cudaMemcpyDeviceToHost, s));
+    return read_status(h);
+}
+
+sph_status sph_set_anchors(sph_handle *h, int32_t body, int32_t n, const int32_t *h_local)
+{
+    if (!h || n < 0 || (n > 0 && !h_local)) return SPH_ERR_ARG;
+    if (h->finalized) return fail(h, SPH_ERR_STATE, "anchors can only be set before the first step");
+    if (body < 0 || body >= (int)h->bodies.size() || h->bodies[body].kind != SPH_BODY_SOFT)
+        return fail(h, SPH_ERR_ARG, "anchors need a soft body");
+    const DevBody &B = h->bodies[body];
+    for (int i = 0; i < n; ++i)
+        if (h_local[i] < 0 || h_local[i] >= B.n) return fail(h, SPH_ERR_ARG, "anchor index out of range");
+    for (int i = 0; i < n; ++i) {
+        float4 &l = h->hlocal[(size_t)(B.first - h->c.nf + h_local[i])];
+        l.w = 1.0f;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_cut_springs(sph_handle *h, const float tri[9], int64_t *h_n_cut)
+{
+    if (!h || !tri || !h_n_cut) return SPH_ERR_ARG;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(tri[i])) return fail(h, SPH_ERR_ARG, "non-finite blade");
+    sph_status st = finalize(h);
+    if (st != SPH_OK) return st;
+    unsigned *cnt = at<unsigned>(h, h->L.cut);
+    SPH_CUDA(h, cudaMemsetAsync(cnt, 0, 4, h->stream));
+    SPH_CUDA(h, launch_cut(h->c, h->stream, tri, cnt));
+    unsigned n = 0;
+    SPH_CUDA(h, cudaMemcpyAsync(&n, cnt, 4, cudaMemcpyDeviceToHost, h->stream));
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+    *h_n_cut = (int64_t)n;
     return read_status(h);
 }
 

@@ -649,10 +649,13 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
         dg[3] = sqrtf(fx * fx + fy * fy + fz * fz);
         if (kind == 0 || kind == KIND_SOFT) {
             float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            bool anchored = false;
             if (kind == KIND_SOFT) {
                 int l = id - c.nf;
+                anchored = c.locals[l].w != 0.0f;      // pinned soft particle (cloth anchor)
                 for (int e = c.spring_row[l]; e < c.spring_row[l + 1]; ++e) {
                     float4 sp = c.spring_e[e];
+                    if (sp.z == 0.0f && sp.w == 0.0f) continue;   // cut spring
                     int q = c.slot_of_id[__float_as_int(sp.x)];
                     float4 xj = c.xA[q], vj = c.vA[q];
                     float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z;
@@ -670,6 +673,10 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
             float a2 = az + sz * im + c.g[2];
             float4 vn = make_float4(vi.x + a0 * c.dt, vi.y + a1 * c.dt, vi.z + a2 * c.dt, vi.w);
             float4 xn = make_float4(xi.x + vn.x * c.dt, xi.y + vn.y * c.dt, xi.z + vn.z * c.dt, xi.w);
+            if (anchored) {                        // an anchor stays where it is, at rest
+                vn = make_float4(0.0f, 0.0f, 0.0f, vi.w);
+                xn = xi;
+            }
             if (!(isfinite(xn.x) && isfinite(xn.y) && isfinite(xn.z))) bad |= ST_NONFINITE;
             c.xB[p] = xn;
             c.vB[p] = vn;
@@ -706,6 +713,60 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
         c.diag_part[(size_t)blk * 8 + lane] = t;
+    }
+}
+
+// ------------------------------------------------------------------ spring cutting
+
+struct Blade {
+    float v[9];                // triangle corners v0, v1, v2
+};
+
+// Does segment a-b meet triangle t (closed)?  Moller and Trumbore's ray-triangle test in
+// FP32, with the segment parameter limited to [0, 1]; parallel (|det| tiny) counts as no.
+__device__ __forceinline__ bool segment_meets_triangle(float3 a, float3 b, const Blade &t)
+{
+    const float e1x = t.v[3] - t.v[0], e1y = t.v[4] - t.v[1], e1z = t.v[5] - t.v[2];
+    const float e2x = t.v[6] - t.v[0], e2y = t.v[7] - t.v[1], e2z = t.v[8] - t.v[2];
+    const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    const float px = dy * e2z - dz * e2y, py = dz * e2x - dx * e2z, pz = dx * e2y - dy * e2x;
+    const float det = e1x * px + e1y * py + e1z * pz;
+    const float scale = (fabsf(e1x) + fabsf(e1y) + fabsf(e1z)) * (fabsf(px) + fabsf(py) + fabsf(pz));
+    if (!(fabsf(det) > 1e-7f * scale)) return false;
+    const float inv = 1.0f / det;
+    const float tx = a.x - t.v[0], ty = a.y - t.v[1], tz = a.z - t.v[2];
+    const float u = (tx * px + ty * py + tz * pz) * inv;
+    if (u < 0.0f || u > 1.0f) return false;
+    const float qx = ty * e1z - tz * e1y, qy = tz * e1x - tx * e1z, qz = tx * e1y - ty * e1x;
+    const float v = (dx * qx + dy * qy + dz * qz) * inv;
+    if (v < 0.0f || u + v > 1.0f) return false;
+    const float s = (e2x * qx + e2y * qy + e2z * qz) * inv;
+    return s >= 0.0f && s <= 1.0f;
+}
+
+// Cuts (sets k_s = c_d = 0) every active spring of a soft body whose current segment meets
+// the blade.  One thread per body particle over its CSR row; both entries of a spring
+// decide on the same endpoint order (lower id first), so they agree.  Reads the sorted
+// copy of the current state (the caller sorts it first), where slot_of_id points.
+__device__ __forceinline__ void cut_item(const SimConst &c, int blk, const Blade &t, unsigned *count)
+{
+    const int l = blk * kTile + threadIdx.x;
+    if (l >= c.n - c.nf) return;
+    const int id = c.nf + l;
+    if (c.body_kind[body_of(c, id)] != KIND_SOFT) return;
+    for (int e = c.spring_row[l]; e < c.spring_row[l + 1]; ++e) {
+        float4 sp = c.spring_e[e];
+        if (sp.z == 0.0f && sp.w == 0.0f) continue;
+        const int pid = __float_as_int(sp.x);
+        const int lo = min(id, pid), hi = max(id, pid);
+        const float4 xa = c.xA[c.slot_of_id[lo]];
+        const float4 xb = c.xA[c.slot_of_id[hi]];
+        if (!segment_meets_triangle(make_float3(xa.x, xa.y, xa.z), make_float3(xb.x, xb.y, xb.z), t))
+            continue;
+        sp.z = 0.0f;
+        sp.w = 0.0f;
+        c.spring_e[e] = sp;
+        if (id == lo) atomicAdd(count, 1u);
     }
 }
 

@@ -102,6 +102,9 @@ constexpr int kSubstepKernels = 8;
 // them as graph nodes when the stream is being captured.
 cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev = nullptr,
                            bool external = false);
+// spring cutting against a blade triangle (sorts the current state first, like the next
+// substep would); count (device) += springs cut
+cudaError_t launch_cut(const SimConst &c, cudaStream_t s, const float tri[9], unsigned *count);
 // the first five substep kernels only: hash, scan, reorder of the current state
 cudaError_t launch_sort(const SimConst &c, cudaStream_t s);
 cudaError_t launch_cycle_end(const SimConst &c, cudaStream_t s);

@@ -92,6 +92,23 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(kTile) k_cut(SimConst c, Blade t, unsigned *count)
+{
+    cut_item(c, blockIdx.x, t, count);
+}
+
+cudaError_t launch_cut(const SimConst &c, cudaStream_t s, const float tri[9], unsigned *count)
+{
+    Blade t;
+    for (int i = 0; i < 9; ++i) t.v[i] = tri[i];
+    const int nbody = c.n - c.nf;
+    if (nbody <= 0) return cudaSuccess;
+    const cudaError_t e = launch_sort(c, s);          // sorted current state + slot_of_id
+    if (e != cudaSuccess) return e;
+    k_cut<<<blocks_for(nbody, 256), kTile, 0, s>>>(c, t, count);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sort(const SimConst &c, cudaStream_t s)
 {
     const int nb = blocks_for(c.n, 256);

@@ -55,6 +55,7 @@ class Body:
     young: float = 0.0
     poisson: float = 0.0
     grab_local: np.ndarray = field(default_factory=lambda: np.zeros(3, np.float32))
+    anchors: Optional[np.ndarray] = None   # soft: local indices of pinned particles
 
     @property
     def n(self) -> int:
@@ -339,6 +340,51 @@ def tiny(seed=0, n=(4, 4, 4), spacing=0.02, dt=1e-3, with_bodies=True):
     params = make_params(s, dt, (-3 * s, -3 * s, -3 * s),
                          ((n[0] + 4) * s, (n[1] + 4) * s, (n[2] + 4) * s))
     return Scene("tiny", params, fluid, v, s, bodies, grab_body=-1, n_substeps=10)
+
+
+def cloth_springs(nx, ny):
+    """Springs of an nx x ny sheet (local index j * nx + i): structural (to the next
+    particle along x and along y), shear (both diagonals of each square) and bending
+    (to the particle two steps away along x and along y)."""
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    pairs = [np.stack([idx[:, :-1].ravel(), idx[:, 1:].ravel()], 1),
+             np.stack([idx[:-1, :].ravel(), idx[1:, :].ravel()], 1),
+             np.stack([idx[:-1, :-1].ravel(), idx[1:, 1:].ravel()], 1),
+             np.stack([idx[:-1, 1:].ravel(), idx[1:, :-1].ravel()], 1),
+             np.stack([idx[:, :-2].ravel(), idx[:, 2:].ravel()], 1),
+             np.stack([idx[:-2, :].ravel(), idx[2:, :].ravel()], 1)]
+    return np.concatenate(pairs).astype(np.int32)
+
+
+def cloth_plane(nx, ny, spacing, origin, young=5e4, anchors="corners"):
+    """A horizontal soft cloth of nx x ny particles at `spacing` from `origin` (x, y, z),
+    with anchor particles at its four corners, along its two x-edges or none."""
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    xyz = np.stack([origin[0] + i.ravel() * spacing, origin[1] + j.ravel() * spacing,
+                    np.full(nx * ny, float(origin[2]))], 1).astype(np.float32)
+    if anchors == "corners":
+        anc = np.array([0, nx - 1, (ny - 1) * nx, ny * nx - 1], np.int32)
+    elif anchors == "edges":
+        anc = np.concatenate([np.arange(nx), (ny - 1) * nx + np.arange(nx)]).astype(np.int32)
+    else:
+        anc = None
+    return Body(KIND_SOFT, xyz, spacing, springs=cloth_springs(nx, ny), young=young,
+                poisson=0.3, anchors=anc)
+
+
+def cloth_bath(seed=0, n=(12, 12, 6), cloth=(16, 16), spacing=0.02, dt=5e-4, anchors="corners"):
+    """A fluid block with a cloth plane stretched just above it (anchored), a floor below."""
+    rng = np.random.default_rng(seed)
+    s = spacing
+    fluid = _jitter(rng, _lattice(n, s, (0.0, 0.0, 0.0)), s).astype(np.float32)
+    floor = _lattice((n[0] + 4, n[1] + 4, 1), s, (-2 * s, -2 * s, -1.2 * s)).astype(np.float32)
+    off = ((n[0] - cloth[0]) * s / 2, (n[1] - cloth[1]) * s / 2, (n[2] + 0.6) * s)
+    sheet = cloth_plane(cloth[0], cloth[1], s, off, anchors=anchors)
+    bodies = [Body(KIND_STATIC, floor, s), sheet]
+    params = make_params(s, dt, (-4 * s, -4 * s, -3 * s),
+                         ((n[0] + 4) * s, (n[1] + 4) * s, (n[2] + 6) * s))
+    return Scene("cloth_bath", params, fluid, np.zeros_like(fluid), s, bodies, grab_body=-1,
+                 n_substeps=10)
 
 
 def column(seed=0, n=(6, 6, 20), spacing=0.02, dt=1e-3):

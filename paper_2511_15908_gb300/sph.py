@@ -34,7 +34,8 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_mlp_param_count", "sph_mlp_workspace_bytes", "sph_mlp_create", "sph_mlp_set_params",
            "sph_mlp_get_params", "sph_mlp_forward", "sph_mlp_gradients", "sph_mlp_train_step",
            "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc",
-           "sph_iso_grid", "sph_iso_field", "sph_iso_workspace_bytes", "sph_iso_polygonize"]
+           "sph_iso_grid", "sph_iso_field", "sph_iso_workspace_bytes", "sph_iso_polygonize",
+           "sph_set_anchors", "sph_cut_springs"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -164,6 +165,10 @@ def load(path: str = LIB_PATH):
     L.sph_mlp_destroy.argtypes = [_vp]
     L.sph_cell_sort_noalloc.restype = st
     L.sph_cell_sort_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.sph_set_anchors.restype = st
+    L.sph_set_anchors.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _i32p]
+    L.sph_cut_springs.restype = st
+    L.sph_cut_springs.argtypes = [_vp, _f32p, _i64p]
     L.sph_iso_grid.restype = st
     L.sph_iso_grid.argtypes = [ctypes.POINTER(Params), ctypes.c_float, _i32p, _f32p]
     L.sph_iso_field.restype = st
@@ -245,6 +250,10 @@ class Simulation:
                 self._check(self.L.sph_add_soft(self.h, b.n, _ptr(xyz, ctypes.c_float), b.spacing,
                                                 pairs.shape[0], _ptr(pairs, ctypes.c_int32),
                                                 b.young, b.poisson, ctypes.byref(bid)))
+                if b.anchors is not None and len(b.anchors):
+                    anc = np.ascontiguousarray(b.anchors, np.int32)
+                    self._check(self.L.sph_set_anchors(self.h, bid.value, anc.shape[0],
+                                                       _ptr(anc, ctypes.c_int32)))
             else:
                 mass = b.mass if b.kind == _scenes.KIND_RIGID else 0.0
                 inertia = np.ascontiguousarray(b.inertia, np.float32).reshape(9)
@@ -356,6 +365,14 @@ class Simulation:
     def descriptor_into(self, d_out) -> None:
         """Write the 269 surrogate inputs of the last substep into a CUDA float tensor."""
         self._check(self.L.sph_get_descriptor(self.h, d_out.data_ptr()))
+
+    def cut_springs(self, tri) -> int:
+        """Cut every soft-body spring whose segment meets the triangle tri (3 x 3 corners);
+        returns how many were cut."""
+        t = np.ascontiguousarray(np.asarray(tri, np.float32).reshape(9))
+        n = np.zeros(1, np.int64)
+        self._check(self.L.sph_cut_springs(self.h, _ptr(t, ctypes.c_float), _ptr(n, ctypes.c_int64)))
+        return int(n[0])
 
     def iso_field(self, cube: float):
         """Fluid density field at the corners of the isosurface grid of edge `cube`

@@ -447,7 +447,8 @@ struct ListWriter {
 // rigid particle, other than its own body's particles) in the neighbour list the force
 // pass reads.  Static particles take no force, so they record nothing unless the debug
 // record is on.
-__device__ __forceinline__ void density_item(const SimConst &c, int blk)
+template <bool VOL>
+__device__ __forceinline__ void density_item_v(const SimConst &c, int blk)
 {
     const int p = blk * kTile + threadIdx.x;
     if (p >= c.n) return;
@@ -458,7 +459,7 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
     // volume-based boundaries: boundary neighbours weigh psi (in their (rho, P) slot) and
     // a boundary particle interacts with none of them
-    const bool vol = (c.flags & FLAG_VOLUME) != 0;
+    constexpr bool vol = VOL;
     const bool vol_boundary = vol && xi.w < 0.0f;
     const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
     DensitySum acc;
@@ -522,6 +523,14 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     report(c, bad);
 }
 
+// The volume-boundary variant is a separate instance, so the default path carries none of
+// its per-neighbour tests.
+__device__ __forceinline__ void density_item(const SimConst &c, int blk)
+{
+    if (c.flags & FLAG_VOLUME) density_item_v<true>(c, blk);
+    else density_item_v<false>(c, blk);
+}
+
 // Volume-based boundaries (Akinci et al.): each static or rigid particle's weight
 // psi_b = rho0 / sum_{k boundary} W_bk (self included), stored in its (rho, P) slot as
 // (psi_b, 0) before the density pass reads it.
@@ -551,7 +560,8 @@ __device__ __forceinline__ void boundary_volume_item(const SimConst &c, int blk)
 
 // -------------------------------------------------------------- force + integrate
 
-__device__ __forceinline__ void force_item(const SimConst &c, int blk)
+template <bool VOL>
+__device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
 {
     __shared__ double sd[8][8];
     __shared__ unsigned s_done;
@@ -569,7 +579,7 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
         int kind, excl_lo, excl_n;
         pair_scope(c, id, kind, excl_lo, excl_n);
         const bool skip = (kind == KIND_STATIC) && !(c.flags & FLAG_RECORD);
-        const bool vol = (c.flags & FLAG_VOLUME) != 0;
+        constexpr bool vol = VOL;
         const float inv_mi = 1.0f / mi;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
         if (!skip) {
@@ -714,6 +724,12 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
         c.diag_part[(size_t)blk * 8 + lane] = t;
     }
+}
+
+__device__ __forceinline__ void force_item(const SimConst &c, int blk)
+{
+    if (c.flags & FLAG_VOLUME) force_item_v<true>(c, blk);
+    else force_item_v<false>(c, blk);
 }
 
 // ------------------------------------------------------------------ spring cutting

@@ -223,7 +223,9 @@ def run_reference(args):
 
 def batched_form(args, flush_l2_factory):
     """Form (2): 64 stirring scenes of log-uniform fluid counts (8k-256k) in one persistent
-    graph-captured launch per substep, autotuned; against stepping them one by one."""
+    graph-captured launch per substep, the launch structure autotuned (persistent kernel,
+    one kernel per phase, or the scenes' own kernels as graph branches); against stepping
+    them one by one."""
     import torch
     from paper_2511_15908_gb300 import scenes, sph
     scs = scenes.batched(seed=0, n_substeps=args.steps + args.warmup + 64)
@@ -283,9 +285,12 @@ def batched_form(args, flush_l2_factory):
            "speedup_vs_one_by_one": (t_seq / k) / (t_b / args.steps),
            "autotuned": {"blocks_per_sm": bps, "tiles_per_fetch": chunk, "sms": info["sms"]},
            "grab_wrench_rel_diff_vs_single_scene": werr,
-           "gpu_launches_per_step": 8 if info["blocks_per_sm"] == 0 else 1,
-           "launch_structure": "one kernel per phase over all scenes" if info["blocks_per_sm"] == 0
-                               else "one persistent cooperative kernel"}
+           "gpu_launches_per_step": (8 if info["blocks_per_sm"] == 0 else
+                                     8 * len(scs) if info["blocks_per_sm"] < 0 else 1),
+           "launch_structure": ("one kernel per phase over all scenes" if info["blocks_per_sm"] == 0
+                                else "every scene's own kernels as branches of one graph"
+                                if info["blocks_per_sm"] < 0
+                                else "one persistent cooperative kernel")}
     for x in sims + solo + ref + chk:
         x.close()
     batch.close()

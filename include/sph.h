@@ -340,7 +340,10 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
 /* Launch structure: blocks_per_sm = 1 .. occupancy limit runs the persistent kernel with
  * that many resident blocks per SM, taking tiles_per_fetch (1 .. 64) tiles per work-queue
  * fetch; blocks_per_sm = 0 runs one kernel per phase over all scenes' tiles instead (same
- * tiles, same results; each phase at its own occupancy). */
+ * tiles, same results; each phase at its own occupancy); blocks_per_sm = -1 runs every
+ * scene's own substep kernels as parallel branches of one captured graph (16 branches,
+ * scenes dealt round-robin; same results).  tiles_per_fetch matters only for the
+ * persistent kernel.  Errors: SPH_ERR_ARG outside these ranges. */
 sph_status sph_batch_configure(sph_batch *b, int32_t blocks_per_sm, int32_t tiles_per_fetch);
 
 /* Autotuner: times substeps_per_trial substeps (after one warm-up substep) for every

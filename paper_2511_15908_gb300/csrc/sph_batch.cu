@@ -141,8 +141,14 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
 
 // Per-phase alternative: one kernel per phase whose blocks are that phase's tiles over all
 // scenes (no grid barrier; each phase keeps its own register budget and occupancy).
+// Resident blocks per SM each phase is built for.  Without a bound the density phase took
+// 64 registers (4 blocks); 5 blocks give 51 without spilling (6 spill: the scene's
+// parameters live in shared memory here), per-phase batch 4.29 -> 3.90 ms on 64 scenes.
 template <int PH>
-__global__ void __launch_bounds__(kTile) k_batch_phase(BatchConst b)
+constexpr int batch_phase_minb() { return PH == P_DENSITY ? 5 : PH == P_FORCE ? 4 : 1; }
+
+template <int PH>
+__global__ void __launch_bounds__(kTile, batch_phase_minb<PH>()) k_batch_phase(BatchConst b)
 {
     __shared__ __align__(16) SimConst s_c;
     const int *pre = b.prefix + PH * (b.n_scenes + 1);
@@ -188,13 +194,20 @@ sph_status scene_for_batch(sph_handle *h, SimConst *out);
 void scene_advanced(sph_handle *h, int n);
 }
 
+constexpr int kBranchStreams = 16;   // scene-graph structure: parallel branches
+
 struct sph_batch {
     int n = 0;
     std::vector<sph_handle *> handles;
+    std::vector<SimConst> table;         // every scene's parameters (host copy)
     char *ws = nullptr;
     cudaStream_t stream = nullptr;
     BatchConst bc;
-    int sms = 0, max_bps = 0, bps = 0;   // bps == 0: per-phase kernels instead of one launch
+    // bps > 0: the persistent kernel; 0: one kernel per phase over all scenes' tiles;
+    // -1: every scene's own substep kernels as parallel branches of one graph
+    int sms = 0, max_bps = 0, bps = 0;
+    cudaStream_t branch[kBranchStreams] = {};
+    cudaEvent_t fork = nullptr, join[kBranchStreams] = {};
     cudaGraphExec_t exec1 = nullptr, exec16 = nullptr;
     bool use_graph = true;
     std::string err;
@@ -253,8 +266,41 @@ cudaError_t launch_phases(sph_batch *b, int n_substeps, int cycle_end)
     return cudaGetLastError();
 }
 
+// Scene-graph structure: the batch stream forks into kBranchStreams streams, each scene's
+// substep kernels (the single-scene kernels, parameters in the constant bank) run on one
+// of them, and the streams join back before the cycle end.  Captured, this is one graph
+// whose branches the GPU runs side by side.
+cudaError_t launch_branches(sph_batch *b, int n_substeps, int cycle_end)
+{
+    cudaError_t e = cudaSuccess;
+    if (!b->fork) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int k = 0; e == cudaSuccess && k < kBranchStreams; ++k) {
+            e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (n_substeps > 0) {
+        e = cudaEventRecord(b->fork, b->stream);
+        for (int k = 0; e == cudaSuccess && k < kBranchStreams; ++k)
+            e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+        for (int sc = 0; e == cudaSuccess && sc < b->n; ++sc)
+            for (int i = 0; e == cudaSuccess && i < n_substeps; ++i)
+                e = launch_substep(b->table[sc], b->branch[sc % kBranchStreams]);
+        for (int k = 0; e == cudaSuccess && k < kBranchStreams; ++k) {
+            e = cudaEventRecord(b->join[k], b->branch[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[k], 0);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (cycle_end) k_batch_cycle_end<<<(b->bc.n_scenes + 127) / 128, 128, 0, b->stream>>>(b->bc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch(sph_batch *b, int n_substeps, int cycle_end)
 {
+    if (b->bps < 0) return launch_branches(b, n_substeps, cycle_end);
     if (b->bps == 0) return launch_phases(b, n_substeps, cycle_end);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(b->bps * b->sms));
@@ -339,6 +385,7 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
     sph_batch *b = new sph_batch();
     b->n = n_scenes;
     b->handles.assign(scenes, scenes + n_scenes);
+    b->table = table;
     b->ws = (char *)d_workspace;
     b->stream = (cudaStream_t)cuda_stream;
     BatchConst &bc = b->bc;
@@ -390,7 +437,7 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
 sph_status sph_batch_configure(sph_batch *b, int32_t blocks_per_sm, int32_t tiles_per_fetch)
 {
     if (!b) return SPH_ERR_ARG;
-    if (blocks_per_sm < 0 || blocks_per_sm > b->max_bps || tiles_per_fetch < 1 || tiles_per_fetch > 64)
+    if (blocks_per_sm < -1 || blocks_per_sm > b->max_bps || tiles_per_fetch < 1 || tiles_per_fetch > 64)
         return bfail(b, SPH_ERR_ARG, "geometry outside the resident limit");
     if (blocks_per_sm != b->bps || tiles_per_fetch != b->bc.chunk) drop_graphs(b);
     b->bps = blocks_per_sm;
@@ -428,8 +475,10 @@ sph_status sph_batch_tune(sph_batch *b, int32_t substeps_per_trial, int32_t out_
     float best = 1e30f;
     int best_bps = b->bps, best_chunk = b->bc.chunk;
     const int chunks[3] = {1, 2, 4};
-    for (int bps = 0; bps <= b->max_bps; ++bps)
-        for (int ci = 0; ci < (bps == 0 ? 1 : 3); ++ci) {
+    int trials = 0;
+    for (int bps = -1; bps <= b->max_bps; ++bps)
+        for (int ci = 0; ci < (bps <= 0 ? 1 : 3); ++ci) {
+            ++trials;
             sph_status st = sph_batch_configure(b, bps, chunks[ci]);
             if (st != SPH_OK) return st;
             BATCH_CUDA(b, launch_batch(b, 1, 0));          // warm-up
@@ -445,7 +494,7 @@ sph_status sph_batch_tune(sph_batch *b, int32_t substeps_per_trial, int32_t out_
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (sph_handle *h : b->handles) scene_advanced(h, (b->max_bps * 3 + 1) * (1 + substeps_per_trial));
+    for (sph_handle *h : b->handles) scene_advanced(h, trials * (1 + substeps_per_trial));
     sph_status st = sph_batch_configure(b, best_bps, best_chunk);
     if (out_choice) { out_choice[0] = best_bps; out_choice[1] = best_chunk; }
     return st;
@@ -494,6 +543,11 @@ void sph_batch_destroy(sph_batch *b)
     if (!b) return;
     cudaStreamSynchronize(b->stream);
     drop_graphs(b);
+    for (int k = 0; k < kBranchStreams; ++k) {
+        if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+        if (b->join[k]) cudaEventDestroy(b->join[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 

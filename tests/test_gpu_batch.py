@@ -42,7 +42,9 @@ def _snapshot(sim):
     return st["x"], st["v"], st["rho"], bodies, sim.diag()
 
 
-def test_batched_substeps_bit_identical_to_single_scene(sph):
+@pytest.mark.parametrize("bps", [None, -1])
+def test_batched_substeps_bit_identical_to_single_scene(sph, bps):
+    # None: the structure the batch starts with (the persistent kernel); -1: scene graph
     scs = _scene_set()
     solo = [sph.Simulation(sc) for sc in scs]
     for s in solo:
@@ -50,6 +52,8 @@ def test_batched_substeps_bit_identical_to_single_scene(sph):
         s.step(4)
     bsims = [sph.Simulation(sc) for sc in scs]
     batch = sph.Batch(bsims)
+    if bps is not None:
+        batch.configure(bps, 1)
     batch.step(3)
     batch.step(4)
     batch.sync()
@@ -74,7 +78,7 @@ def test_batched_volume_boundaries_bit_identical_and_mixed(sph):
     solo = [sph.Simulation(sc) for sc in scs]
     for s in solo:
         s.step(4)
-    for bps in (0, 1):
+    for bps in (-1, 0, 1):
         bsims = [sph.Simulation(sc) for sc in scs]
         batch = sph.Batch(bsims)
         batch.configure(bps, 1)
@@ -113,12 +117,14 @@ def test_autotuner_picks_a_valid_geometry_and_keeps_results(sph):
     batch = sph.Batch(bsims)
     max_bps = batch.info()["blocks_per_sm"]
     bps, chunk = batch.tune(substeps_per_trial=1)
-    assert 0 <= bps <= max_bps and chunk in (1, 2, 4)
+    assert -1 <= bps <= max_bps and chunk in (1, 2, 4)
     batch.step(2)
     batch.sync()
     for sc, b in zip(scs, bsims):
         a = sph.Simulation(sc)
-        for _ in range(max_bps * 3 + 1):  # warm-up + 1 timed substep per tuner candidate
+        # warm-up + 1 timed substep per tuner candidate: scene graph, per phase, and
+        # 3 fetch sizes for each persistent geometry
+        for _ in range(max_bps * 3 + 2):
             a.step(2)
         a.step(2)
         assert np.array_equal(a.state()["x"], b.state()["x"])

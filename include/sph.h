@@ -143,6 +143,10 @@ size_t sph_workspace_bytes(const sph_params *p, const sph_capacity *cap);
  *                default stream).
  *   n_fluid      fluid particles; h_xyz (n_fluid x 3, host, copied) positions,
  *                h_vel (n_fluid x 3, host, nullable -> zero) velocities.
+ * The handle allocates no device memory; it pins a small host buffer (64 + 16 + 48 x
+ * smooth_window bytes, freed by sph_destroy) through which the synchronising reads
+ * (wrenches, status) arrive in one stream synchronisation; if pinning is refused they use
+ * ordinary host copies.
  * Synchronises.  Errors: SPH_ERR_ARG, SPH_ERR_WORKSPACE, SPH_ERR_CAPACITY, SPH_ERR_CUDA.
  */
 sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_workspace,

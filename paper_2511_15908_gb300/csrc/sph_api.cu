@@ -124,6 +124,10 @@ struct sph_handle {
     cudaEvent_t ev[kSubstepKernels + 1] = {};
     int64_t substeps = 0;
     std::string err;
+    // pinned host memory for the synchronising reads (status at 0, the read's data from
+    // 64 on): the copies are truly asynchronous and one stream synchronisation ends a read
+    unsigned char *pin = nullptr;
+    size_t pin_bytes = 0;
 };
 
 namespace {
@@ -168,12 +172,9 @@ void place(const float pose[7], const float l[3], float out[3])
     }
 }
 
-sph_status read_status(sph_handle *h)
+// Turns a fetched status word into the call's result; clears it on the device if set.
+sph_status eval_status(sph_handle *h, const uint32_t st[3])
 {
-    uint32_t st[3];
-    SPH_CUDA(h, cudaMemcpyAsync(st, at<uint32_t>(h, h->L.status), 12, cudaMemcpyDeviceToHost,
-                                h->stream));
-    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
     if (st[0] == 0) return SPH_OK;
     SPH_CUDA(h, cudaMemsetAsync(at<uint32_t>(h, h->L.status), 0, 12, h->stream));
     SPH_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -190,6 +191,29 @@ sph_status read_status(sph_handle *h)
     if (st[0] & ST_TIMEOUT) return fail(h, SPH_ERR_TIMEOUT, "a bounded device wait gave up");
     return fail(h, SPH_ERR_CUDA, "unknown device status");
 }
+
+// Waits for the stream and reports the device status word; `extra`/`bytes` (device, may be
+// null) is fetched in the same synchronisation into `dst`.
+sph_status read_status_with(sph_handle *h, const void *extra, size_t bytes, void *dst)
+{
+    uint32_t st[3];
+    if (h->pin && 64 + bytes <= h->pin_bytes) {
+        if (extra) SPH_CUDA(h, cudaMemcpyAsync(h->pin + 64, extra, bytes, cudaMemcpyDeviceToHost, h->stream));
+        SPH_CUDA(h, cudaMemcpyAsync(h->pin, at<uint32_t>(h, h->L.status), 12,
+                                    cudaMemcpyDeviceToHost, h->stream));
+        SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+        if (extra) std::memcpy(dst, h->pin + 64, bytes);
+        std::memcpy(st, h->pin, 12);
+    } else {
+        if (extra) SPH_CUDA(h, cudaMemcpyAsync(dst, extra, bytes, cudaMemcpyDeviceToHost, h->stream));
+        SPH_CUDA(h, cudaMemcpyAsync(st, at<uint32_t>(h, h->L.status), 12, cudaMemcpyDeviceToHost,
+                                    h->stream));
+        SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    return eval_status(h, st);
+}
+
+sph_status read_status(sph_handle *h) { return read_status_with(h, nullptr, 0, nullptr); }
 
 sph_status finalize(sph_handle *h)
 {
@@ -390,6 +414,14 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     if (e != cudaSuccess) {
         delete h;
         return SPH_ERR_CUDA;
+    }
+    // pinned staging for the synchronising reads: status, then the counters and the
+    // smoothing window's cycle log (host memory; unpinned copies if refused)
+    h->pin_bytes = 64 + 16 + 48 * (size_t)c.smooth_window;
+    if (cudaHostAlloc((void **)&h->pin, h->pin_bytes, cudaHostAllocDefault) != cudaSuccess) {
+        h->pin = nullptr;
+        h->pin_bytes = 0;
+        cudaGetLastError();
     }
     *out = h;
     return SPH_OK;
@@ -602,8 +634,7 @@ sph_status sph_get_body_wrench(sph_handle *h, int32_t body_id, double out[6])
     if (!h || !out || body_id < 0 || body_id >= (int)h->bodies.size()) return SPH_ERR_ARG;
     sph_status st = finalize(h);
     if (st != SPH_OK) return st;
-    SPH_CUDA(h, cudaMemcpyAsync(out, h->c.wrench + 6 * body_id, 48, cudaMemcpyDeviceToHost, h->stream));
-    return read_status(h);
+    return read_status_with(h, h->c.wrench + 6 * body_id, 48, out);
 }
 
 sph_status sph_get_grab_wrench(sph_handle *h, double out[6], int32_t smoothed)
@@ -614,10 +645,21 @@ sph_status sph_get_grab_wrench(sph_handle *h, double out[6], int32_t smoothed)
     const int W = h->c.smooth_window;
     std::vector<double> log(6 * (size_t)W);
     uint32_t ctr[3];
-    SPH_CUDA(h, cudaMemcpyAsync(log.data(), h->c.cyc_log, 48 * (size_t)W, cudaMemcpyDeviceToHost,
-                                h->stream));
-    SPH_CUDA(h, cudaMemcpyAsync(ctr, h->c.ctr, 12, cudaMemcpyDeviceToHost, h->stream));
-    sph_status st = read_status(h);
+    sph_status st;
+    if (h->pin) {
+        // counters at 64, the log at 80, the status at 0: one synchronisation
+        SPH_CUDA(h, cudaMemcpyAsync(h->pin + 64, h->c.ctr, 12, cudaMemcpyDeviceToHost, h->stream));
+        SPH_CUDA(h, cudaMemcpyAsync(h->pin + 80, h->c.cyc_log, 48 * (size_t)W, cudaMemcpyDeviceToHost,
+                                    h->stream));
+        st = read_status_with(h, nullptr, 0, nullptr);
+        std::memcpy(ctr, h->pin + 64, 12);
+        std::memcpy(log.data(), h->pin + 80, 48 * (size_t)W);
+    } else {
+        SPH_CUDA(h, cudaMemcpyAsync(log.data(), h->c.cyc_log, 48 * (size_t)W, cudaMemcpyDeviceToHost,
+                                    h->stream));
+        SPH_CUDA(h, cudaMemcpyAsync(ctr, h->c.ctr, 12, cudaMemcpyDeviceToHost, h->stream));
+        st = read_status(h);
+    }
     uint32_t cycles = ctr[2];
     int m = (int)std::min<uint32_t>(cycles, (uint32_t)W);
     for (int a = 0; a < 6; ++a) out[a] = 0.0;
@@ -836,6 +878,7 @@ void sph_destroy(sph_handle *h)
     if (h->exec_prof) cudaGraphExecDestroy(h->exec_prof);
     for (int i = 0; i <= kSubstepKernels; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    if (h->pin) cudaFreeHost(h->pin);
     delete h;
 }
 

@@ -169,6 +169,31 @@ def _oracle_substep_time(sc, max_seconds=60.0):
     return time.perf_counter() - t0, out
 
 
+def _oracle_modes():
+    """The survey's CPU-baseline table: the oracle (as it stands) in brute-force mode on the
+    dam break and in grid mode on the dam break, the stirring tank and the coupled scene, on
+    all host cores and on one; ms per substep (each a bounded number of substeps)."""
+    import oracle
+    from paper_2511_15908_gb300 import scenes
+    cases = [("brute", "dam_break", 0, lambda: scenes.dam_break(seed=0), 1),
+             ("grid", "dam_break", 1, lambda: scenes.dam_break(seed=0), 3),
+             ("grid", "stirring", 1, lambda: scenes.stirring_tank(seed=0, n_substeps=8), 1),
+             ("grid", "coupled", 1, lambda: scenes.coupled(seed=0, n_substeps=8), 1)]
+    out = {}
+    for kind, name, mode, make, reps in cases:
+        sc = make()
+        for threads in (0, 1):
+            oracle.set_threads(threads)
+            sysm = oracle.System(sc, mode=mode)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                sysm.substep()
+            ms = 1e3 * (time.perf_counter() - t0) / reps
+            out[f"{kind}_{name}_{'all_cores' if threads == 0 else '1_core'}_ms"] = ms
+    oracle.set_threads(0)
+    return out
+
+
 def _reference_sample(seed=0):
     """A bounded sample of the coupled workload for the CPU oracle: the same tank height,
     spacing, probe and soft cube, on a 1/4-length slab (250k fluid particles)."""
@@ -553,6 +578,7 @@ def run_ours(args):
                "kind": "oracle",
                "sample": f"1 substep of the full coupled scene ({sc.n_total} particles), "
                          f"FP64 uniform-grid oracle, {t_cpu:.2f} s"}
+        cpu["modes"] = _oracle_modes()
         fe = np.linalg.norm(w_gpu[:3] - ref_wrench[:3]) / max(np.linalg.norm(ref_wrench[:3]), 1e-30)
         te = np.linalg.norm(w_gpu[3:] - ref_wrench[3:]) / max(np.linalg.norm(ref_wrench[3:]), 1e-30)
         wrench_err = {"force_rel": float(fe), "torque_rel": float(te)}

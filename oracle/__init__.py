@@ -104,6 +104,8 @@ def _declare(L):
                               ctypes.c_int, _P(BodyC), ctypes.c_int, _u32p, _i32p, _u32p,
                               _f64p, _f64p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
     L.orc_boxcar.argtypes = [ctypes.c_int, ctypes.c_int, _f64p, _f64p]
+    L.orc_set_threads.restype = None
+    L.orc_set_threads.argtypes = [ctypes.c_int]
     if hasattr(L, "orc_mlp_forward"):
         from . import mlp as _mlp
         _mlp.declare(L)
@@ -128,6 +130,11 @@ def params(p: dict) -> Params:
     P.cell = p["cell"]
     P.flags = int(p["flags"]) & (CLAMP_PRESSURE | TAIT | VOLUME_BOUNDARY)
     return P
+
+
+def set_threads(n: int) -> None:
+    """Host threads for the oracle's parallel loops (0: all cores)."""
+    lib().orc_set_threads(int(n))
 
 
 def W(r, h):

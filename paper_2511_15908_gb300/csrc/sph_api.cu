@@ -119,7 +119,9 @@ struct sph_handle {
     int n_springs = 0;
     int grab = -1;
     bool finalized = false;
-    cudaGraphExec_t exec1 = nullptr, exec16 = nullptr, exec_prof = nullptr;
+    // graphs: 1 and 16 substeps, 1 substep followed by the update cycle's end (the last
+    // launch of a call), and the profiling substep with event nodes
+    cudaGraphExec_t exec1 = nullptr, exec16 = nullptr, exec1c = nullptr, exec_prof = nullptr;
     bool profiling = false;
     cudaEvent_t ev[kSubstepKernels + 1] = {};
     int64_t substeps = 0;
@@ -268,13 +270,15 @@ sph_status finalize(sph_handle *h)
     return SPH_OK;
 }
 
-sph_status capture(sph_handle *h, int count, cudaGraphExec_t *out, bool prof = false)
+sph_status capture(sph_handle *h, int count, cudaGraphExec_t *out, bool prof = false,
+                   bool cycle_end = false)
 {
     cudaGraph_t g = nullptr;
     SPH_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < count && le == cudaSuccess; ++i)
         le = launch_substep(h->c, h->stream, prof ? h->ev : nullptr, prof);
+    if (le == cudaSuccess && cycle_end) le = launch_cycle_end(h->c, h->stream);
     cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, le, "capture launch"); }
     if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
@@ -601,6 +605,7 @@ sph_status sph_step(sph_handle *h, int32_t n_substeps)
     if (h->c.n == 0 || n_substeps == 0) return SPH_OK;
     const bool graphs = !(h->p.flags & SPH_FLAG_NO_GRAPH) && h->stream != nullptr;
     int left = n_substeps;
+    bool cycle_done = false;
     if (h->profiling) {
         if (graphs && !h->exec_prof) {
             st = capture(h, 1, &h->exec_prof, true);
@@ -619,12 +624,21 @@ sph_status sph_step(sph_handle *h, int32_t n_substeps)
             st = capture(h, 16, &h->exec16);
             if (st != SPH_OK) return st;
         }
+        if (left % 16 && !h->exec1c) {
+            st = capture(h, 1, &h->exec1c, false, true);
+            if (st != SPH_OK) return st;
+        }
         for (; left >= 16; left -= 16) SPH_CUDA(h, cudaGraphLaunch(h->exec16, h->stream));
-        for (; left > 0; --left) SPH_CUDA(h, cudaGraphLaunch(h->exec1, h->stream));
+        for (; left > 1; --left) SPH_CUDA(h, cudaGraphLaunch(h->exec1, h->stream));
+        if (left == 1) {
+            // the last substep and the cycle's end in one launch (a haptic tick's step)
+            SPH_CUDA(h, cudaGraphLaunch(h->exec1c, h->stream));
+            cycle_done = true;
+        }
     } else {
         for (; left > 0; --left) SPH_CUDA(h, launch_substep(h->c, h->stream));
     }
-    SPH_CUDA(h, launch_cycle_end(h->c, h->stream));
+    if (!cycle_done) SPH_CUDA(h, launch_cycle_end(h->c, h->stream));
     h->substeps += n_substeps;
     return SPH_OK;
 }
@@ -875,6 +889,7 @@ void sph_destroy(sph_handle *h)
     if (h->stream || h->finalized) cudaStreamSynchronize(h->stream);
     if (h->exec1) cudaGraphExecDestroy(h->exec1);
     if (h->exec16) cudaGraphExecDestroy(h->exec16);
+    if (h->exec1c) cudaGraphExecDestroy(h->exec1c);
     if (h->exec_prof) cudaGraphExecDestroy(h->exec_prof);
     for (int i = 0; i <= kSubstepKernels; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);

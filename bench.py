@@ -21,6 +21,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -79,7 +80,7 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"sph_bench_clocks_{os.getpid()}_rank{index}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
@@ -170,7 +171,7 @@ def _oracle_substep_time(sc, max_seconds=60.0):
 
 
 def _oracle_modes():
-    """The survey's CPU-baseline table: the oracle (as it stands) in brute-force mode on the
+    """A table of CPU-baseline timings: the oracle (as it stands) in brute-force mode on the
     dam break and in grid mode on the dam break, the stirring tank and the coupled scene, on
     all host cores and on one; ms per substep (each a bounded number of substeps)."""
     import oracle

@@ -1,7 +1,7 @@
 // sph_mlp.cu -- the learned haptic-rate wrench surrogate: a 269-128-128-128-6 GELU MLP with
 // BF16 weights and FP32 accumulation on tcgen05 tensor cores, trained on the GPU by these
 // kernels (forward, backward, Adam), and the pooled local descriptor it reads from the SPH
-// state.  The exact FP64 coupling reduction of the substep stays the fallback and judge.
+// state.  The exact FP64 coupling reduction of the substep stays the fallback and reference.
 //
 // Parameters (FP32 master copy, logical layout, 68,358 values):
 //   W1[128][269] b1[128] W2[128][128] b2[128] W3[128][128] b3[128] W4[6][128] b4[6]

@@ -8,7 +8,7 @@ correction.  The correction is the network's output for 269 inputs: 13 kinematic
 relative to the last cycle -- the grab point's displacement since the cycle (3), the time
 since the cycle started (1), the change of linear velocity since the cycle (3), the current
 linear and angular velocity (6) -- and the pooled fluid grid of the cycle (256).  The exact FP64 coupling
-reduction of the substep is therefore both the anchor (fallback) and the judge.
+reduction of the substep is therefore both the anchor (fallback) and the reference.
 
 Everything numerical runs in the library's kernels (descriptor, MLP forward/backward/Adam,
 the substep itself); this module only schedules calls, selects rows and moves arrays.

@@ -248,7 +248,7 @@ def run_reference(args):
 
 
 def batched_form(args, flush_l2_factory):
-    """Form (2): 64 stirring scenes of log-uniform fluid counts (8k-256k) in one persistent
+    """Batched scenes: 64 stirring scenes of log-uniform fluid counts (8k-256k) in one persistent
     graph-captured launch per substep, the launch structure autotuned (persistent kernel,
     one kernel per phase, or the scenes' own kernels as graph branches); against stepping
     them one by one."""
@@ -392,7 +392,7 @@ def isosurface_form(args, sc):
 
 
 def surrogate_form(args):
-    """Form (4): the BF16 tcgen05 MLP surrogate at 1 kHz haptic ticks on the stirring tank
+    """The learned wrench surrogate: the BF16 tcgen05 MLP at 1 kHz haptic ticks on the stirring tank
     (250k fluid), trained on the GPU from logged (descriptor, wrench) pairs: (a) pairs logged
     from the stirring tank itself (time split), (b) the dam-break pairs of the cube grab
     (transfer).  Errors are against the exact FP64 coupling reduction at every tick."""

@@ -259,8 +259,8 @@ sph_status sph_get_sort(sph_handle *h, uint32_t *h_keys, int32_t *h_ids, uint32_
 sph_status sph_get_diag(sph_handle *h, double out[8]);
 
 /*
- * Learned haptic-rate wrench surrogate (form 4 of the build; the paper has no learned
- * part -- it motivates one by the ~60 Hz update rate of the engine loop, Sec. 3.3).
+ * Learned haptic-rate wrench surrogate (the paper has no learned part -- it motivates one
+ * by the ~60 Hz update rate of the engine loop, Sec. 3.3).
  *
  * sph_get_descriptor writes the 269 surrogate inputs of the grabbed body for the last
  * substep into DEVICE memory d_out (enqueued on the handle's stream): pose (x y z qw qx qy
@@ -395,8 +395,8 @@ sph_status sph_set_anchors(sph_handle *h, int32_t body, int32_t n, const int32_t
  * with the spring's lower particle id as the segment start.  The current state is sorted
  * first, as the next substep's hash would (the simulation is unaffected).  *h_n_cut
  * receives the number of springs cut by this call.  Synchronises.  Errors: SPH_ERR_ARG,
- * SPH_ERR_CUDA and the handle's pending status.  The paper's cutting model is not given;
- * this is the build's reading of it.
+ * SPH_ERR_CUDA and the handle's pending status.  The paper does not give its cutting
+ * model; this is one reading of it.
  */
 sph_status sph_cut_springs(sph_handle *h, const float tri[9], int64_t *h_n_cut);
 

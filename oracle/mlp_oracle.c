@@ -3,9 +3,9 @@
  * input descriptor.  TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark baseline).
  *
  * The paper has no learned part; it motivates one by the ~60 Hz update cycle of the
- * engine loop (Sec. 3.3, haptic smoothing).  The network and its precision are fixed by
- * the build's form 4: a 269-128-128-128-6 multilayer perceptron with the tanh form of
- * GELU, BF16 weights and activations, accumulation in FP32 or better.  With bf16 = 1 the
+ * engine loop (Sec. 3.3, haptic smoothing).  The network and its precision: a
+ * 269-128-128-128-6 multilayer perceptron with the tanh form of GELU, BF16 weights and
+ * activations, accumulation in FP32 or better.  With bf16 = 1 the
  * oracle rounds to BF16 (round to nearest even) at exactly those points -- standardised
  * input, weights, hidden activations, output gradient, pre-activation gradients -- and
  * accumulates in FP64; with bf16 = 0 everything is FP64 (used for finite differences).

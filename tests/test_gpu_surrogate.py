@@ -1,4 +1,4 @@
-"""Form 4: the BF16 tcgen05 MLP surrogate (forward, backward, Adam) and its descriptor,
+"""The learned wrench surrogate: the BF16 tcgen05 MLP (forward, backward, Adam) and its descriptor,
 against the FP64 oracle with BF16 rounding at the same points."""
 import numpy as np
 import pytest

@@ -345,8 +345,9 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
  * that many resident blocks per SM, taking tiles_per_fetch (1 .. 64) tiles per work-queue
  * fetch; blocks_per_sm = 0 runs one kernel per phase over all scenes' tiles instead (same
  * tiles, same results; each phase at its own occupancy); blocks_per_sm = -1 runs every
- * scene's own substep kernels as parallel branches of one captured graph (16 branches,
- * scenes dealt round-robin; same results).  tiles_per_fetch matters only for the
+ * scene's own substep kernels as parallel branches of one captured graph (one branch per
+ * scene up to 64; beyond that, scenes balanced over 64 branches by particle count; same
+ * results).  tiles_per_fetch matters only for the
  * persistent kernel.  Errors: SPH_ERR_ARG outside these ranges. */
 sph_status sph_batch_configure(sph_batch *b, int32_t blocks_per_sm, int32_t tiles_per_fetch);
 

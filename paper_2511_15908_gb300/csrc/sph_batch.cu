@@ -194,7 +194,7 @@ sph_status scene_for_batch(sph_handle *h, SimConst *out);
 void scene_advanced(sph_handle *h, int n);
 }
 
-constexpr int kBranchStreams = 16;   // scene-graph structure: parallel branches
+constexpr int kBranchStreams = 64;   // scene-graph structure: at most this many branches
 
 struct sph_batch {
     int n = 0;
@@ -208,6 +208,8 @@ struct sph_batch {
     int sms = 0, max_bps = 0, bps = 0;
     cudaStream_t branch[kBranchStreams] = {};
     cudaEvent_t fork = nullptr, join[kBranchStreams] = {};
+    int n_branches = 0;
+    std::vector<int> branch_of;          // scene -> branch, balanced by particle count
     cudaGraphExec_t exec1 = nullptr, exec16 = nullptr;
     bool use_graph = true;
     std::string err;
@@ -266,16 +268,30 @@ cudaError_t launch_phases(sph_batch *b, int n_substeps, int cycle_end)
     return cudaGetLastError();
 }
 
-// Scene-graph structure: the batch stream forks into kBranchStreams streams, each scene's
-// substep kernels (the single-scene kernels, parameters in the constant bank) run on one
-// of them, and the streams join back before the cycle end.  Captured, this is one graph
-// whose branches the GPU runs side by side.
+// Scene-graph structure: the batch stream forks into one stream per scene (up to
+// kBranchStreams; with more scenes, the largest go first to the least-loaded branch), each
+// scene's substep kernels (the single-scene kernels, parameters in the constant bank) run
+// on its branch, and the branches join back before the cycle end.  Captured, this is one
+// graph whose branches the GPU runs side by side; a substep lasts as long as its most
+// loaded branch, hence the balancing.
 cudaError_t launch_branches(sph_batch *b, int n_substeps, int cycle_end)
 {
     cudaError_t e = cudaSuccess;
     if (!b->fork) {
+        b->n_branches = std::min(b->n, kBranchStreams);
+        std::vector<int> order(b->n);
+        for (int sc = 0; sc < b->n; ++sc) order[sc] = sc;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return b->table[x].n > b->table[y].n; });
+        std::vector<long long> load(b->n_branches, 0);
+        b->branch_of.assign(b->n, 0);
+        for (int sc : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            b->branch_of[sc] = k;
+            load[k] += b->table[sc].n;
+        }
         e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-        for (int k = 0; e == cudaSuccess && k < kBranchStreams; ++k) {
+        for (int k = 0; e == cudaSuccess && k < b->n_branches; ++k) {
             e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
         }
@@ -283,12 +299,12 @@ cudaError_t launch_branches(sph_batch *b, int n_substeps, int cycle_end)
     }
     if (n_substeps > 0) {
         e = cudaEventRecord(b->fork, b->stream);
-        for (int k = 0; e == cudaSuccess && k < kBranchStreams; ++k)
+        for (int k = 0; e == cudaSuccess && k < b->n_branches; ++k)
             e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
         for (int sc = 0; e == cudaSuccess && sc < b->n; ++sc)
             for (int i = 0; e == cudaSuccess && i < n_substeps; ++i)
-                e = launch_substep(b->table[sc], b->branch[sc % kBranchStreams]);
-        for (int k = 0; e == cudaSuccess && k < kBranchStreams; ++k) {
+                e = launch_substep(b->table[sc], b->branch[b->branch_of[sc]]);
+        for (int k = 0; e == cudaSuccess && k < b->n_branches; ++k) {
             e = cudaEventRecord(b->join[k], b->branch[k]);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[k], 0);
         }

@@ -362,3 +362,35 @@ def test_haptic_smoothing_and_wrench_log(sph):
     b = sim.body(1)
     np.testing.assert_allclose(b[:3], sc.trajectory[4 * (W + 5) - 1, :3], atol=0)
     sim.close()
+
+
+def test_overfull_cell_reports_capacity_and_keeps_per_particle_results(sph):
+    # 600 particles inside one cell (the stable in-cell rank handles up to 512): the sort
+    # falls back to the atomic claim order and reports SPH_ERR_CAPACITY, but the order is
+    # still a permutation and every particle's neighbours, density and acceleration are
+    # those of the oracle (compared by id; only the order within the cell may differ)
+    rng = np.random.default_rng(21)
+    p = scenes.make_params(0.02, 1e-4, (-0.1, -0.1, -0.1), (0.1, 0.1, 0.1), flags=0)
+    x = (0.0301 + rng.uniform(0.0, 0.005, (600, 3))).astype(np.float32)
+    sc = scenes.Scene("packed", p, x, np.zeros_like(x), 0.02, [])
+    sim = sph.Simulation(sc, flags=sph.FLAG_RECORD)
+    sim.step(1)
+    with pytest.raises(sph.SphError) as e:
+        sim.sync()
+    assert e.value.status == sph.ERR_CAPACITY
+    keys, ids, cs = sim.sort()
+    assert np.all(np.diff(keys.astype(np.int64)) >= 0)
+    assert np.array_equal(np.sort(ids), np.arange(sc.n_total))
+    st = sim.state(record=True)
+    ref = oracle.System(sc, mode=0).substep()
+    n = sc.n_total
+    np.testing.assert_array_equal(st["nnbr"], _by_id(ref, "nnbr", n))
+    rho_ref = _by_id(ref, "rho", n)
+    assert (np.abs(st["rho"] - rho_ref) / rho_ref).max() <= RHO_TOL
+    acc_ref = _by_id(ref, "acc", n)
+    cond = _by_id(ref, "cond", n)
+    k = float(np.float32(sc.params["k"]))
+    scale = np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * G)
+    dif = np.linalg.norm(st["acc"].astype(np.float64) - acc_ref, axis=1)
+    assert np.all(dif <= ACC_TOL * scale + EPS32 * (8.0 * k * cond[:, 0] / rho_ref + 4.0 * cond[:, 1]))
+    sim.close()

@@ -49,7 +49,9 @@ typedef enum {
     SPH_ERR_NONFINITE = 5,  /* a particle position or velocity became NaN/Inf */
     SPH_ERR_DOMAIN = 6,     /* a particle left the grid domain (its cell was clamped) */
     SPH_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up */
-    SPH_ERR_STATE = 8       /* call not legal in the current state */
+    SPH_ERR_STATE = 8,      /* call not legal in the current state */
+    SPH_ERR_BOUNDS = 9      /* an index check failed (only the build compiled with
+                               -DSPH_CHECKED checks; the access was redirected to index 0) */
 } sph_status;
 
 /* sph_params.flags */
@@ -376,6 +378,25 @@ const char *sph_batch_last_error(const sph_batch *b);
 
 /* Free the host-side batch and its graphs (the workspace and the scenes stay). */
 void sph_batch_destroy(sph_batch *b);
+
+/*
+ * Checkpoint and resume.  A checkpoint holds everything that carries over from one substep
+ * to the next: particle state in its current slot order (the stable sort ties on it),
+ * body-frame offsets and anchors, the spring table with its cuts, the body table, the grab
+ * path, the last wrenches, both wrench logs, the status word and the counters, behind a
+ * small header (magic "SPHCKPT1", substep count, particle and body counts, grabbed body).
+ * Everything else is recomputed by every substep.  A handle created from the same scene
+ * (same parameters, capacities, bodies and springs) that loads it continues bit-identically
+ * to the uninterrupted run.
+ *   sph_checkpoint_bytes  size of a checkpoint of h (0 on error)
+ *   sph_checkpoint_save   writes it to host memory h_buf (>= that size); synchronises
+ *   sph_checkpoint_load   restores it into h; synchronises
+ * Errors: SPH_ERR_ARG (buffer too small, not a checkpoint, another scene), SPH_ERR_CUDA.
+ * The paper has no checkpoint.
+ */
+size_t sph_checkpoint_bytes(sph_handle *h);
+sph_status sph_checkpoint_save(sph_handle *h, void *h_buf, size_t bytes);
+sph_status sph_checkpoint_load(sph_handle *h, const void *h_buf, size_t bytes);
 
 /*
  * Cloth anchors (Sec. 4: a soft-body cloth plane with definable anchor points).  The listed

@@ -2,6 +2,9 @@
 
 Every ``csrc/*.cu`` file is compiled in parallel to an object for
 ``arch=compute_103a,code=sm_103a`` and linked into ``libsph_gb300.so`` beside this file.
+``build(checked=True)`` makes ``libsph_gb300_checked.so`` from the same sources with
+``-DSPH_CHECKED`` (every data-dependent index checked; a failed check latches
+SPH_ERR_BOUNDS) in a build folder of its own.
 """
 from __future__ import annotations
 
@@ -16,6 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph_gb300.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libsph_gb300_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -38,14 +43,17 @@ def _stale(target, inputs):
     return any(os.path.getmtime(i) > t for i in inputs)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    if checked:
+        extra = ("-DSPH_CHECKED", *extra)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = _sources()
     deps = _deps()
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + deps):
             jobs.append([NVCC, *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
@@ -62,13 +70,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp"
         run([NVCC, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else ()))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else (),
+                checked="--checked" in sys.argv))

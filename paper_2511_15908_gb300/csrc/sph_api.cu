@@ -181,6 +181,7 @@ sph_status eval_status(sph_handle *h, const uint32_t st[3])
     SPH_CUDA(h, cudaMemsetAsync(at<uint32_t>(h, h->L.status), 0, 12, h->stream));
     SPH_CUDA(h, cudaStreamSynchronize(h->stream));
     char buf[160];
+    if (st[0] & ST_BOUNDS) return fail(h, SPH_ERR_BOUNDS, "an index check failed (bounds-checked build)");
     if (st[0] & ST_NONFINITE) {
         snprintf(buf, sizeof buf, "non-finite particle state (%u reports)", st[1]);
         return fail(h, SPH_ERR_NONFINITE, buf);
@@ -770,6 +771,102 @@ sph_status sph_set_state(sph_handle *h, const float *h_x, const float *h_v)
     SPH_CUDA(h, cudaMemcpyAsync(h->c.xB, x.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s));
     SPH_CUDA(h, cudaMemcpyAsync(h->c.vB, v.data(), 16 * (size_t)n, cudaMemcpyHostToDevice, s));
     SPH_CUDA(h, cudaStreamSynchronize(s));
+    return SPH_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint / resume
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    int64_t substeps;
+    int32_t n, nf, n_bodies, grab;
+    uint64_t payload;
+};
+
+// Workspace regions that carry over from one substep to the next (everything else is
+// recomputed by every substep): the state in its current slot order (the stable sort ties
+// on it), body-frame offsets and anchor flags, the spring table (with its cuts), the body
+// table, the grab path, the last wrenches, both wrench logs, status word and counters.
+std::vector<std::pair<size_t, size_t>> ckpt_regions(const sph_handle *h)
+{
+    const size_t N = (size_t)std::max(h->cap.max_particles, 1);
+    const size_t n = (size_t)h->c.n;
+    const size_t P = (size_t)std::max(h->cap.max_path, 1);
+    return {{h->L.xB, 16 * n}, {h->L.vB, 16 * n}, {h->L.locals, 16 * N},
+            {h->L.spring_e, 16 * 2 * (size_t)std::max(h->cap.max_springs, 1)},
+            {h->L.body, sizeof(DevBody) * kMaxBodies}, {h->L.path, 4 * 13 * P},
+            {h->L.wrench, 8 * 6 * kMaxBodies}, {h->L.wlog, 8 * 6 * P},
+            {h->L.cyc_log, 8 * 6 * (size_t)std::max(h->p.smooth_window, 1)},
+            {h->L.status, 16}, {h->L.ctr, 16}};
+}
+
+size_t ckpt_total(const sph_handle *h)
+{
+    size_t t = sizeof(CkptHeader);
+    for (const auto &r : ckpt_regions(h)) t += r.second;
+    return t;
+}
+
+const char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
+
+}  // namespace
+
+size_t sph_checkpoint_bytes(sph_handle *h)
+{
+    if (!h || finalize(h) != SPH_OK) return 0;
+    return ckpt_total(h);
+}
+
+sph_status sph_checkpoint_save(sph_handle *h, void *h_buf, size_t bytes)
+{
+    if (!h || !h_buf) return SPH_ERR_ARG;
+    sph_status st = finalize(h);
+    if (st != SPH_OK) return st;
+    if (bytes < ckpt_total(h)) return fail(h, SPH_ERR_ARG, "checkpoint buffer too small");
+    CkptHeader hd;
+    std::memset(&hd, 0, sizeof hd);
+    std::memcpy(hd.magic, kCkptMagic, 8);
+    hd.substeps = h->substeps;
+    hd.n = h->c.n;
+    hd.nf = h->c.nf;
+    hd.n_bodies = (int32_t)h->bodies.size();
+    hd.grab = h->grab;
+    hd.payload = ckpt_total(h) - sizeof hd;
+    char *out = (char *)h_buf;
+    std::memcpy(out, &hd, sizeof hd);
+    size_t off = sizeof hd;
+    for (const auto &r : ckpt_regions(h)) {
+        SPH_CUDA(h, cudaMemcpyAsync(out + off, h->ws + r.first, r.second, cudaMemcpyDeviceToHost, h->stream));
+        off += r.second;
+    }
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+    return SPH_OK;
+}
+
+sph_status sph_checkpoint_load(sph_handle *h, const void *h_buf, size_t bytes)
+{
+    if (!h || !h_buf) return SPH_ERR_ARG;
+    sph_status st = finalize(h);
+    if (st != SPH_OK) return st;
+    CkptHeader hd;
+    if (bytes < sizeof hd) return fail(h, SPH_ERR_ARG, "not a checkpoint");
+    std::memcpy(&hd, h_buf, sizeof hd);
+    if (std::memcmp(hd.magic, kCkptMagic, 8) != 0) return fail(h, SPH_ERR_ARG, "not a checkpoint");
+    if (hd.n != h->c.n || hd.nf != h->c.nf || hd.n_bodies != (int32_t)h->bodies.size() ||
+        hd.payload != ckpt_total(h) - sizeof hd || bytes < ckpt_total(h))
+        return fail(h, SPH_ERR_ARG, "checkpoint of a different scene or capacity");
+    if (hd.grab >= hd.n_bodies || hd.grab < -1) return fail(h, SPH_ERR_ARG, "corrupt checkpoint");
+    const char *in = (const char *)h_buf;
+    size_t off = sizeof hd;
+    for (const auto &r : ckpt_regions(h)) {
+        SPH_CUDA(h, cudaMemcpyAsync(h->ws + r.first, in + off, r.second, cudaMemcpyHostToDevice, h->stream));
+        off += r.second;
+    }
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->substeps = hd.substeps;
+    h->grab = hd.grab;
     return SPH_OK;
 }
 

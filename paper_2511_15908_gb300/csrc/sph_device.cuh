@@ -35,6 +35,22 @@ constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u, FLAG_TAIT = 8u, FLAG_VOLUM
 
 // ------------------------------------------------------------------ small helpers
 
+// Index check of the bounds-checked build (compiled with -DSPH_CHECKED): an index that
+// comes from data (a cell key, a sorted slot, a particle id, a list entry) and falls
+// outside [0, n) latches ST_BOUNDS and is replaced by 0, so the access stays inside its
+// buffer.  The default build compiles the check away.
+__device__ __forceinline__ int in_range(const SimConst &c, long long i, long long n)
+{
+#ifdef SPH_CHECKED
+    if (i >= 0 && i < n) return (int)i;
+    atomicOr(c.status, ST_BOUNDS);
+    return 0;
+#else
+    (void)c; (void)n;
+    return (int)i;
+#endif
+}
+
 __device__ __forceinline__ int body_of(const SimConst &c, int id)
 {
     int b = 0;
@@ -167,8 +183,8 @@ __device__ __forceinline__ void for_each_row(const SimConst &c, float4 x, uint32
             const float w = w2 * rsqrtf(fmaxf(w2, 1e-30f)) + mc;
             const int xa = cell_floor(ux - w, c.nx), xb = cell_floor(ux + w, c.nx);
             const int base = (z * c.ny + y) * c.nx;
-            const int s = (int)__ldg(c.cell_start + base + xa);
-            int e = (int)__ldg(c.cell_start + base + xb + 1);
+            const int s = in_range(c, __ldg(c.cell_start + in_range(c, base + xa, c.ncell)), c.n + 1);
+            int e = in_range(c, __ldg(c.cell_start + in_range(c, base + xb + 1, c.ncell + 1)), c.n + 1);
             if (e - s > kMaxCellRun) { e = s + kMaxCellRun; bad |= ST_CAPACITY; }
             f(s, e);
         }
@@ -224,7 +240,7 @@ __device__ __forceinline__ void hash_item(const SimConst &c, int blk)
             Pose P = body_pose(c, c.body[b], c.ctr[0]);
             float R[9];
             rot_f32(P.q, R);
-            float4 l = c.locals[id - c.nf];
+            float4 l = c.locals[in_range(c, id - c.nf, c.n_body_particles)];
             x.x = body_coord(R, P.t, l, 0);
             x.y = body_coord(R, P.t, l, 1);
             x.z = body_coord(R, P.t, l, 2);
@@ -239,7 +255,7 @@ __device__ __forceinline__ void hash_item(const SimConst &c, int blk)
     uint32_t bad = 0;
     int cx, cy, cz;
     cell_of(c, x, cx, cy, cz, bad);
-    uint32_t k = (uint32_t)((cz * c.ny + cy) * c.nx + cx);
+    uint32_t k = (uint32_t)in_range(c, (cz * c.ny + cy) * c.nx + cx, c.ncell);
     c.key[e] = k;
     c.rank[e] = atomicAdd(c.cnt + k, 1u);
     report(c, bad);
@@ -343,7 +359,8 @@ __device__ __forceinline__ void scatter_item(const SimConst &c, int blk)
 {
     int e = blk * kTile + threadIdx.x;
     if (e >= c.n) return;
-    c.perm[c.cell_start[c.key[e]] + c.rank[e]] = (uint32_t)e;
+    c.perm[in_range(c, (long long)c.cell_start[in_range(c, c.key[e], c.ncell)] + c.rank[e], c.n)] =
+        (uint32_t)e;
 }
 
 // Within a cell the atomic claim order is arbitrary; the final slot of particle e is
@@ -352,9 +369,9 @@ __device__ __forceinline__ void rank_gather_item(const SimConst &c, int blk)
 {
     int p = blk * kTile + threadIdx.x;
     if (p >= c.n) return;
-    uint32_t e = c.perm[p];
-    uint32_t k = c.key[e];
-    int cs = (int)c.cell_start[k], ce = (int)c.cell_start[k + 1];
+    uint32_t e = (uint32_t)in_range(c, c.perm[p], c.n);
+    uint32_t k = (uint32_t)in_range(c, c.key[e], c.ncell);
+    int cs = in_range(c, c.cell_start[k], c.n), ce = in_range(c, c.cell_start[k + 1], c.n + 1);
     int dst;
     if (ce - cs <= kMaxCell) {
         int r = 0;
@@ -364,12 +381,13 @@ __device__ __forceinline__ void rank_gather_item(const SimConst &c, int blk)
         dst = cs + (int)c.rank[e];          // still a permutation; order not stable
         atomicOr(c.status, (uint32_t)ST_CAPACITY);
     }
+    dst = in_range(c, dst, c.n);
     float4 x = c.xB[e];
     float4 v = c.vB[e];
     c.xA[dst] = x;
     c.vA[dst] = v;
     int id = __float_as_int(v.w);
-    if (id >= c.nf && c.body_kind[body_of(c, id)] == KIND_SOFT) c.slot_of_id[id] = dst;
+    if (id >= c.nf && c.body_kind[body_of(c, id)] == KIND_SOFT) c.slot_of_id[in_range(c, id, c.n)] = dst;
 }
 
 // ------------------------------------------------------------------- density pass
@@ -631,7 +649,7 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         if (j >= m) break;
-                        const int q = (int)(j == 0 ? e.x : j == 1 ? e.y : j == 2 ? e.z : e.w);
+                        const int q = in_range(c, j == 0 ? e.x : j == 1 ? e.y : j == 2 ? e.z : e.w, c.n);
                         const float4 xj = __ldg(c.xA + q);
                         float dx, dy, dz;
                         const float r2 = dist2(xi, xj, dx, dy, dz);
@@ -661,12 +679,12 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
             float sx = 0.0f, sy = 0.0f, sz = 0.0f;
             bool anchored = false;
             if (kind == KIND_SOFT) {
-                int l = id - c.nf;
+                int l = in_range(c, id - c.nf, c.n_body_particles);
                 anchored = c.locals[l].w != 0.0f;      // pinned soft particle (cloth anchor)
                 for (int e = c.spring_row[l]; e < c.spring_row[l + 1]; ++e) {
                     float4 sp = c.spring_e[e];
                     if (sp.z == 0.0f && sp.w == 0.0f) continue;   // cut spring
-                    int q = c.slot_of_id[__float_as_int(sp.x)];
+                    int q = in_range(c, c.slot_of_id[in_range(c, __float_as_int(sp.x), c.n)], c.n);
                     float4 xj = c.xA[q], vj = c.vA[q];
                     float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z;
                     float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
@@ -696,7 +714,7 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
         } else {
             c.xB[p] = xi;
             c.vB[p] = vi;
-            int l = id - c.nf;
+            int l = in_range(c, id - c.nf, c.n_body_particles);
             c.fb[l] = make_float4(fx, fy, fz, 0.0f);
             c.xb[l] = xi;
             if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(ax, ay, az, 0.0f);
@@ -774,9 +792,9 @@ __device__ __forceinline__ void cut_item(const SimConst &c, int blk, const Blade
         float4 sp = c.spring_e[e];
         if (sp.z == 0.0f && sp.w == 0.0f) continue;
         const int pid = __float_as_int(sp.x);
-        const int lo = min(id, pid), hi = max(id, pid);
-        const float4 xa = c.xA[c.slot_of_id[lo]];
-        const float4 xb = c.xA[c.slot_of_id[hi]];
+        const int lo = in_range(c, min(id, pid), c.n), hi = in_range(c, max(id, pid), c.n);
+        const float4 xa = c.xA[in_range(c, c.slot_of_id[lo], c.n)];
+        const float4 xb = c.xA[in_range(c, c.slot_of_id[hi], c.n)];
         if (!segment_meets_triangle(make_float3(xa.x, xa.y, xa.z), make_float3(xb.x, xb.y, xb.z), t))
             continue;
         sp.z = 0.0f;
@@ -894,7 +912,7 @@ __device__ __forceinline__ void wrench_item(const SimConst &c, int blk)
     if (has_body) {
         const int l = wb.y + threadIdx.x;
         if (l < wb.z) {
-            int i = c.body[wb.x].first - c.nf + l;
+            int i = in_range(c, c.body[wb.x].first - c.nf + l, c.n_body_particles);
             float4 f = c.fb[i], x = c.xb[i];
             double fd[3] = {f.x, f.y, f.z};
             double r[3] = {(double)x.x - sxg[0], (double)x.y - sxg[1], (double)x.z - sxg[2]}, t[3];

@@ -27,6 +27,7 @@ enum : uint32_t {
     ST_DOMAIN = 1u << 6,
     ST_TIMEOUT = 1u << 7,
     ST_CAPACITY = 1u << 4,
+    ST_BOUNDS = 1u << 9,       // an index check of the bounds-checked build failed
 };
 
 struct DevBody {

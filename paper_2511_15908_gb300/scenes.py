@@ -399,6 +399,44 @@ def column(seed=0, n=(6, 6, 20), spacing=0.02, dt=1e-3):
     return Scene("column", params, fluid, np.zeros_like(fluid), s, [walls], n_substeps=2000)
 
 
+def held_cube_tank(seed=0, n=(14, 14, 18), cube_cells=6, spacing=0.02, dt=1e-3, nu=5e-3):
+    """A tank of fluid at rest with a cube held still at mid-depth (a grabbed body whose path
+    is one fixed pose).  The cube fills `cube_cells`^3 lattice cells carved out of the
+    fluid, sampled at half the fluid spacing; its faces lie on lattice cell faces."""
+    rng = np.random.default_rng(seed)
+    s = spacing
+    c = int(cube_cells)
+    lo_c = np.array([(n[0] - c) // 2, (n[1] - c) // 2, (n[2] - c) // 2])
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    ijk = np.stack([i, j, k], -1).reshape(-1, 3)
+    inside = np.all((ijk >= lo_c) & (ijk < lo_c + c), axis=1)
+    fluid = _jitter(rng, (ijk[~inside] + 0.5) * s, s).astype(np.float32)
+    box_hi = (n[0] * s, n[1] * s, (n[2] + 4) * s)
+    walls = Body(KIND_STATIC, wall_shell((0, 0, 0), box_hi, s), s)
+    a = c * s
+    cube_local, _ = solid_box((a, a, a), s / 2)
+    centre = (lo_c + 0.5 * c) * s
+    pose = np.array([*centre, 1, 0, 0, 0], np.float32)
+    cube = Body(KIND_RIGID, cube_local, s / 2, mass=500.0 * a ** 3,
+                inertia=_box_inertia(500.0 * a ** 3, (a, a, a)), pose=pose)
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s),
+                         (box_hi[0] + 3 * s, box_hi[1] + 3 * s, box_hi[2] + 3 * s), nu=nu)
+    traj = np.zeros((1, 13), np.float32)
+    traj[0, :7] = pose
+    return Scene("held_cube_tank", params, fluid, np.zeros_like(fluid), s, [walls, cube],
+                 grab_body=1, trajectory=traj, n_substeps=2000)
+
+
+def released_cube_tank(seed=0, sigma=0.2, **kw):
+    """The held-cube tank with the cube let go (density 500: it rises) and seeded random
+    fluid and cube velocities: undriven two-way coupling in a closed tank."""
+    sc = held_cube_tank(seed=seed, **kw)
+    sc.name = "released_cube_tank"
+    sc.grab_body = -1
+    sc.trajectory = None
+    return with_velocity_noise(sc, seed=seed, sigma=sigma)
+
+
 def with_velocity_noise(scene: Scene, seed: int = 0, sigma: float = 0.2) -> Scene:
     """Seeded Gaussian fluid velocities and rigid-body velocities (exercises viscosity
     and the kinematic boundary velocities from the very first substep)."""

@@ -16,9 +16,11 @@ from . import scenes as _scenes
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsph_gb300.so")
+# the same library built with -DSPH_CHECKED (index checks; build.build(checked=True))
+CHECKED_LIB_PATH = os.path.join(_HERE, "libsph_gb300_checked.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_CAPACITY, ERR_NONFINITE, ERR_DOMAIN, ERR_TIMEOUT, \
-    ERR_STATE = range(9)
+    ERR_STATE, ERR_BOUNDS = range(10)
 FLAG_CLAMP_PRESSURE, FLAG_RECORD, FLAG_NO_GRAPH, FLAG_TAIT, FLAG_VOLUME_BOUNDARY = 1, 2, 4, 8, 16
 BODY_STATIC, BODY_RIGID, BODY_SOFT = 1, 2, 3
 
@@ -35,7 +37,8 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_mlp_get_params", "sph_mlp_forward", "sph_mlp_gradients", "sph_mlp_train_step",
            "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc",
            "sph_iso_grid", "sph_iso_field", "sph_iso_workspace_bytes", "sph_iso_polygonize",
-           "sph_set_anchors", "sph_cut_springs"]
+           "sph_set_anchors", "sph_cut_springs", "sph_checkpoint_bytes", "sph_checkpoint_save",
+           "sph_checkpoint_load"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -61,7 +64,7 @@ class Capacity(ctypes.Structure):
                 ("max_neighbours", ctypes.c_int32)]
 
 
-_lib = None
+_libs = {}
 _f32p = ctypes.POINTER(ctypes.c_float)
 _f64p = ctypes.POINTER(ctypes.c_double)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -72,9 +75,9 @@ _vp = ctypes.c_void_p
 
 def load(path: str = LIB_PATH):
     """Load the sm_103a library; raises if it has not been built."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    path = os.path.abspath(path)
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is missing: build it with paper_2511_15908_gb300.build.build()")
     L = ctypes.CDLL(path)
@@ -165,6 +168,12 @@ def load(path: str = LIB_PATH):
     L.sph_mlp_destroy.argtypes = [_vp]
     L.sph_cell_sort_noalloc.restype = st
     L.sph_cell_sort_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.sph_checkpoint_bytes.restype = ctypes.c_size_t
+    L.sph_checkpoint_bytes.argtypes = [_vp]
+    L.sph_checkpoint_save.restype = st
+    L.sph_checkpoint_save.argtypes = [_vp, _vp, ctypes.c_size_t]
+    L.sph_checkpoint_load.restype = st
+    L.sph_checkpoint_load.argtypes = [_vp, _vp, ctypes.c_size_t]
     L.sph_set_anchors.restype = st
     L.sph_set_anchors.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _i32p]
     L.sph_cut_springs.restype = st
@@ -184,7 +193,7 @@ def load(path: str = LIB_PATH):
     L.sph_last_error.argtypes = [_vp]
     L.sph_destroy.restype = None
     L.sph_destroy.argtypes = [_vp]
-    _lib = L
+    _libs[path] = L
     return L
 
 
@@ -213,11 +222,11 @@ class Simulation:
     """One scene on one GPU behind the C ABI.  The workspace is a torch CUDA tensor."""
 
     def __init__(self, scene: _scenes.Scene, flags: Optional[int] = None, max_path: Optional[int] = None,
-                 device: int = 0, stream=None, max_neighbours: int = 0):
+                 device: int = 0, stream=None, max_neighbours: int = 0, lib: Optional[str] = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the SPH library needs a CUDA device")
-        self.L = load()
+        self.L = load(lib or LIB_PATH)
         self.scene = scene
         self.device = torch.device("cuda", device)
         self.params = make_params(scene.params, scene.fluid_spacing, flags)
@@ -366,6 +375,27 @@ class Simulation:
         """Write the 269 surrogate inputs of the last substep into a CUDA float tensor."""
         self._check(self.L.sph_get_descriptor(self.h, d_out.data_ptr()))
 
+    def checkpoint(self) -> np.ndarray:
+        """Everything that carries over between substeps, as a uint8 array (sph_checkpoint_save)."""
+        n = self.L.sph_checkpoint_bytes(self.h)
+        if n == 0:
+            raise SphError(ERR_ARG, "sph_checkpoint_bytes failed")
+        buf = np.zeros(n, np.uint8)
+        self._check(self.L.sph_checkpoint_save(self.h, buf.ctypes.data, n))
+        return buf
+
+    def restore(self, buf: np.ndarray) -> None:
+        """Continue from a checkpoint of the same scene (sph_checkpoint_load)."""
+        b = np.ascontiguousarray(buf, np.uint8)
+        self._check(self.L.sph_checkpoint_load(self.h, b.ctypes.data, b.size))
+
+    def save_checkpoint(self, path: str) -> None:
+        np.savez(path, checkpoint=self.checkpoint())
+
+    def load_checkpoint(self, path: str) -> None:
+        with np.load(path) as f:
+            self.restore(f["checkpoint"])
+
     def cut_springs(self, tri) -> int:
         """Cut every soft-body spring whose segment meets the triangle tri (3 x 3 corners);
         returns how many were cut."""
@@ -422,8 +452,11 @@ class Batch:
 
     def __init__(self, sims, stream=None):
         import torch
-        self.L = load()
         self.sims = list(sims)
+        # the scenes' handles belong to the library that made them
+        self.L = self.sims[0].L if self.sims else load()
+        if any(sm.L is not self.L for sm in self.sims):
+            raise SphError(ERR_ARG, "scenes of a batch must come from one library")
         n = len(self.sims)
         nbytes = self.L.sph_batch_workspace_bytes(n)
         if nbytes == 0:

@@ -1,0 +1,110 @@
+"""Checkpoint and resume through the C ABI: a handle created from the same scene that loads a
+checkpoint continues bit-identically to the run that was never interrupted (positions,
+velocities, body table, raw and smoothed grab wrench, wrench log), and a checkpoint of
+another scene, or bytes that are not a checkpoint, are refused.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_15908_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15908_gb300 import build, sph as _sph
+    build.build()
+    _sph.load()
+    return _sph
+
+
+def _grabbed():
+    return scenes.with_velocity_noise(
+        scenes.dam_break(seed=6, grab=True, n_substeps=200, cube_pos=(0.3, 0.3, 0.15)),
+        seed=6, sigma=0.3)
+
+
+def _cloth():
+    return scenes.cloth_bath(seed=2, anchors="corners")
+
+
+def _snapshot(sim, sc, grabbed):
+    st = sim.state()
+    out = [st["x"], st["v"]] + [sim.body(b) for b in range(len(sc.bodies))]
+    if grabbed:
+        out += [sim.grab_wrench(smoothed=False), sim.grab_wrench(smoothed=True), sim.wrench_log(9)]
+    return out
+
+
+@pytest.mark.parametrize("make,grabbed,cut", [(_grabbed, True, False), (_cloth, False, True)])
+def test_resume_is_bit_identical(sph, make, grabbed, cut, tmp_path):
+    sc = make()
+    xc = float(sc.bodies[-1].xyz[5, 0]) + 0.5 * sc.fluid_spacing
+    blade = [[xc, -1.0, -1.0], [xc, 3.0, -1.0], [xc, -1.0, 3.0]]
+    a = sph.Simulation(sc)
+    a.step(7)
+    if cut:
+        assert a.cut_springs(blade) > 0
+    a.step(6)
+    ck = a.checkpoint()
+    a.step(5)
+    a.step(4)
+    want = _snapshot(a, sc, grabbed)
+    info_a = a.info()
+    a.close()
+
+    for via_file in (False, True):
+        b = sph.Simulation(make())
+        if via_file:
+            p = str(tmp_path / "ck.npz")
+            np.savez(p, checkpoint=ck)
+            b.load_checkpoint(p)
+        else:
+            b.restore(ck)
+        b.step(5)
+        b.step(4)
+        got = _snapshot(b, sc, grabbed)
+        assert b.info()[4] == info_a[4]              # substeps advanced
+        b.close()
+        for i, (u, w) in enumerate(zip(got, want)):
+            assert np.array_equal(u, w), f"item {i} differs after resume"
+
+
+def test_checkpoint_taken_after_resume_equals_the_original(sph):
+    sc = _grabbed()
+    a = sph.Simulation(sc)
+    a.step(9)
+    ck = a.checkpoint()
+    b = sph.Simulation(_grabbed())
+    b.restore(ck)
+    assert np.array_equal(b.checkpoint(), ck)
+    a.close()
+    b.close()
+
+
+def test_foreign_or_damaged_checkpoints_are_refused(sph):
+    a = sph.Simulation(_grabbed())
+    a.step(3)
+    ck = a.checkpoint()
+    other = sph.Simulation(_cloth())
+    with pytest.raises(sph.SphError) as e:
+        other.restore(ck)
+    assert e.value.status == sph.ERR_ARG
+    bad = ck.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(sph.SphError) as e:
+        a.restore(bad)
+    assert e.value.status == sph.ERR_ARG
+    with pytest.raises(sph.SphError) as e:
+        a.restore(ck[:-1])
+    assert e.value.status == sph.ERR_ARG
+    # a refused load leaves the handle as it was
+    a.step(2)
+    a.sync()
+    assert np.all(np.isfinite(a.state()["x"]))
+    a.close()
+    other.close()

@@ -396,6 +396,62 @@ def isosurface_form(args, sc):
                     "and sph_iso_polygonize (count, scan, write) after 20 substeps"}
 
 
+def cloth_form(args, flush_l2_factory):
+    """The cloth plane with anchors and incision (Sec. 4): a 100 x 100 soft sheet anchored at
+    its corners over a 100 x 100 x 40 fluid block, timed per substep like the plain path,
+    before and after a full-width incision; the incision call (sort of the current state +
+    the segment-triangle test over every spring) is timed on the simulation's stream."""
+    import torch
+    from paper_2511_15908_gb300 import scenes, sph
+    sc = scenes.cloth_bath(seed=0, n=(100, 100, 40), cloth=(100, 100), anchors="corners")
+    sim = sph.Simulation(sc)
+    sim.set_profiling(True)
+    flush = flush_l2_factory(sim.stream)
+    domain = [0]
+    n = max(5, args.steps)
+
+    def timed():
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        kt = np.zeros((n, len(sph.KERNELS)))
+        for i in range(n):
+            flush()
+            ev0[i].record(sim.stream)
+            sim.step(1)
+            ev1[i].record(sim.stream)
+            kt[i] = _reported(sim.kernel_times, domain, sph)
+        _reported(sim.sync, domain, sph)
+        km = kt.mean(axis=0)
+        return (float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)])),
+                float(km[sph.KERNELS.index("density")]), float(km[sph.KERNELS.index("force")]))
+
+    for _ in range(max(3, args.warmup)):
+        flush()
+        sim.step(1)
+    _reported(sim.sync, domain, sph)
+    before = timed()
+    sheet = sc.bodies[1]
+    xc = float(sheet.xyz[50, 0]) + 0.5 * sc.fluid_spacing
+    blade = [[xc, -10.0, -10.0], [xc, 30.0, -10.0], [xc, -10.0, 30.0]]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(sim.stream)
+    n_cut = _reported(lambda: sim.cut_springs(blade), domain, sph)
+    e1.record(sim.stream)
+    e1.synchronize()
+    cut_ms = e0.elapsed_time(e1)
+    after = timed()
+    n_springs = int(sheet.springs.shape[0])
+    sim.close()
+    return {"ms_per_substep": before[0], "value": sc.n_fluid / (before[0] / 1e3), "unit": UNIT,
+            "density_ms": before[1], "force_ms": before[2],
+            "after_cut": {"ms_per_substep": after[0], "density_ms": after[1], "force_ms": after[2]},
+            "cut_ms": cut_ms, "springs": n_springs, "springs_cut": n_cut,
+            "fluid": sc.n_fluid, "cloth_particles": sheet.n, "out_of_domain_reports": domain[0],
+            "what": "cloth bath: 100 x 100 sheet (corner anchors, structural/shear/bending "
+                    "springs) over 400k fluid particles, dt 5e-4; incision = one "
+                    "sph_cut_springs call with a full-width blade between two columns"}
+
+
 def surrogate_form(args):
     """The learned wrench surrogate: the BF16 tcgen05 MLP at 1 kHz haptic ticks on the stirring tank
     (250k fluid), trained on the GPU from logged (descriptor, wrench) pairs: (a) pairs logged
@@ -607,6 +663,7 @@ def run_ours(args):
             "same workload with SPH_FLAG_VOLUME_BOUNDARY (boundary weights psi = rho0 / "
             "sum_boundary W; the density interval includes the psi pass)")
         forms["isosurface"] = isosurface_form(args, sc)
+        forms["cloth"] = cloth_form(args, factory)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

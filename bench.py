@@ -408,7 +408,9 @@ def cloth_form(args, flush_l2_factory):
     sim.set_profiling(True)
     flush = flush_l2_factory(sim.stream)
     domain = [0]
-    n = max(5, args.steps)
+    # a fixed, short run: the block has a floor but no walls, and spreads out of the grid
+    # domain after a few hundred substeps
+    n = 20
 
     def timed():
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -425,7 +427,7 @@ def cloth_form(args, flush_l2_factory):
         return (float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)])),
                 float(km[sph.KERNELS.index("density")]), float(km[sph.KERNELS.index("force")]))
 
-    for _ in range(max(3, args.warmup)):
+    for _ in range(3):
         flush()
         sim.step(1)
     _reported(sim.sync, domain, sph)
@@ -448,7 +450,8 @@ def cloth_form(args, flush_l2_factory):
             "cut_ms": cut_ms, "springs": n_springs, "springs_cut": n_cut,
             "fluid": sc.n_fluid, "cloth_particles": sheet.n, "out_of_domain_reports": domain[0],
             "what": "cloth bath: 100 x 100 sheet (corner anchors, structural/shear/bending "
-                    "springs) over 400k fluid particles, dt 5e-4; incision = one "
+                    "springs) over 400k fluid particles, dt 5e-4, 3 warm-up and 20 timed "
+                    "substeps before and 20 after the incision; incision = one "
                     "sph_cut_springs call with a full-width blade between two columns"}
 
 

@@ -35,6 +35,18 @@ constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u, FLAG_TAIT = 8u, FLAG_VOLUM
 
 // ------------------------------------------------------------------ small helpers
 
+// Neighbour loads the force pass issues together from a list quad (1, 2 or 4): with 2 the
+// pass ran 187 -> 155 us (same registers); 4 needs more registers than the occupancy the
+// pass wants.
+#ifndef SPH_FORCE_BATCH
+#define SPH_FORCE_BATCH 2
+#endif
+// Candidates per unrolled step of the density pass's distance-mask loop.
+#ifndef SPH_MASK_UNROLL
+#define SPH_MASK_UNROLL 4
+#endif
+constexpr int kMaskUnroll = SPH_MASK_UNROLL;
+
 // Index check of the bounds-checked build (compiled with -DSPH_CHECKED): an index that
 // comes from data (a cell key, a sorted slot, a particle id, a list entry) and falls
 // outside [0, n) latches ST_BOUNDS and is replaced by 0, so the access stays inside its
@@ -491,7 +503,7 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk)
         for (int b = s0; b < e0; b += 32) {
             const int end = min(e0, b + 32);
             uint32_t mm = 0u, bit = 1u;
-#pragma unroll 4
+#pragma unroll kMaskUnroll
             for (int q = b; q < end; ++q) {
                 const float4 xj = __ldg(c.xA + q);
                 float dx, dy, dz;
@@ -601,11 +613,9 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
         const float inv_mi = 1.0f / mi;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
         if (!skip) {
-            auto pair = [&](int q, float4 xj, float dx, float dy, float dz, float r2) {
-                float4 vj = __ldg(c.vA + q);
+            auto pair = [&](float4 xj, float4 vj, float2 pj, float dx, float dy, float dz, float r2) {
                 int jd = __float_as_int(vj.w);
                 if ((unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
-                float2 pj = __ldg(c.prho + q);
                 const bool bi = xi.w < 0.0f, bj = xj.w < 0.0f;
                 if (vol && bi && bj) return;       // volume boundaries: no boundary pairs
                 float rinv = 0.0f;                 // coincident particles: no force
@@ -646,6 +656,32 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                     const uint4 e = nxt;
                     if (4 * (g + 1) < nl) nxt = __ldg(lq + (size_t)(g + 1) * c.n);
                     const int m = min(4, nl - 4 * g);
+#if SPH_FORCE_BATCH > 1
+                    // all of the quad's neighbour loads are issued before the first pair is
+                    // evaluated (a short last quad repeats its first entry, unused)
+                    constexpr int B = SPH_FORCE_BATCH;
+                    const uint32_t qq[4] = {e.x, m > 1 ? e.y : e.x, m > 2 ? e.z : e.x, m > 3 ? e.w : e.x};
+#pragma unroll
+                    for (int j0 = 0; j0 < 4; j0 += B) {
+                        float4 xs[B], vs[B];
+                        float2 ps[B];
+#pragma unroll
+                        for (int j = 0; j < B; ++j) {
+                            const int q = in_range(c, qq[j0 + j], c.n);
+                            xs[j] = __ldg(c.xA + q);
+                            vs[j] = __ldg(c.vA + q);
+                            ps[j] = __ldg(c.prho + q);
+                        }
+#pragma unroll
+                        for (int j = 0; j < B; ++j) {
+                            if (j0 + j < m) {
+                                float dx, dy, dz;
+                                const float r2 = dist2(xi, xs[j], dx, dy, dz);
+                                pair(xs[j], vs[j], ps[j], dx, dy, dz, r2);
+                            }
+                        }
+                    }
+#else
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         if (j >= m) break;
@@ -653,8 +689,9 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                         const float4 xj = __ldg(c.xA + q);
                         float dx, dy, dz;
                         const float r2 = dist2(xi, xj, dx, dy, dz);
-                        pair(q, xj, dx, dy, dz, r2);
+                        pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2);
                     }
+#endif
                 }
             } else {
                 // more partners than list slots: search again
@@ -664,7 +701,7 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                         const float4 xj = __ldg(c.xA + q);
                         float dx, dy, dz;
                         const float r2 = dist2(xi, xj, dx, dy, dz);
-                        if (r2 < c.R2) pair(q, xj, dx, dy, dz, r2);
+                        if (r2 < c.R2) pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2);
                     }
                 });
             }

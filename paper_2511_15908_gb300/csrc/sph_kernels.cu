@@ -2,11 +2,15 @@
 // (captured once into a CUDA graph).  The arithmetic lives in sph_device.cuh.
 #include "sph_device.cuh"
 
+// Resident 256-thread blocks per SM each pass is built for (its register budget).  Measured
+// on the 1.16 M-particle coupled scene: density 4 (62 registers) 317 us against 354 at 6
+// (40 registers) and 336 at 5; force 5 with two neighbours' loads in flight 147 us against
+// 155 at 4 and 175 at 6.
 #ifndef SPH_DENSITY_MINB
-#define SPH_DENSITY_MINB 6    // resident 256-thread blocks per SM the density pass is built for
+#define SPH_DENSITY_MINB 4
 #endif
 #ifndef SPH_FORCE_MINB
-#define SPH_FORCE_MINB 4      // resident 256-thread blocks per SM the force pass is built for
+#define SPH_FORCE_MINB 5
 #endif
 
 namespace sphgb {

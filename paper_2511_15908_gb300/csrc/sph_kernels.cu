@@ -2,16 +2,23 @@
 // (captured once into a CUDA graph).  The arithmetic lives in sph_device.cuh.
 #include "sph_device.cuh"
 
-// Resident 256-thread blocks per SM each pass is built for (its register budget).  Measured
-// on the 1.16 M-particle coupled scene: density 4 (62 registers) 317 us against 354 at 6
-// (40 registers) and 336 at 5; force 5 with two neighbours' loads in flight 147 us against
-// 155 at 4 and 175 at 6.
+// Block shape and resident blocks per SM each pass is built for (its register budget).
+// Measured on the 1.16 M-particle coupled scene: density in 512-thread blocks, 2 per SM (62
+// registers) 305 us, against 317 for 256 x 4, 354 for 256 x 6 (40 registers), 320 for
+// 128 x 8 and 316 for 1024 x 1; force in 256-thread blocks, 5 per SM, with two neighbours'
+// loads in flight 147 us against 155 at 4 and 175 at 6.  Scenes too small to fill two
+// waves of the wide blocks (kDensityWideMin particles) take 256 x 4: on 64 scenes of
+// 8k-256k particles the wide blocks alone cost 4 % more.
+#ifndef SPH_DENSITY_THREADS
+#define SPH_DENSITY_THREADS 512
+#endif
 #ifndef SPH_DENSITY_MINB
-#define SPH_DENSITY_MINB 4
+#define SPH_DENSITY_MINB 2
 #endif
 #ifndef SPH_FORCE_MINB
 #define SPH_FORCE_MINB 5
 #endif
+constexpr int kDensityWideMin = 300000;   // ~ 2 x 152 SMs x 2 blocks x 512 threads
 
 namespace sphgb {
 
@@ -20,7 +27,11 @@ __global__ void __launch_bounds__(kTile) k_scan_tiles(SimConst c) { scan_tiles_i
 __global__ void __launch_bounds__(kTile) k_scan_apply(SimConst c) { scan_apply_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_scatter(SimConst c) { scatter_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_rank_gather(SimConst c) { rank_gather_item(c, blockIdx.x); }
-__global__ void __launch_bounds__(kTile, SPH_DENSITY_MINB) k_density(SimConst c) { density_item(c, blockIdx.x); }
+__global__ void __launch_bounds__(SPH_DENSITY_THREADS, SPH_DENSITY_MINB) k_density(SimConst c)
+{
+    density_item(c, blockIdx.x);
+}
+__global__ void __launch_bounds__(kTile, 4) k_density_narrow(SimConst c) { density_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_boundary_volume(SimConst c) { boundary_volume_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force(SimConst c) { force_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_wrench(SimConst c) { wrench_item(c, blockIdx.x); }
@@ -87,7 +98,10 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     mark();
     // volume-based boundaries: their weights first (timed with the density pass)
     if (c.flags & FLAG_VOLUME) k_boundary_volume<<<nb, kTile, 0, s>>>(c);
-    k_density<<<nb, kTile, 0, s>>>(c);
+    if (c.n >= kDensityWideMin)
+        k_density<<<blocks_for(c.n, SPH_DENSITY_THREADS), SPH_DENSITY_THREADS, 0, s>>>(c);
+    else
+        k_density_narrow<<<nb, kTile, 0, s>>>(c);
     mark();
     k_force<<<c.n_force_blocks, kTile, 0, s>>>(c);
     mark();

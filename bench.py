@@ -162,12 +162,35 @@ def _workload(name):
 
 
 def _oracle_substep_time(sc, max_seconds=60.0):
-    """Time one FP64 grid-oracle substep of `sc` on all host cores; returns (s, result)."""
+    """Time one FP64 grid-oracle substep of `sc` on all host cores; returns (s, result, the
+    signed particle masses in the result's sorted order)."""
     import oracle
     sysm = oracle.System(sc, mode=1)
     t0 = time.perf_counter()
     out = sysm.substep()
-    return time.perf_counter() - t0, out
+    return time.perf_counter() - t0, out, sysm.m.astype(np.float64)
+
+
+def _cancellation(sc, out, m_sorted, g):
+    """Cancellation ratios of the grabbed body's wrench in one oracle substep:
+    kappa_F = sum_i |f_i| / |sum_i f_i| and kappa_tau = sum_i |r_i x f_i| / |sum_i r_i x f_i|
+    over its particles (f_i = m_i a_i, the pair force; r_i from the grab point).  An FP32
+    error of the pair forces reaches the summed wrench amplified by kappa."""
+    first = sc.n_fluid + sum(b.n for b in sc.bodies[:g])
+    ids = out["id"]
+    sel = (ids >= first) & (ids < first + sc.bodies[g].n)
+    f = np.abs(m_sorted[sel])[:, None] * out["acc"][sel]
+    t, q = out["body_new"][g][:3], out["body_new"][g][3:7]
+    w, x, y, z = q / np.linalg.norm(q)
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    xg = R @ np.asarray(sc.bodies[g].grab_local, np.float64) + t
+    tau = np.cross(out["x_new"][sel] - xg, f)
+    F, T = f.sum(axis=0), tau.sum(axis=0)
+    return {"kappa_force": float(np.linalg.norm(f, axis=1).sum() / max(np.linalg.norm(F), 1e-300)),
+            "kappa_torque": float(np.linalg.norm(tau, axis=1).sum() / max(np.linalg.norm(T), 1e-300)),
+            "force_from_pairs": F.tolist(), "torque_from_pairs": T.tolist()}
 
 
 def _oracle_modes():
@@ -637,7 +660,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        t_cpu, out = _oracle_substep_time(sc)
+        t_cpu, out, m_sorted = _oracle_substep_time(sc)
         ref_wrench = out["wrench"][sc.grab_body]
         cpu = {"value": sc.n_fluid / t_cpu, "unit": UNIT, "cores": os.cpu_count(),
                "kind": "oracle",
@@ -646,7 +669,9 @@ def run_ours(args):
         cpu["modes"] = _oracle_modes()
         fe = np.linalg.norm(w_gpu[:3] - ref_wrench[:3]) / max(np.linalg.norm(ref_wrench[:3]), 1e-30)
         te = np.linalg.norm(w_gpu[3:] - ref_wrench[3:]) / max(np.linalg.norm(ref_wrench[3:]), 1e-30)
-        wrench_err = {"force_rel": float(fe), "torque_rel": float(te)}
+        kap = _cancellation(sc, out, m_sorted, sc.grab_body)
+        wrench_err = {"force_rel": float(fe), "torque_rel": float(te),
+                      "kappa_force": kap["kappa_force"], "kappa_torque": kap["kappa_torque"]}
 
     forms = {}
     if not args.no_forms:

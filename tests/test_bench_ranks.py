@@ -6,6 +6,7 @@ throughput counts every rank's particles over that time.
 import importlib.util
 import os
 
+import numpy as np
 import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
@@ -55,3 +56,18 @@ def test_single_process_passes_through():
     b = _bench()
     assert b.max_over_ranks(2.5, device="cpu") == 2.5
     assert b.job_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_cancellation_ratios_rebuild_the_oracle_wrench():
+    # the per-particle pair forces and the grab point the ratios use must give back the
+    # oracle's own wrench; a ratio is at least 1 (triangle inequality)
+    from paper_2511_15908_gb300 import scenes
+    bench = _bench()
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=3, grab=True, cube_pos=(0.2, 0.2, 0.15)),
+                                    seed=3, sigma=0.3)
+    _, out, m = bench._oracle_substep_time(sc)
+    k = bench._cancellation(sc, out, m, sc.grab_body)
+    w = out["wrench"][sc.grab_body]
+    np.testing.assert_allclose(k["force_from_pairs"], w[:3], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(k["torque_from_pairs"], w[3:], rtol=1e-6, atol=1e-9 * np.abs(w[3:]).max())
+    assert k["kappa_force"] >= 1.0 and k["kappa_torque"] >= 1.0

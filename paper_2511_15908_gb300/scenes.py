@@ -427,6 +427,37 @@ def held_cube_tank(seed=0, n=(14, 14, 18), cube_cells=6, spacing=0.02, dt=1e-3, 
                  grab_body=1, trajectory=traj, n_substeps=2000)
 
 
+def three_balls_tank(seed=0, ratios=(0.1, 0.3, 1.0), n=(24, 12, 10), radius=0.05, spacing=0.02,
+                     dt=1e-3, nu=5e-3):
+    """Free balls of the given densities relative to the fluid's (Sec. 4 demo: 0.1, 0.3, 1.0)
+    placed half-submerged in a tank of fluid at rest, along x at the fluid surface; the
+    fluid cells within a ball are carved out.  Balls are sampled at half the spacing."""
+    rng = np.random.default_rng(seed)
+    s = spacing
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    cells = (np.stack([i, j, k], -1).reshape(-1, 3) + 0.5) * s
+    surface = n[2] * s
+    centres = [np.array([(m + 0.5) * n[0] * s / len(ratios), 0.5 * n[1] * s, surface])
+               for m in range(len(ratios))]
+    keep = np.ones(len(cells), bool)
+    for c in centres:
+        keep &= np.linalg.norm(cells - c, axis=1) > radius
+    fluid = _jitter(rng, cells[keep], s).astype(np.float32)
+    box_hi = (n[0] * s, n[1] * s, (n[2] + 8) * s)
+    bodies = [Body(KIND_STATIC, wall_shell((0, 0, 0), box_hi, s), s)]
+    ball = solid_sphere(radius, s / 2)
+    vol = 4.0 / 3.0 * np.pi * radius ** 3
+    for r, c in zip(ratios, centres):
+        mass = r * 1000.0 * vol
+        bodies.append(Body(KIND_RIGID, ball, s / 2, mass=mass,
+                           inertia=(0.4 * mass * radius ** 2 * np.eye(3)).astype(np.float32),
+                           pose=np.array([*c, 1, 0, 0, 0], np.float32)))
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s),
+                         (box_hi[0] + 3 * s, box_hi[1] + 3 * s, box_hi[2] + 3 * s), nu=nu)
+    return Scene("three_balls_tank", params, fluid, np.zeros_like(fluid), s, bodies,
+                 n_substeps=3000)
+
+
 def released_cube_tank(seed=0, sigma=0.2, **kw):
     """The held-cube tank with the cube let go (density 500: it rises) and seeded random
     fluid and cube velocities: undriven two-way coupling in a closed tank."""

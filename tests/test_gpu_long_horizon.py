@@ -3,6 +3,8 @@
 
 - a cube held still in settled fluid feels Archimedes' buoyancy rho0 g a^3, and the walls
   and the cube together carry the fluid's weight (Sec. 3.2 two-way coupling);
+- free balls of density 0.1, 0.3 and 1.0 of the fluid's settle in that order, the light ones
+  floating (the Sec. 4 buoyancy demo);
 - fluid and a released buoyant cube in a closed tank, undriven, never gain mechanical energy
   over 3000 substeps;
 - a stirred coupled scene with a soft body stays finite, with at most a few spray particles
@@ -47,6 +49,24 @@ def test_held_cube_feels_archimedes_buoyancy(sph):
     assert np.abs(st["v"][:sc.n_fluid]).max() < 0.08
     # the held cube has not moved
     np.testing.assert_array_equal(sim.body(1)[:7], sc.trajectory[0, :7])
+    sim.close()
+
+
+def test_three_balls_float_in_density_order(sph):
+    # the buoyancy demo (Sec. 4): free balls of density 0.1, 0.3 and 1.0 of the fluid's,
+    # released half-submerged, over 3000 substeps
+    import physics_checks
+    sc = scenes.three_balls_tank(seed=1)
+    sim = sph.Simulation(sc)
+    sim.step(2700)
+    fz = []
+    for _ in range(300):
+        sim.step(1)
+        fz.append([sim.body_wrench(b)[2] for b in (1, 2, 3)])
+    bodies = np.array([sim.body(b) for b in (1, 2, 3)])
+    st = sim.state()
+    physics_checks.three_balls(sc, bodies[:, 2], st["x"][:sc.n_fluid, 2], np.mean(fz, axis=0),
+                               np.abs(bodies[:, 7:10]).max())
     sim.close()
 
 

@@ -15,6 +15,7 @@ from scipy.spatial import cKDTree
 from scipy.spatial.transform import Rotation
 
 import oracle
+import physics_checks
 from paper_2511_15908_gb300 import scenes
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -599,3 +600,17 @@ def test_released_cube_tank_mechanical_energy_never_grows():
     assert es.max() <= e0
     assert es[-1] < e0 - 0.05 * abs(e0)
     assert out["body_new"][1][2] > cube.pose[2] + 0.1
+
+
+def test_three_balls_float_in_density_order():
+    sc = scenes.three_balls_tank(seed=0)
+    s = oracle.System(sc, mode=1)
+    fz = []
+    for it in range(2000):
+        out = s.substep()
+        if it >= 1700:
+            fz.append(out["wrench"][1:4, 2].copy())
+    b = out["body_new"]
+    fluid = out["id"] < sc.n_fluid
+    physics_checks.three_balls(sc, b[1:4, 2], out["x_new"][fluid, 2], np.mean(fz, axis=0),
+                               np.abs(b[1:4, 7:10]).max())

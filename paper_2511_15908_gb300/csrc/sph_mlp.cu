@@ -138,11 +138,14 @@ __global__ void k_adam(float *w, float *m, float *v, const float *g, int n, floa
 // Surrogate input for the grabbed body: pose (x 3, q 4) and velocity (v 3, w 3) of the
 // substep's pose, then a 4 x 4 x 4 grid of cells of edge R = 2h centred on the grab point;
 // per cell (x fastest) the mean density of the fluid particles inside and their
-// mass-weighted mean velocity (zeros for an empty cell).  One thread per descriptor cell
-// scans the grid cells that overlap it in a fixed order (deterministic).
-__global__ void k_descriptor(SimConst c, int grab_body, float *out)
+// mass-weighted mean velocity (zeros for an empty cell).  One warp per descriptor cell:
+// the lanes stride over the grid cells that overlap it, then a fixed shuffle tree sums
+// their partials (deterministic).
+__global__ void __launch_bounds__(256) k_descriptor(SimConst c, int grab_body, float *out)
 {
-    const int cell = threadIdx.x;                  // 0..63
+    const int cell = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);   // 0..63
+    const int lane = threadIdx.x & 31;
+    if (cell >= 64) return;
     const DevBody &B = c.body[grab_body];
     Pose P = body_pose(c, B, c.ctr[0] > 0 ? c.ctr[0] - 1u : 0u);
     double R9[9], xg[3];
@@ -164,7 +167,7 @@ __global__ void k_descriptor(SimConst c, int grab_body, float *out)
         for (int y = g0[1]; y <= g1[1]; ++y) {
             const int base = (z * c.ny + y) * c.nx;
             const int s = (int)c.cell_start[base + g0[0]], e = (int)c.cell_start[base + g1[0] + 1];
-            for (int q = s; q < e; ++q) {
+            for (int q = s + lane; q < e; q += 32) {
                 const float4 x = c.xA[q];
                 const float4 v = c.vA[q];
                 if (__float_as_int(v.w) >= c.nf) continue;          // fluid particles only
@@ -177,20 +180,28 @@ __global__ void k_descriptor(SimConst c, int grab_body, float *out)
                 ++cnt;
             }
         }
-    float *d = out + 13 + 4 * cell;
-    d[0] = cnt ? sr / (float)cnt : 0.0f;
-    d[1] = sm > 0.0f ? svx / sm : 0.0f;
-    d[2] = sm > 0.0f ? svy / sm : 0.0f;
-    d[3] = sm > 0.0f ? svz / sm : 0.0f;
-    if (cell == 0) {
-        for (int a = 0; a < 3; ++a) { out[a] = P.t[a]; out[7 + a] = P.v[a]; out[10 + a] = P.w[a]; }
-        for (int a = 0; a < 4; ++a) out[3 + a] = P.q[a];
+    sr = warp_sum(sr);
+    sm = warp_sum(sm);
+    svx = warp_sum(svx);
+    svy = warp_sum(svy);
+    svz = warp_sum(svz);
+    cnt = warp_sum(cnt);
+    if (lane == 0) {
+        float *d = out + 13 + 4 * cell;
+        d[0] = cnt ? sr / (float)cnt : 0.0f;
+        d[1] = sm > 0.0f ? svx / sm : 0.0f;
+        d[2] = sm > 0.0f ? svy / sm : 0.0f;
+        d[3] = sm > 0.0f ? svz / sm : 0.0f;
+        if (cell == 0) {
+            for (int a = 0; a < 3; ++a) { out[a] = P.t[a]; out[7 + a] = P.v[a]; out[10 + a] = P.w[a]; }
+            for (int a = 0; a < 4; ++a) out[3 + a] = P.q[a];
+        }
     }
 }
 
 cudaError_t launch_descriptor(const SimConst &c, cudaStream_t s, int grab_body, float *d_out)
 {
-    k_descriptor<<<1, 64, 0, s>>>(c, grab_body, d_out);
+    k_descriptor<<<8, 256, 0, s>>>(c, grab_body, d_out);
     return cudaGetLastError();
 }
 

@@ -77,9 +77,33 @@ __device__ __forceinline__ uint32_t kmajor_off(int r, int k)
 }
 
 // Load rows [r0, r0 + rows) x K-chunk [k0, k0 + 64) of an operand into shared memory.
+// A K-contiguous BF16 operand whose rows start on 16-byte boundaries moves 8 elements (one
+// core-matrix row) per 16-byte load, and rows past the operand's end are zero-filled
+// without a load; other operands go element by element.  Both write the same bytes.
 __device__ __forceinline__ void load_chunk(unsigned char *dst, const void *src, int ld, int kcontig,
                                            int f32, int r0, int rows, int nrows, int k0, int K)
 {
+    if (kcontig && !f32 && (ld & 7) == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(src);
+        constexpr int kGroups = kTcKChunk / 8;
+        for (int idx = threadIdx.x; idx < rows * kGroups; idx += kTcThreads) {
+            const int r = idx / kGroups, k = (idx % kGroups) * 8;
+            const int gr = r0 + r, gk = k0 + k;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (gr < nrows && gk < K) {
+                const __nv_bfloat16 *row = b + (size_t)gr * ld + gk;
+                if (gk + 8 <= K) {
+                    v = __ldg(reinterpret_cast<const uint4 *>(row));
+                } else {
+                    __align__(16) __nv_bfloat16 e[8];
+                    for (int j = 0; j < 8; ++j) e[j] = gk + j < K ? row[j] : __float2bfloat16_rn(0.0f);
+                    v = *reinterpret_cast<const uint4 *>(e);
+                }
+            }
+            *reinterpret_cast<uint4 *>(dst + kmajor_off(r, k)) = v;
+        }
+        return;
+    }
     const int total = rows * kTcKChunk;
     for (int idx = threadIdx.x; idx < total; idx += kTcThreads) {
         int r, k;
@@ -93,7 +117,7 @@ __device__ __forceinline__ void load_chunk(unsigned char *dst, const void *src, 
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(TcGemm g)
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(TcGemm g, int ntile)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sA = smem;
@@ -103,8 +127,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(TcGemm g)
     __shared__ int s_fail;
 
     const int m0 = blockIdx.x * kTcM;
-    const int n0 = blockIdx.y * kTcMaxN;
-    const int nt_raw = min(kTcMaxN, g.N - n0);
+    const int n0 = blockIdx.y * ntile;
+    const int nt_raw = min(ntile, g.N - n0);
     const int nt = (nt_raw + 15) & ~15;              // UMMA N: multiple of 16
     int ncols = 32;
     while (ncols < nt) ncols <<= 1;                  // TMEM allocation: power of two >= 32
@@ -217,8 +241,11 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s)
         configured = true;
     }
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
-    dim3 grid((g.M + kTcM - 1) / kTcM, (g.N + kTcMaxN - 1) / kTcMaxN);
-    k_tc_gemm<<<grid, kTcThreads, kSmemBytes, s>>>(g);
+    // A single row tile (small batches, e.g. one haptic tick) spreads its columns over
+    // CTAs of 32, so that B is loaded by several SMs at once; larger M keeps wide tiles.
+    const int ntile = g.M <= kTcM ? kTcSmallN : kTcMaxN;
+    dim3 grid((g.M + kTcM - 1) / kTcM, (g.N + ntile - 1) / ntile);
+    k_tc_gemm<<<grid, kTcThreads, kSmemBytes, s>>>(g, ntile);
     return cudaGetLastError();
 }
 

@@ -2,7 +2,8 @@
 //
 //   C[M, N] = A[M, K] * B[N, K]^T      (both operands "row = output index, K = contraction")
 //
-// One CTA of 128 threads computes a 128 x Nt tile (Nt <= 256, multiple of 16).  For every
+// One CTA of 128 threads computes a 128 x Nt tile (Nt <= 256, multiple of 16; Nt = 32 when
+// M fits one row tile, so that small batches use several SMs).  For every
 // 64-wide K chunk the threads convert their part of A and B to BF16 and write it to shared
 // memory in the canonical no-swizzle K-major layout (8 x 8 core matrices of 128 bytes:
 // rows of a core matrix 16 B apart, core matrices along K 128 B apart = LBO, 8-row groups
@@ -25,6 +26,7 @@ constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;          // rows per CTA tile (UMMA M)
 constexpr int kTcKChunk = 64;      // K per shared-memory stage
 constexpr int kTcMaxN = 256;       // columns per CTA tile (UMMA N <= 256)
+constexpr int kTcSmallN = 32;      // columns per CTA tile when M fits one row tile
 constexpr unsigned kTcSpin = 1u << 22;
 
 enum TcEpilogue : int {

@@ -104,6 +104,26 @@ __device__ __forceinline__ void load_chunk(unsigned char *dst, const void *src, 
         }
         return;
     }
+    if (!kcontig && !f32 && (ld & 7) == 0 && (r0 & 7) == 0 && (rows & 7) == 0 &&
+        (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        // row-contiguous BF16: 8 rows of one k per 16-byte load, scattered into 8 core-matrix rows
+        const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(src);
+        const int groups = rows / 8;
+        for (int idx = threadIdx.x; idx < groups * kTcKChunk; idx += kTcThreads) {
+            const int r = (idx % groups) * 8, k = idx / groups;
+            const int gr = r0 + r, gk = k0 + k;
+            __align__(16) __nv_bfloat16 e[8];
+            if (gk < K && gr + 8 <= nrows) {
+                *reinterpret_cast<uint4 *>(e) = __ldg(reinterpret_cast<const uint4 *>(b + (size_t)gk * ld + gr));
+            } else {
+                for (int j = 0; j < 8; ++j)
+                    e[j] = (gk < K && gr + j < nrows) ? b[(size_t)gk * ld + gr + j] : __float2bfloat16_rn(0.0f);
+            }
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<__nv_bfloat16 *>(dst + kmajor_off(r + j, k)) = e[j];
+        }
+        return;
+    }
     const int total = rows * kTcKChunk;
     for (int idx = threadIdx.x; idx < total; idx += kTcThreads) {
         int r, k;

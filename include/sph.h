@@ -221,6 +221,16 @@ sph_status sph_step(sph_handle *h, int32_t n_substeps);
  */
 sph_status sph_get_grab_wrench(sph_handle *h, double out[6], int32_t smoothed);
 
+/*
+ * One update cycle of the haptic loop (Sec. 3.3) in a single call: the device pose and
+ * velocity of the grabbed body (as sph_set_grab_pose with grab_point_local = NULL), then
+ * n_substeps substeps (as sph_step), then its wrench, raw or smoothed (as
+ * sph_get_grab_wrench, which synchronises).  Equal, bit for bit, to the three calls.
+ * Errors: those of the three calls, in that order.
+ */
+sph_status sph_haptic_cycle(sph_handle *h, int32_t body_id, const float pose[7], const float vel[6],
+                            int32_t n_substeps, int32_t smoothed, double out[6]);
+
 /* Wrench of any static or rigid body after the last substep (static bodies only with
  * SPH_FLAG_RECORD).  Synchronises. */
 sph_status sph_get_body_wrench(sph_handle *h, int32_t body_id, double out[6]);

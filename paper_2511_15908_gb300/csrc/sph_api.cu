@@ -870,6 +870,17 @@ sph_status sph_checkpoint_load(sph_handle *h, const void *h_buf, size_t bytes)
     return SPH_OK;
 }
 
+sph_status sph_haptic_cycle(sph_handle *h, int32_t body_id, const float pose[7], const float vel[6],
+                            int32_t n_substeps, int32_t smoothed, double out[6])
+{
+    if (!h || !out) return SPH_ERR_ARG;
+    sph_status st = sph_set_grab_pose(h, body_id, pose, vel, nullptr);
+    if (st != SPH_OK) return st;
+    st = sph_step(h, n_substeps);
+    if (st != SPH_OK) return st;
+    return sph_get_grab_wrench(h, out, smoothed);
+}
+
 sph_status sph_get_sort(sph_handle *h, uint32_t *h_keys, int32_t *h_ids, uint32_t *h_cell_start)
 {
     if (!h) return SPH_ERR_ARG;

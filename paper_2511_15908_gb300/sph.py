@@ -38,7 +38,7 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc",
            "sph_iso_grid", "sph_iso_field", "sph_iso_workspace_bytes", "sph_iso_polygonize",
            "sph_set_anchors", "sph_cut_springs", "sph_checkpoint_bytes", "sph_checkpoint_save",
-           "sph_checkpoint_load"]
+           "sph_checkpoint_load", "sph_haptic_cycle"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -168,6 +168,9 @@ def load(path: str = LIB_PATH):
     L.sph_mlp_destroy.argtypes = [_vp]
     L.sph_cell_sort_noalloc.restype = st
     L.sph_cell_sort_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.sph_haptic_cycle.restype = st
+    L.sph_haptic_cycle.argtypes = [_vp, ctypes.c_int32, _f32p, _f32p, ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.POINTER(ctypes.c_double)]
     L.sph_checkpoint_bytes.restype = ctypes.c_size_t
     L.sph_checkpoint_bytes.argtypes = [_vp]
     L.sph_checkpoint_save.restype = st
@@ -329,6 +332,19 @@ class Simulation:
         gl = None if grab_local is None else np.ascontiguousarray(grab_local, np.float32)
         self._check(self.L.sph_set_grab_pose(self.h, body, _ptr(pose, ctypes.c_float),
                                              _ptr(vel, ctypes.c_float), _ptr(gl, ctypes.c_float)))
+
+    def haptic_cycle(self, body: int, pose, vel, n_substeps: int = 1, smoothed: bool = False,
+                     out: Optional[np.ndarray] = None) -> np.ndarray:
+        """Set the grabbed body's pose and velocity, step, and read its wrench, in one call
+        (sph_haptic_cycle).  pose: 7 float32 (x, q wxyz), vel: 6 float32; `out` (6 float64)
+        may be given to avoid an allocation."""
+        pose = np.ascontiguousarray(pose, np.float32)
+        vel = np.ascontiguousarray(vel, np.float32)
+        if out is None:
+            out = np.zeros(6, np.float64)
+        self._check(self.L.sph_haptic_cycle(self.h, body, _ptr(pose, ctypes.c_float), _ptr(vel, ctypes.c_float),
+                                            int(n_substeps), int(smoothed), _ptr(out, ctypes.c_double)))
+        return out
 
     def set_grab_path(self, path):
         path = np.ascontiguousarray(path, np.float32).reshape(-1, 13)

@@ -108,3 +108,26 @@ def test_foreign_or_damaged_checkpoints_are_refused(sph):
     assert np.all(np.isfinite(a.state()["x"]))
     a.close()
     other.close()
+
+
+def test_haptic_cycle_equals_the_three_calls(sph):
+    sc = _grabbed()
+    b = sc.grab_body
+    outs = []
+    for fused in (False, True):
+        sim = sph.Simulation(sc)
+        sim.step(3)
+        ws = []
+        for i in range(6):
+            row = sc.trajectory[10 + i]
+            if fused:
+                ws.append(sim.haptic_cycle(sim.body_ids[b], row[:7], row[7:], 2, smoothed=bool(i % 2)).copy())
+            else:
+                sim.set_grab_pose(sim.body_ids[b], row[:7], row[7:])
+                sim.step(2)
+                ws.append(sim.grab_wrench(smoothed=bool(i % 2)))
+        st = sim.state()
+        outs.append((np.array(ws), st["x"], st["v"], sim.body(b)))
+        sim.close()
+    for u, w in zip(*outs):
+        assert np.array_equal(u, w)

@@ -507,21 +507,27 @@ def surrogate_form(args):
                               "train_steps": steps, "train_s": t_fit, "log_s": t_log,
                               "first_last_loss": [losses[0][1], losses[-1][1]]}
     out["tick_latency_us"] = lat
-    # (b) dam-break pairs (cube grabbed on a seeded random walk): held-out dam-break substeps
-    # (in distribution) and the stirring tank above (transfer to another body and spacing)
-    nd = args.sur_dam_substeps
-    nd_train = int(0.75 * nd)
-    sd = scenes.dam_break(seed=1, grab=True, n_substeps=nd, cube_pos=(0.4, 0.4, 0.2))
+    # (b) dam-break pairs: the cube grabbed along seeded random-walk episodes of 100 substeps
+    # (2000 episodes = 200k pairs); the first 3/4 of the episodes train, the rest are held
+    # out (in distribution); the stirring tank above tests transfer to another body and spacing
+    per_ep = 100
+    nd = args.sur_dam_episodes * per_ep
+    nd_train = (3 * args.sur_dam_episodes // 4) * per_ep
+    sd = scenes.dam_break(seed=1, grab=True, n_substeps=per_ep, cube_pos=(0.4, 0.4, 0.2))
+    sd.trajectory = scenes.episode_trajectory(args.sur_dam_episodes, per_ep, float(sd.params["dt"]),
+                                              (0.4, 0.4, 0.2), (0.08, 0.08, 0.08), (0.42, 0.42, 0.35),
+                                              seed0=1000)
     sim_d = sph.Simulation(sd, max_path=nd + 16)
     d_d, w_d = surrogate.log_run(sim_d, nd)
     dtd = float(np.float32(sd.params["dt"]))
     cyc_d = 17                                   # dt 1e-3 s: ~60 Hz update cycle
     model_d = sph.Surrogate(max_batch=2048)
     xd_, yd_ = surrogate.lagged_inputs(d_d, cyc_d, dtd), surrogate.residual_targets(w_d, cyc_d)
-    surrogate.fit(model_d, xd_[:nd_train], yd_[:nd_train], steps=1500, batch=1024, lr=1e-3)
+    surrogate.fit(model_d, xd_[:nd_train], yd_[:nd_train], steps=3000, batch=1024, lr=1e-3)
     ev_in = surrogate.haptic_errors(d_d[nd_train:], w_d[nd_train:], model_d, cyc_d, 1, dtd)
     ev_tr = surrogate.haptic_errors(desc[n_train:], wr[n_train:], model_d, cycle, tick, dt)
-    out["dam_break_trained"] = {"train_pairs": nd_train, "held_out_dam_break_1khz": ev_in,
+    out["dam_break_trained"] = {"train_pairs": nd_train, "episodes": args.sur_dam_episodes,
+                                "substeps_per_episode": per_ep, "held_out_dam_break_1khz": ev_in,
                                 "transfer_to_stirring_1khz": ev_tr}
     out["target_rel_force_err"] = 0.05
     for m_ in (model, model_d):
@@ -740,7 +746,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / surrogate forms")
     ap.add_argument("--sur-substeps", type=int, default=32000)
-    ap.add_argument("--sur-dam-substeps", type=int, default=40000)
+    ap.add_argument("--sur-dam-episodes", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -208,6 +208,18 @@ def random_walk_trajectory(rng, n_sub, dt, start, lo, hi, sigma=0.05, vmax=0.5):
     return traj.astype(np.float32)
 
 
+def episode_trajectory(n_episodes, per_episode, dt, start, lo, hi, seed0=0, sigma=0.02, vmax=0.4):
+    """A grab path of n_episodes seeded random-walk episodes of per_episode substeps (seeds
+    seed0, seed0 + 1, ...), each starting at rest where the previous one ended."""
+    parts, x = [], np.asarray(start, np.float64)
+    for e in range(n_episodes):
+        seg = random_walk_trajectory(np.random.default_rng(seed0 + e), per_episode, dt, x, lo, hi,
+                                     sigma=sigma, vmax=vmax)
+        parts.append(seg)
+        x = seg[-1, 0:3].astype(np.float64)
+    return np.concatenate(parts)
+
+
 def dam_break(seed=0, n_side=16, n_substeps=100, grab=False, cube_pos=(0.4, 0.25, 0.12)):
     """3D dam break: n_side^3 fluid at 0.02 m, 0.5 m static box, one free 0.1 m cube (density 500)."""
     rng = np.random.default_rng(seed)

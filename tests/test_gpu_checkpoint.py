@@ -131,3 +131,19 @@ def test_haptic_cycle_equals_the_three_calls(sph):
         sim.close()
     for u, w in zip(*outs):
         assert np.array_equal(u, w)
+
+
+def test_readme_example_runs(sph):
+    # the usage example of the README, verbatim apart from the assertions
+    sc = scenes.dam_break(seed=0, grab=True)
+    sim = sph.Simulation(sc)
+    b = sim.body_ids[sc.grab_body]
+    for row in sc.trajectory[:60]:
+        wrench = sim.haptic_cycle(b, row[:7], row[7:], n_substeps=1)
+    assert wrench.shape == (6,) and np.all(np.isfinite(wrench))
+    ck = sim.checkpoint()
+    sim.close()
+    sim2 = sph.Simulation(sc)
+    sim2.restore(ck)
+    assert sim2.info()[4] == 60
+    sim2.close()

@@ -619,9 +619,12 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
         const float inv_mi = 1.0f / mi;
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
         if (!skip) {
-            auto pair = [&](float4 xj, float4 vj, float2 pj, float dx, float dy, float dz, float r2) {
+            // check_own: skip the particle's own rigid body (the neighbour list has no such
+            // entries, so only the re-search needs the test)
+            auto pair = [&](float4 xj, float4 vj, float2 pj, float dx, float dy, float dz, float r2,
+                            bool check_own) {
                 int jd = __float_as_int(vj.w);
-                if ((unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
+                if (check_own && (unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
                 const bool bi = xi.w < 0.0f, bj = xj.w < 0.0f;
                 if (vol && bi && bj) return;       // volume boundaries: no boundary pairs
                 float rinv = 0.0f;                 // coincident particles: no force
@@ -683,7 +686,7 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                             if (j0 + j < m) {
                                 float dx, dy, dz;
                                 const float r2 = dist2(xi, xs[j], dx, dy, dz);
-                                pair(xs[j], vs[j], ps[j], dx, dy, dz, r2);
+                                pair(xs[j], vs[j], ps[j], dx, dy, dz, r2, false);
                             }
                         }
                     }
@@ -695,7 +698,7 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                         const float4 xj = __ldg(c.xA + q);
                         float dx, dy, dz;
                         const float r2 = dist2(xi, xj, dx, dy, dz);
-                        pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2);
+                        pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2, false);
                     }
 #endif
                 }
@@ -707,7 +710,7 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                         const float4 xj = __ldg(c.xA + q);
                         float dx, dy, dz;
                         const float r2 = dist2(xi, xj, dx, dy, dz);
-                        if (r2 < c.R2) pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2);
+                        if (r2 < c.R2) pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2, true);
                     }
                 });
             }

@@ -6,7 +6,7 @@
 // Measured on the 1.16 M-particle coupled scene: density in 512-thread blocks, 2 per SM (62
 // registers) 305 us, against 317 for 256 x 4, 354 for 256 x 6 (40 registers), 320 for
 // 128 x 8 and 316 for 1024 x 1; force in 256-thread blocks, 5 per SM, with two neighbours'
-// loads in flight 147 us against 155 at 4 and 175 at 6.  Scenes too small to fill two
+// loads in flight 136 us against 146 at 4 and 158 at 6.  Scenes too small to fill two
 // waves of the wide blocks (kDensityWideMin particles) take 256 x 4: on 64 scenes of
 // 8k-256k particles the wide blocks alone cost 4 % more.
 #ifndef SPH_DENSITY_THREADS

@@ -446,7 +446,7 @@ struct ListWriter {
     uint4 *dst;                // this particle's quad 0; quad g at dst[g * n]
     size_t n;
     int cap, nl = 0;
-    uint4 quad;
+    uint4 quad = make_uint4(0u, 0u, 0u, 0u);   // the last four entries pushed
     __device__ __forceinline__ void push(uint32_t q)
     {
         quad = make_uint4(quad.y, quad.z, quad.w, q);

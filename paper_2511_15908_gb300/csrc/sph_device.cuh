@@ -770,10 +770,22 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
     // FP32 within the warp, FP64 above it; the last warp of the block to finish sums the
     // per-warp partials in a fixed order (no block barrier, so no warp waits for another)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    {
+        // the 8 warp sums by a halving exchange: after the xor-16, -8 and -4 steps each lane
+        // holds one component (bits 4, 3, 2 of the lane pick it), then xor-2 and -1 finish
+        const unsigned full = 0xffffffffu;
+        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+        float v4[4], v2[2];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        float s = warp_sum(dg[a]);
-        if (lane == 0) sd[wid][a] = (double)s;
+        for (int k = 0; k < 4; ++k)
+            v4[k] = (h16 ? dg[k + 4] : dg[k]) + __shfl_xor_sync(full, h16 ? dg[k] : dg[k + 4], 16);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            v2[k] = (h8 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(full, h8 ? v4[k] : v4[k + 2], 8);
+        float v1 = (h4 ? v2[1] : v2[0]) + __shfl_xor_sync(full, h4 ? v2[0] : v2[1], 4);
+        v1 += __shfl_xor_sync(full, v1, 2);
+        v1 += __shfl_xor_sync(full, v1, 1);
+        if ((lane & 3) == 0) sd[wid][(h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0)] = (double)v1;
     }
     unsigned last = 0;
     if (lane == 0) {

@@ -478,6 +478,40 @@ def cloth_form(args, flush_l2_factory):
                     "sph_cut_springs call with a full-width blade between two columns"}
 
 
+def size_sweep_form(args, flush_l2_factory, sc_main):
+    """Substep time against particle count (the paper relates particle count to frame rate):
+    the dam break (4,096 fluid), the stirring tank (250k fluid) and the coupled scene (1M
+    fluid), each 10 warm-up and 50 timed substeps with an L2 flush before each, CUDA events
+    on the simulation's stream."""
+    import torch
+    from paper_2511_15908_gb300 import scenes, sph
+    out = {}
+    for name, sc in (("dam_break_4k", scenes.dam_break(seed=0)),
+                     ("stirring_250k", scenes.stirring_tank(seed=0, n_substeps=64)),
+                     ("coupled_1M", sc_main)):
+        sim = sph.Simulation(sc)
+        flush = flush_l2_factory(sim.stream)
+        domain = [0]
+        for _ in range(10):
+            flush()
+            sim.step(1)
+        _reported(sim.sync, domain, sph)
+        n = 50
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for e0, e1 in ev:
+            flush()
+            e0.record(sim.stream)
+            sim.step(1)
+            e1.record(sim.stream)
+        _reported(sim.sync, domain, sph)
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        out[name] = {"particles_all": int(sc.n_total), "particles_fluid": int(sc.n_fluid),
+                     "ms_per_substep": ms, "substeps_per_s": 1e3 / ms,
+                     "fluid_particle_steps_per_s": sc.n_fluid / (ms / 1e3)}
+        sim.close()
+    return out
+
+
 def surrogate_form(args):
     """The learned wrench surrogate: the BF16 tcgen05 MLP at 1 kHz haptic ticks on the stirring tank
     (250k fluid), trained on the GPU from logged (descriptor, wrench) pairs: (a) pairs logged
@@ -703,6 +737,7 @@ def run_ours(args):
             "sum_boundary W; the density interval includes the psi pass)")
         forms["isosurface"] = isosurface_form(args, sc)
         forms["cloth"] = cloth_form(args, factory)
+        forms["size_sweep"] = size_sweep_form(args, factory, sc)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -405,6 +405,36 @@ def test_two_particle_spring_period():
     assert period == pytest.approx(T, rel=0.01)
 
 
+def test_two_particle_spring_damping_ratio():
+    # with c_d = 2 zeta sqrt(k_s m / 2) the relative coordinate u of two particles on one
+    # spring obeys u'' + (2 c_d / m) u' + (2 k_s / m) u = 0, a damped oscillator of damping
+    # ratio exactly zeta: successive maxima of u shrink by exp(-2 pi zeta / sqrt(1 - zeta^2))
+    # (a wrong sign, factor or mass in the damping term changes the ratio)
+    s_ = 0.02
+    p = _params(h=s_, dt=2e-5, nu=0.0, lo=(-0.1, -0.1, -0.1), hi=(0.1, 0.1, 0.1))
+    zeta = 0.1
+    p["spring_zeta"] = zeta
+    rest = np.array([[0, 0, 0], [s_, 0, 0]], np.float32)
+    start = np.array([[0, 0, 0], [1.1 * s_, 0, 0]], np.float32)
+    b = scenes.Body(scenes.KIND_SOFT, rest, s_, springs=np.array([[0, 1]], np.int32), young=50.0)
+    sc = scenes.Scene("spring", p, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                      s_, [b])
+    sysm = oracle.System(sc, mode=0)
+    sysm.x = start.copy()
+    m, ks = 1000.0 * s_ ** 3, 50.0 * s_
+    T = 2 * np.pi * np.sqrt(m / (2 * ks))
+    ext = []
+    for _ in range(int(2.3 * T / p["dt"])):
+        out = sysm.substep()
+        xs = sysm.by_id(out["x_new"])
+        ext.append(xs[1, 0] - xs[0, 0] - s_)
+    ext = np.asarray(ext)
+    peaks = np.nonzero((ext[1:-1] > ext[:-2]) & (ext[1:-1] >= ext[2:]) & (ext[1:-1] > 0))[0] + 1
+    assert len(peaks) >= 2
+    ratio = ext[peaks[1]] / ext[peaks[0]]
+    assert ratio == pytest.approx(np.exp(-2 * np.pi * zeta / np.sqrt(1 - zeta ** 2)), rel=0.01)
+
+
 def test_boxcar_smoothing():
     const = np.tile(np.arange(6, dtype=np.float64), (50, 1))
     np.testing.assert_allclose(oracle.boxcar(const, 20), const)

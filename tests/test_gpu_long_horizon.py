@@ -5,6 +5,7 @@
   and the cube together carry the fluid's weight (Sec. 3.2 two-way coupling);
 - free balls of density 0.1, 0.3 and 1.0 of the fluid's settle in that order, the light ones
   floating (the Sec. 4 buoyancy demo);
+- a torque-free asymmetric top keeps its world-frame angular momentum while it tumbles;
 - fluid and a released buoyant cube in a closed tank, undriven, never gain mechanical energy
   over 3000 substeps;
 - a stirred coupled scene with a soft body stays finite, with at most a few spray particles
@@ -67,6 +68,24 @@ def test_three_balls_float_in_density_order(sph):
     st = sim.state()
     physics_checks.three_balls(sc, bodies[:, 2], st["x"][:sc.n_fluid, 2], np.mean(fz, axis=0),
                                np.abs(bodies[:, 7:10]).max())
+    sim.close()
+
+
+def test_torque_free_asymmetric_top_conserves_angular_momentum(sph):
+    # the GPU's FP64 rigid update over 5000 substeps (the oracle pin's statement)
+    import physics_checks
+    sc, I, w0 = physics_checks.asymmetric_top_scene()
+    sim = sph.Simulation(sc)
+    L0, E0 = physics_checks.top_momentum_energy(sim.body(0), I)
+    w_change = 0.0
+    for _ in range(100):
+        sim.step(50)
+        st = sim.body(0)
+        L, E = physics_checks.top_momentum_energy(st, I)
+        assert np.linalg.norm(L - L0) <= 1e-3 * np.linalg.norm(L0)
+        w_change = max(w_change, np.linalg.norm(st[10:13] - w0) / np.linalg.norm(w0))
+    assert E == pytest.approx(E0, rel=1e-3)
+    assert w_change > 0.1
     sim.close()
 
 

@@ -376,6 +376,25 @@ def test_rigid_body_free_flight():
     assert np.all(out["wrench"] == 0)
 
 
+def test_torque_free_asymmetric_top_conserves_angular_momentum():
+    # spin about no principal axis: omega changes (Euler's equations, through the
+    # gyroscopic term omega x I omega) while the world-frame angular momentum R I R^T omega
+    # and the kinetic energy stay fixed; a wrong sign or frame of the gyroscopic term, or
+    # of the inertia transform, breaks them at order one
+    sc, I, w0 = physics_checks.asymmetric_top_scene()
+    s = oracle.System(sc, mode=0)
+    L0, E0 = physics_checks.top_momentum_energy(s.body_state(0), I)
+    w_change = 0.0
+    for _ in range(5000):
+        s.substep()
+        st = s.body_state(0)
+        L, E = physics_checks.top_momentum_energy(st, I)
+        assert np.linalg.norm(L - L0) <= 1e-3 * np.linalg.norm(L0)
+        w_change = max(w_change, np.linalg.norm(st[10:13] - w0) / np.linalg.norm(w0))
+    assert E == pytest.approx(E0, rel=1e-3)
+    assert w_change > 0.1                      # the body really tumbles
+
+
 def test_two_particle_spring_period():
     # soft body of two particles and one spring, no SPH pressure (clamped), no viscosity,
     # no damping: relative motion has period 2 pi sqrt(m / (2 k_s))

@@ -351,6 +351,38 @@ def test_fp32_rotation_matches_scipy():
         np.testing.assert_allclose(oracle.body_point_f32(R.ravel(), t, l), ref @ l + t, atol=2e-6)
 
 
+def test_grabbed_body_places_its_particles_and_their_velocities():
+    # Sec. 3.2: a driven body's particles sit at fixed offsets in its frame, x = R(q) l + t,
+    # and move with it, v = v_b + w x (x - t); checked against scipy's rotation, for a
+    # rotated pose and a spinning path row, over two substeps of the path
+    p = _params(lo=(-0.5, -0.5, -0.5), hi=(0.5, 0.5, 0.5))
+    loc, _ = scenes.solid_box((0.04, 0.02, 0.06), 0.01)
+    rng = np.random.default_rng(3)
+    traj = np.zeros((2, 13), np.float32)
+    for k in range(2):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        traj[k, 0:3] = rng.uniform(-0.1, 0.1, 3)
+        traj[k, 3:7] = q
+        traj[k, 7:10] = rng.normal(0, 0.3, 3)
+        traj[k, 10:13] = rng.normal(0, 3.0, 3)
+    b = scenes.Body(scenes.KIND_RIGID, loc, 0.01, mass=0.3,
+                    inertia=scenes._box_inertia(0.3, (0.04, 0.02, 0.06)), pose=traj[0, :7])
+    sc = scenes.Scene("grab", p, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32),
+                      0.02, [b], grab_body=0, trajectory=traj)
+    s = oracle.System(sc, mode=0)
+    for k in range(2):
+        out = s.substep()
+        x = s.by_id(out["x_new"]).astype(np.float64)
+        v = s.by_id(out["v_new"]).astype(np.float64)
+        row = traj[k].astype(np.float64)
+        R = Rotation.from_quat([row[4], row[5], row[6], row[3]]).as_matrix()
+        x_ref = loc.astype(np.float64) @ R.T + row[0:3]
+        v_ref = row[7:10] + np.cross(row[10:13], x_ref - row[0:3])
+        np.testing.assert_allclose(x, x_ref, atol=2e-7)
+        np.testing.assert_allclose(v, v_ref, atol=2e-6)
+
+
 def test_rigid_body_free_flight():
     # an isolated rigid body: no pair forces, so it falls with g and spins torque-free
     p = _params(lo=(-1, -1, -1), hi=(1, 1, 1))

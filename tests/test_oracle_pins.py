@@ -383,6 +383,36 @@ def test_grabbed_body_places_its_particles_and_their_velocities():
         np.testing.assert_allclose(v, v_ref, atol=2e-6)
 
 
+def test_free_body_responds_to_its_wrench_by_newton_euler():
+    # a free body at rest, rotated, with compressed fluid pressing on one side: after one
+    # substep v = (F / M + g) dt and w = I_w^-1 tau dt, I_w = R I_b R^T, with F and tau the
+    # wrench the substep reports (torque about the centre of mass); a body-frame inertia
+    # used in the world frame, or a sign slip, fails this
+    p = _params(lo=(-0.3, -0.3, -0.3), hi=(0.3, 0.3, 0.3), h=0.02, dt=1e-4)
+    size = (0.06, 0.04, 0.08)
+    loc, _ = scenes.solid_box(size, 0.01)
+    M = 0.5
+    I_b = scenes._box_inertia(M, size).astype(np.float64)
+    q = np.array([0.9, 0.2, -0.3, 0.25])
+    q /= np.linalg.norm(q)
+    body = scenes.Body(scenes.KIND_RIGID, loc, 0.01, mass=M, inertia=I_b.astype(np.float32),
+                       pose=np.array([0, 0, 0, *q], np.float32))
+    # a slab of fluid squeezed to 0.8 of its spacing against the body's +x side, off-centre
+    g = np.stack(np.meshgrid(np.arange(4), np.arange(6), np.arange(3), indexing="ij"), -1).reshape(-1, 3)
+    fluid = (g * 0.016 + np.array([0.045, -0.02, 0.01])).astype(np.float32)
+    sc = scenes.Scene("push", p, fluid, np.zeros_like(fluid), 0.02, [body])
+    s = oracle.System(sc, mode=0)
+    out = s.substep()
+    F, tau = out["wrench"][0, :3], out["wrench"][0, 3:]
+    assert np.linalg.norm(F) > 1e-3 and np.linalg.norm(tau) > 1e-5   # a real push and twist
+    st = s.body_state(0).astype(np.float64)
+    dt = p["dt"]
+    np.testing.assert_allclose(st[7:10], (F / M + np.asarray(p["g"])) * dt, rtol=1e-5, atol=1e-9)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+    I_w = R @ I_b @ R.T
+    np.testing.assert_allclose(st[10:13], np.linalg.solve(I_w, tau) * dt, rtol=1e-4, atol=1e-9)
+
+
 def test_rigid_body_free_flight():
     # an isolated rigid body: no pair forces, so it falls with g and spins torque-free
     p = _params(lo=(-1, -1, -1), hi=(1, 1, 1))

@@ -59,12 +59,14 @@ def test_single_process_passes_through():
 
 
 def test_cancellation_ratios_rebuild_the_oracle_wrench():
-    # the per-particle pair forces and the grab point the ratios use must give back the
-    # oracle's own wrench; a ratio is at least 1 (triangle inequality)
+    # the per-particle pair forces and the grab point R(q) l_g + t the ratios use must give
+    # back the oracle's own wrench; a ratio is at least 1 (triangle inequality)
     from paper_2511_15908_gb300 import scenes
     bench = _bench()
     sc = scenes.with_velocity_noise(scenes.dam_break(seed=3, grab=True, cube_pos=(0.2, 0.2, 0.15)),
                                     seed=3, sigma=0.3)
+    # a grab point off the centre of mass: the torque is taken about it
+    sc.bodies[sc.grab_body].grab_local = np.array([0.02, -0.01, 0.03], np.float32)
     _, out, m = bench._oracle_substep_time(sc)
     k = bench._cancellation(sc, out, m, sc.grab_body)
     w = out["wrench"][sc.grab_body]

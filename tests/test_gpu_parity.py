@@ -147,6 +147,14 @@ def test_dam_break_grabbed_cube(sph):
     check_one_substep(sph, sc, mode=0)
 
 
+def test_grab_point_off_the_centre_of_mass(sph):
+    # the coupling torque is taken about the grab point R(q) l_g + t (Sec. 3.3)
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=7, grab=True, cube_pos=(0.2, 0.2, 0.15)),
+                                    seed=7, sigma=0.3)
+    sc.bodies[sc.grab_body].grab_local = np.array([0.02, -0.01, 0.03], np.float32)
+    check_one_substep(sph, sc, mode=0)
+
+
 def test_stirring_tank_reduced(sph):
     sc = scenes.with_velocity_noise(
         scenes.stirring_tank(seed=0, n_fluid=30_000, cols=(50, 50), tank=(0.4, 0.4, 0.3),

@@ -147,3 +147,29 @@ def test_readme_example_runs(sph):
     sim2.restore(ck)
     assert sim2.info()[4] == 60
     sim2.close()
+
+
+def test_released_body_is_a_free_body(sph):
+    # release (body id -1) leaves the body free with its last pose and velocity: stepping
+    # on equals, bit for bit, a scene that had the free body from the start
+    grabbed = scenes.with_velocity_noise(
+        scenes.dam_break(seed=8, grab=True, cube_pos=(0.2, 0.2, 0.15)), seed=8, sigma=0.3)
+    row = grabbed.trajectory[0]
+    free = scenes.with_velocity_noise(
+        scenes.dam_break(seed=8, grab=True, cube_pos=(0.2, 0.2, 0.15)), seed=8, sigma=0.3)
+    b = free.grab_body
+    free.bodies[b].pose = row[:7].copy()
+    free.bodies[b].vel = row[7:].copy()
+    free.grab_body, free.trajectory = -1, None
+    a = sph.Simulation(grabbed)
+    a.set_grab_pose(-1, None)
+    c = sph.Simulation(free)
+    outs = []
+    for sim in (a, c):
+        sim.step(25)
+        st = sim.state()
+        outs.append((st["x"], st["v"], sim.body(b), sim.body_wrench(b)))
+        sim.close()
+    for u, w in zip(*outs):
+        assert np.array_equal(u, w)
+    assert not np.array_equal(outs[0][2][7:10], row[7:10])     # it moved under gravity

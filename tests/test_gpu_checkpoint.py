@@ -173,3 +173,43 @@ def test_released_body_is_a_free_body(sph):
     for u, w in zip(*outs):
         assert np.array_equal(u, w)
     assert not np.array_equal(outs[0][2][7:10], row[7:10])     # it moved under gravity
+
+
+def test_set_state_overwrites_fluid_and_soft_particles(sph):
+    # two scenes with the same bodies and body states but different fluid states
+    s2 = scenes.with_velocity_noise(scenes.tiny(seed=1, n=(8, 8, 8)), seed=12, sigma=0.3)
+    s1 = scenes.with_velocity_noise(scenes.tiny(seed=1, n=(8, 8, 8)), seed=12, sigma=0.3)
+    rng = np.random.default_rng(13)
+    s1.fluid_v = rng.normal(0.0, 0.3, s1.fluid_v.shape).astype(np.float32)
+    s1.fluid_x = (s1.fluid_x + rng.uniform(-1e-3, 1e-3, s1.fluid_x.shape)).astype(np.float32)
+    st2 = sph.Simulation(s2).state()                # id order, fluid and bodies
+    ref = sph.Simulation(s2)
+    ref.step(1)
+    want = ref.state()
+    # before the first substep: the handle becomes the other scene, bit for bit
+    a = sph.Simulation(s1)
+    a.set_state(st2["x"], st2["v"])
+    a.step(1)
+    got = a.state()
+    assert np.array_equal(got["x"], want["x"]) and np.array_equal(got["v"], want["v"])
+    # after substeps of its own (its free rigid body has moved): the next substep agrees
+    # with a fresh handle holding the same fluid state and the body where it now is (the
+    # slot order it sorts from, and with it the order of each sum, differs)
+    b = sph.Simulation(s1)
+    b.step(5)
+    s3 = scenes.with_velocity_noise(scenes.tiny(seed=1, n=(8, 8, 8)), seed=12, sigma=0.3)
+    for i, body in enumerate(s3.bodies):
+        if body.kind == scenes.KIND_RIGID:
+            row = b.body(i)
+            body.pose, body.vel = row[:7].copy(), row[7:13].copy()
+    b.set_state(st2["x"], st2["v"])
+    b.step(1)
+    c = sph.Simulation(s3)
+    c.step(1)
+    got, want3 = b.state(), c.state()
+    nf = s2.n_fluid
+    assert np.abs(got["x"][:nf] - want3["x"][:nf]).max() < 1e-6
+    vscale = max(1.0, np.abs(want3["v"][:nf]).max())
+    assert np.abs(got["v"][:nf] - want3["v"][:nf]).max() < 1e-3 * vscale
+    for sim in (ref, a, b, c):
+        sim.close()

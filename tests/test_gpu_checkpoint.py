@@ -213,3 +213,20 @@ def test_set_state_overwrites_fluid_and_soft_particles(sph):
     assert np.abs(got["v"][:nf] - want3["v"][:nf]).max() < 1e-3 * vscale
     for sim in (ref, a, b, c):
         sim.close()
+
+
+def test_new_grab_path_mid_run_starts_at_its_first_row(sph):
+    sc = scenes.dam_break(seed=6, grab=True, n_substeps=200, cube_pos=(0.3, 0.3, 0.15))
+    b = sc.grab_body
+    sim = sph.Simulation(sc)
+    sim.step(10)
+    rng = np.random.default_rng(4)
+    path = scenes.random_walk_trajectory(rng, 30, float(sc.params["dt"]), (0.25, 0.25, 0.2),
+                                         (0.08, 0.08, 0.08), (0.42, 0.42, 0.35), sigma=0.05, vmax=0.5)
+    sim.set_grab_path(path)
+    for k in range(1, 8):
+        sim.step(1)
+        np.testing.assert_array_equal(sim.body(b)[:7], path[k - 1, :7])
+    sim.step(25)                                 # past the path's end: it holds the last row
+    np.testing.assert_array_equal(sim.body(b)[:7], path[-1, :7])
+    sim.close()

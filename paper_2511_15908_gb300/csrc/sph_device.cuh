@@ -410,7 +410,129 @@ __device__ __forceinline__ void rank_gather_item(const SimConst &c, int blk)
 
 // ------------------------------------------------------------------- density pass
 
-// Compensated sum of m_j * 6 w(q_ij) over a particle's neighbours (see below).
+// Error-free transformations (Knuth's TwoSum; Dekker's Fast2Sum for |a| >= |b|; the FMA
+// product residual).  Every operation is an explicit round-to-nearest intrinsic, so the
+// compiler neither contracts nor reorders them.
+__device__ __forceinline__ float two_sum(float a, float b, float &err)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// (th + tl)^3 as hi + lo for a small tl: th^3 exactly as t3 + e3 + e2 th (two FMA
+// residuals), plus the first-order term 3 th^2 tl.
+__device__ __forceinline__ float cube_pair(float th, float tl, float &lo)
+{
+    const float t2 = __fmul_rn(th, th), e2 = __fmaf_rn(th, th, -t2);
+    const float t3 = __fmul_rn(t2, th), e3 = __fmaf_rn(t2, th, -t3);
+    lo = __fmaf_rn(__fmul_rn(3.0f, t2), tl, __fmaf_rn(e2, th, e3));
+    return t3;
+}
+
+// The low part of an FP32 difference: (a - b) - fl(a - b), exact (TwoSum of a and -b).
+// Nonzero only when a or b lies near zero (for |a| >= 2|a - b| the difference is exact).
+__device__ __forceinline__ float diff_lo(float a, float b, float d)
+{
+    const float bb = __fsub_rn(d, a);
+    return __fadd_rn(__fsub_rn(a, __fsub_rn(d, bb)), __fsub_rn(-b, bb));
+}
+
+// Sum of m_j * 6 w(q_ij) over a particle's neighbours with an error of a few units of the
+// second order in FP32 rounding (~1e-13 relative), i.e. as good as the FP64 definition for
+// the pressure the force pass needs: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000
+// (6e-5) into a pressure change that moves wall-adjacent accelerations by ~1e-4 m/s^2,
+// and every FP32 stage of the plain evaluation (r^2, sqrt, q, the cubic, the product with
+// m, the summation) costs about that much.  So each stage carries its rounding error:
+// r^2 = dx^2 + dy^2 + dz^2 from FMA product residuals and TwoSums, r = sqrt(r^2) and
+// q = r / h as float pairs (Newton residual, 1/h as a float pair), 6 w = t^3 - 4 u^3 with
+// t = 2 - q and u = max(1 - q, 0) as pairs and both cubes as pairs (Fast2Sum for the
+// difference, t^3 >= 4 u^3), the term m 6w as a pair, and the running sum by TwoSum; all
+// low parts are summed in L.  The value is S + L.
+struct PairDensitySum {
+    float S = 0.0f, L = 0.0f;
+    int cnt = 0;
+    // the particle itself (q = 0: 6 w = 4)
+    __device__ __forceinline__ void self(float mi)
+    {
+        S = __fmul_rn(4.0f, mi);
+        cnt = 1;
+    }
+    // neighbour of weight (mh + ml) at d = x_j - x_i (FP32 differences; r2x = the first-order
+    // r^2 correction 2 d . d_lo when a difference was not exact)
+    __device__ __forceinline__ void add(const SimConst &c, float mh, float ml, float dx, float dy,
+                                        float dz, float r2x)
+    {
+        const float px = __fmul_rn(dx, dx), py = __fmul_rn(dy, dy), pz = __fmul_rn(dz, dz);
+        const float ex = __fmaf_rn(dx, dx, -px), ey = __fmaf_rn(dy, dy, -py);
+        const float ez = __fmaf_rn(dz, dz, -pz);
+        float e1, e2;
+        const float s1 = two_sum(px, py, e1);
+        const float r2h = two_sum(s1, pz, e2);
+        const float r2l = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), __fadd_rn(__fadd_rn(e1, e2), r2x));
+        // r: rsqrt, one Newton step, then the residual r2 - r^2 over 2r
+        const float rs = rsqrtf(fmaxf(r2h, 1e-30f));
+        const float hrs = __fmul_rn(0.5f, rs);
+        float r = __fmul_rn(r2h, rs);
+        r = __fmaf_rn(hrs, __fmaf_rn(-r, r, r2h), r);
+        const float rl = __fmul_rn(__fadd_rn(__fmaf_rn(-r, r, r2h), r2l), hrs);
+        // q = r (1/h)_hi + r (1/h)_lo + rl (1/h)_hi
+        const float qh = __fmul_rn(r, c.invh_hi);
+        const float ql = __fadd_rn(__fmaf_rn(r, c.invh_hi, -qh),
+                                   __fmaf_rn(r, c.invh_lo, __fmul_rn(rl, c.invh_hi)));
+        // t = 2 - q: 2 - th and (2 - th) - qh are exact (Sterbenz); likewise u = 1 - q
+        const float th = __fsub_rn(2.0f, qh);
+        const float tl = __fsub_rn(__fsub_rn(__fsub_rn(2.0f, th), qh), ql);
+        float uh = __fsub_rn(1.0f, qh);
+        float ul = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, uh), qh), ql);
+        if (!(uh > 0.0f)) { uh = 0.0f; ul = 0.0f; }
+        float t3l, u3l;
+        const float t3 = cube_pair(th, tl, t3l);
+        const float u3 = cube_pair(uh, ul, u3l);
+        const float m4u3 = __fmul_rn(-4.0f, u3);                 // exact
+        const float w6h = __fadd_rn(t3, m4u3);
+        const float w6l = __fadd_rn(__fsub_rn(m4u3, __fsub_rn(w6h, t3)), __fmaf_rn(-4.0f, u3l, t3l));
+        // term (mh + ml)(w6h + w6l)
+        const float th_ = __fmul_rn(mh, w6h);
+        const float lo = __fmaf_rn(ml, w6h, __fmaf_rn(mh, w6l, __fmaf_rn(mh, w6h, -th_)));
+        float es;
+        S = two_sum(S, th_, es);
+        L = __fadd_rn(L, __fadd_rn(lo, es));
+        ++cnt;
+    }
+    // alpha/6 (S + L) - rho0 with alpha/6 = hi + lo
+    __device__ __forceinline__ float excess(const SimConst &c, float rho0) const
+    {
+        return __fadd_rn(__fmaf_rn(c.alpha6_hi, S, -rho0),
+                         __fmaf_rn(c.alpha6_lo, S, __fmul_rn(c.alpha6_hi, L)));
+    }
+};
+
+// d = x_j - x_i with the first-order r^2 correction of inexact differences (only particles
+// within 2R of a coordinate plane through the origin can have them).
+__device__ __forceinline__ void pair_offset(float4 xi, float4 xj, bool near0, float &dx, float &dy,
+                                            float &dz, float &r2x)
+{
+    dx = __fsub_rn(xj.x, xi.x);
+    dy = __fsub_rn(xj.y, xi.y);
+    dz = __fsub_rn(xj.z, xi.z);
+    r2x = 0.0f;
+    if (near0) {
+        const float lx = diff_lo(xj.x, xi.x, dx), ly = diff_lo(xj.y, xi.y, dy);
+        const float lz = diff_lo(xj.z, xi.z, dz);
+        r2x = __fmul_rn(2.0f, __fmaf_rn(dx, lx, __fmaf_rn(dy, ly, __fmul_rn(dz, lz))));
+    }
+}
+
+__device__ __forceinline__ bool near_origin_planes(const SimConst &c, float4 x)
+{
+    const float lim = 4.0f * c.h;                 // 2R
+    return fabsf(x.x) < lim || fabsf(x.y) < lim || fabsf(x.z) < lim;
+}
+
+// Compensated FP32 sum of m_j * 6 w(q_ij) (Kahan), for the isosurface field, whose
+// tolerance is far looser than the pressure's.
 struct DensitySum {
     float S = 0.0f, C = 0.0f;
     int cnt = 0;
@@ -470,12 +592,8 @@ struct ListWriter {
     }
 };
 
-// Density to a few 1e-8: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000 into a
-// pressure change that moves free-surface accelerations by ~1e-4 m/s^2, so every term is
-// unbiased (q = r/h from the float pair 1/h with one rounding -- r * fl(1/h) alone biases
-// q low), the shape is evaluated as (2-q)^3 - 4(1-q)^3 (no cancellation near q = 1), the
-// sum is compensated (Kahan), and rho - rho0 is formed with an FMA against alpha/6 kept
-// as a float pair.
+// Density and pressure (Eq. density, Eq. pressure) with the pair sum above, so that
+// rho - rho0 (and p) carry no FP32 rounding of their own beyond the final one.
 //
 // Each row of candidates is taken 32 at a time in two phases: a branch-free distance test
 // that sets one bit per neighbour, then the kernel on the set bits.  The pass also records
@@ -498,8 +616,9 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk)
     constexpr bool vol = VOL;
     const bool vol_boundary = vol && xi.w < 0.0f;
     const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
-    DensitySum acc;
-    acc.add(c, xi, 0.0f);                               // self term
+    const bool near0 = near_origin_planes(c, xi);
+    PairDensitySum acc;
+    acc.self(fabsf(xi.w));
     ListWriter list;
     list.dst = c.nlist4 + p;
     list.n = (size_t)c.n;
@@ -521,14 +640,17 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk)
                 const int q = b + __ffs(mm) - 1;
                 mm &= mm - 1u;
                 const float4 xj = __ldg(c.xA + q);
-                float dx, dy, dz;
-                const float r2 = dist2(xi, xj, dx, dy, dz);
                 if (vol && xj.w < 0.0f) {
-                    if (!vol_boundary) acc.add_m(c, __ldg(&c.prho[q].x), r2);
-                    else ++acc.cnt;
-                    if (vol_boundary) continue;
+                    if (vol_boundary) { ++acc.cnt; continue; }
+                    // a boundary neighbour weighs psi = (rho, P) slot as a float pair
+                    const float2 psi = __ldg(&c.prho[q]);
+                    float dx, dy, dz, r2x;
+                    pair_offset(xi, xj, near0, dx, dy, dz, r2x);
+                    acc.add(c, psi.x, psi.y, dx, dy, dz, r2x);
                 } else {
-                    acc.add(c, xj, r2);
+                    float dx, dy, dz, r2x;
+                    pair_offset(xi, xj, near0, dx, dy, dz, r2x);
+                    acc.add(c, fabsf(xj.w), 0.0f, dx, dy, dz, r2x);
                 }
                 if (!keep_list) continue;
                 if (excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) <
@@ -540,10 +662,8 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk)
     });
     list.flush();
     c.nlist_n[p] = list.nl;
-    // rho - rho0 = alpha6 * (S - C) - rho0 with alpha6 = hi + lo
-    float drho = __fmaf_rn(c.alpha6_hi, acc.S, -c.rho0) +
-                 __fmaf_rn(c.alpha6_lo, acc.S, -c.alpha6_hi * acc.C);
-    float rho = c.rho0 + drho;
+    const float drho = acc.excess(c, c.rho0);
+    const float rho = __fadd_rn(c.rho0, drho);
     float pr;
     if (c.flags & FLAG_TAIT) {
         // Tait variation (Sec. 3.1): B ((rho/rho0)^7 - 1), B = k rho0 / 7; (1+x)^7 - 1 by its
@@ -569,28 +689,35 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
 
 // Volume-based boundaries (Akinci et al.): each static or rigid particle's weight
 // psi_b = rho0 / sum_{k boundary} W_bk (self included), stored in its (rho, P) slot as
-// (psi_b, 0) before the density pass reads it.
+// (psi_b, its low part) before the density pass reads it.
 __device__ __forceinline__ void boundary_volume_item(const SimConst &c, int blk)
 {
     const int p = blk * kTile + threadIdx.x;
     if (p >= c.n) return;
     const float4 xi = c.xA[p];
     if (!(xi.w < 0.0f)) return;
-    DensitySum acc;
-    acc.add_m(c, 1.0f, 0.0f);                            // self
+    const bool near0 = near_origin_planes(c, xi);
+    PairDensitySum acc;
+    acc.self(1.0f);
     uint32_t bad = 0;
     for_each_row(c, xi, bad, [&](int s0, int e0) {
         for (int q = s0; q < e0; ++q) {
             const float4 xj = __ldg(c.xA + q);
             if (q == p || !(xj.w < 0.0f)) continue;
             float dx, dy, dz;
-            const float r2 = dist2(xi, xj, dx, dy, dz);
-            if (r2 < c.R2) acc.add_m(c, 1.0f, r2);
+            if (!(dist2(xi, xj, dx, dy, dz) < c.R2)) continue;
+            float r2x;
+            pair_offset(xi, xj, near0, dx, dy, dz, r2x);
+            acc.add(c, 1.0f, 0.0f, dx, dy, dz, r2x);
         }
     });
-    // sum W = alpha6 (S - C), alpha6 = hi + lo
-    const float sumW = __fmaf_rn(c.alpha6_hi, acc.S, __fmaf_rn(c.alpha6_lo, acc.S, -c.alpha6_hi * acc.C));
-    c.prho[p] = make_float2(c.rho0 / sumW, 0.0f);
+    // sum W = alpha6 (S + L) as a float pair (Wh, Wl); psi = rho0 / sum W as a float pair
+    const float Wh = __fmul_rn(c.alpha6_hi, acc.S);
+    const float Wl = __fadd_rn(__fmaf_rn(c.alpha6_hi, acc.S, -Wh),
+                               __fmaf_rn(c.alpha6_lo, acc.S, __fmul_rn(c.alpha6_hi, acc.L)));
+    const float ph = __fdiv_rn(c.rho0, Wh);
+    const float pl = __fdiv_rn(__fmaf_rn(-ph, Wl, __fmaf_rn(-ph, Wh, c.rho0)), Wh);
+    c.prho[p] = make_float2(ph, pl);
     report(c, bad);
 }
 
@@ -642,7 +769,7 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                 float coef;
                 if (vol && (bi || bj)) {
                     // the fluid side's density and pressure only; the boundary side
-                    // weighs psi (its (rho, P) slot holds (psi, 0))
+                    // weighs psi (its (rho, P) slot holds psi as a float pair)
                     const float rf = bi ? pj.x : pi.x, Pf = bi ? pj.y : pi.y;
                     const float w = bi ? fabsf(xj.w) * pi.x * inv_mi : pj.x;
                     const float visc = __fdividef(c.nu20 * vx, (rf + rf) * (r2 + c.eps_h2));

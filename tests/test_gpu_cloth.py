@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_2511_15908_gb300 import scenes
-from test_gpu_parity import check_one_substep, _by_id, G, ACC_TOL, EPS32
+from test_gpu_parity import check_one_substep, _by_id, G, ACC_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -81,11 +81,7 @@ def test_random_blade_cut_then_substep_matches_oracle(sph, seed):
     ref = sysm.substep()
     n = sc.n_total
     acc_ref = _by_id(ref, "acc", n)
-    rho_ref = _by_id(ref, "rho", n)
-    cond = _by_id(ref, "cond", n)
-    k = float(np.float32(sc.params["k"]))
     scale = np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * G)
     dif = np.linalg.norm(st["acc"].astype(np.float64) - acc_ref, axis=1)
-    bound = ACC_TOL * scale + EPS32 * (8.0 * k * cond[:, 0] / rho_ref + 4.0 * cond[:, 1])
-    assert np.all(dif <= bound)
+    assert np.all(dif <= ACC_TOL * scale), (dif / scale).max()
     sim.close()

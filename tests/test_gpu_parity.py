@@ -1,15 +1,12 @@
 """GPU parity: the sm_103a substep against the FP64 oracle, element by element.
 
 Bar (one substep from the same seeded FP32 state): cell keys, sorted order, cell_start
-and neighbour counts bit-exact; densities within 1e-5 relative; body wrench force and
-torque within 1e-4 relative.  Accelerations: within 1e-4 * max(|a|, 0.1 g) for at least
-99.5 % of the particles, and every particle within that bar plus the FP32 rounding bound
-of its own terms,
-    eps32 * (8 k G_i / rho_i + 4 A_i),
-where G_i = sum_j m_j |grad_i W_ij| and A_i = sum_j |F_ij| / m_i come from the oracle:
-p = k (rho - rho0) turns a few-ulp density error into an acceleration error k G_i / rho_i
-times larger, and the pair sum carries eps32 * A_i.  The fraction inside the plain bar is
-printed for every case.
+and neighbour counts bit-exact; densities within 1e-5 relative; every particle's
+acceleration within 1e-4 * max(|a|, 0.1 g); body wrench force and torque within 1e-4
+relative.  With the record flag the kernel's accelerations are compared directly;
+without it (the benchmark's launch configuration) the new velocities are, and the
+acceleration error is (|v - v_ref| - the FP32 rounding of storing v) / dt.  The fraction
+of particles inside the bar and the largest error are printed for every case.
 """
 import numpy as np
 import pytest
@@ -23,7 +20,6 @@ G = 9.81
 RHO_TOL = 1e-5
 ACC_TOL = 1e-4
 WRENCH_TOL = 1e-4
-EPS32 = 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -52,14 +48,22 @@ def _kinds(sc):
     return kinds
 
 
+def velocity_acc_error(v, v_ref, dt):
+    """Acceleration error implied by the new FP32 velocities: |v - v_ref| less the rounding
+    of storing each component in FP32 (half an ulp; not an error of the acceleration),
+    over dt."""
+    v = v.astype(np.float32)
+    ulp = np.spacing(np.abs(v)).astype(np.float64)
+    store = 0.5 * np.sqrt(np.sum(ulp * ulp, axis=1))
+    dv = np.linalg.norm(v.astype(np.float64) - v_ref, axis=1)
+    return np.maximum(dv - store, 0.0) / dt
+
+
 def check_one_substep(sph, sc, mode, record=True, max_neighbours=0):
     """Run one substep on the GPU and in the oracle; assert the parity bar."""
     flags = sc.params["flags"] | (sph.FLAG_RECORD if record else 0)
     sim = sph.Simulation(sc, flags=flags, max_neighbours=max_neighbours)
     n = sc.n_total
-    v0 = None
-    if not record:
-        v0 = sim.state()["v"]
     sim.step(1)
     keys, ids, cs = sim.sort()
     st = sim.state(record=record)
@@ -83,27 +87,19 @@ def check_one_substep(sph, sc, mode, record=True, max_neighbours=0):
     # accelerations
     kinds = _kinds(sc)
     acc_ref = _by_id(ref, "acc", n)
+    scale = np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * G)
     if record:
-        acc = st["acc"].astype(np.float64)
+        dif = np.linalg.norm(st["acc"].astype(np.float64) - acc_ref, axis=1)
         sel = np.ones(n, bool)
     else:
-        acc = (st["v"].astype(np.float64) - v0) / sc.params["dt"]
+        dif = velocity_acc_error(st["v"], _by_id(ref, "v_new", n), float(np.float32(sc.params["dt"])))
         sel = (kinds == 0) | (kinds == scenes.KIND_SOFT)
-    scale = np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * G)
-    dif = np.linalg.norm(acc - acc_ref, axis=1)
     err = dif / scale
-    cond = _by_id(ref, "cond", n)
-    k = float(np.float32(sc.params["k"]))
-    if sc.params["flags"] & scenes.FLAG_TAIT:
-        # the Tait form's slope dp/drho = k (rho / rho0)^6 takes the place of k
-        k = k * np.maximum(1.0, (rho_ref / float(np.float32(sc.params["rho0"]))) ** 6)
-    fp32_bound = EPS32 * (8.0 * k * cond[:, 0] / rho_ref + 4.0 * cond[:, 1])
-    ok = dif <= ACC_TOL * scale + fp32_bound
     frac = float(np.mean(err[sel] <= ACC_TOL))
     print(f"[{sc.name} n={n}] acc: max rel err {err[sel].max():.2e}, "
           f"{100 * frac:.3f} % within 1e-4, rho max rel err {rel.max():.2e}")
-    assert ok[sel].all(), f"acc err {err[sel].max():.3e} beyond the FP32 bound at id {np.argmax(err * sel)}"
-    assert frac >= 0.995, f"only {frac:.4f} of particles within 1e-4"
+    assert err[sel].max() <= ACC_TOL, \
+        f"acc err {err[sel].max():.3e} at id {np.argmax(err * sel)} (kind {kinds[np.argmax(err * sel)]})"
 
     # wrenches and rigid update
     for b, body in enumerate(sc.bodies):
@@ -113,8 +109,7 @@ def check_one_substep(sph, sc, mode, record=True, max_neighbours=0):
         Fr, Tr = ref["wrench"][b, :3], ref["wrench"][b, 3:]
         fscale = max(np.linalg.norm(Fr), 1e-9)
         assert np.linalg.norm(F - Fr) <= WRENCH_TOL * fscale + 1e-9, (b, F, Fr)
-        assert np.linalg.norm(T - Tr) <= WRENCH_TOL * max(np.linalg.norm(Tr), 1e-9) + 1e-9 or \
-            np.linalg.norm(T - Tr) <= 1e-6 * fscale, (b, T, Tr)
+        assert np.linalg.norm(T - Tr) <= WRENCH_TOL * max(np.linalg.norm(Tr), 1e-9) + 1e-9, (b, T, Tr)
         if body.kind == scenes.KIND_RIGID and sc.grab_body != b and body.mass > 0:
             np.testing.assert_allclose(bodies[b][:3], ref["body_new"][b, :3], atol=1e-6)
             np.testing.assert_allclose(bodies[b][7:], ref["body_new"][b, 7:],
@@ -178,6 +173,13 @@ def test_stirring_tank_full_size_bench_config(sph):
 def test_coupled_full_size_bench_config(sph):
     sc = scenes.with_velocity_noise(scenes.coupled(seed=0, n_substeps=10), seed=6, sigma=0.2)
     check_one_substep(sph, sc, mode=1, record=False)
+
+
+def test_coupled_full_size_record_mode(sph):
+    # the full scene runs the 512-thread density instance: neighbour counts bit-exact and
+    # every particle's acceleration (walls and probe included) inside the bar
+    sc = scenes.with_velocity_noise(scenes.coupled(seed=0, n_substeps=10), seed=16, sigma=0.2)
+    check_one_substep(sph, sc, mode=1, record=True)
 
 
 def test_tait_eos_dam_break_grabbed_cube(sph):
@@ -401,9 +403,7 @@ def test_overfull_cell_reports_capacity_and_keeps_per_particle_results(sph):
     rho_ref = _by_id(ref, "rho", n)
     assert (np.abs(st["rho"] - rho_ref) / rho_ref).max() <= RHO_TOL
     acc_ref = _by_id(ref, "acc", n)
-    cond = _by_id(ref, "cond", n)
-    k = float(np.float32(sc.params["k"]))
     scale = np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * G)
     dif = np.linalg.norm(st["acc"].astype(np.float64) - acc_ref, axis=1)
-    assert np.all(dif <= ACC_TOL * scale + EPS32 * (8.0 * k * cond[:, 0] / rho_ref + 4.0 * cond[:, 1]))
+    assert np.all(dif <= ACC_TOL * scale)
     sim.close()

@@ -40,9 +40,11 @@ KERNEL_SRC = [os.path.join(ROOT, "paper_2511_15908_gb300", "csrc", f)
 # Algorithmic cost model (documented in the design notes):
 BYTES_PER_PARTICLE_STEP = 168          # HBM bytes of one substep per particle
 FORCE_BYTES_PER_PARTICLE = 72          # force pass: read x, v, (rho, P); write x, v
-FORCE_FLOPS_PER_PAIR = 42              # pressure + viscosity pair term (FMA = 2 flops)
-DENSITY_FLOPS_PER_PAIR = 21
+DENSITY_BYTES_PER_PARTICLE = 20        # density pass: read x (16), write rho (4)
+FORCE_FLOPS_PER_PAIR = 50              # the method's flops per pair (pressure + viscosity)
+DENSITY_FLOPS_PER_PAIR = 15            # the method's flops per pair (r, W, m W, sum)
 FP32_LANES_PER_SM, SMS = 128, 152
+SPIN_UP_SUBSTEPS = 300                 # untimed: the probe stirs the settled tank first
 
 
 def _peaks():
@@ -153,7 +155,7 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 def _workload(name):
     from paper_2511_15908_gb300 import scenes
     if name == "coupled":
-        return scenes.coupled(seed=0, n_substeps=4096)
+        return scenes.coupled(seed=0, n_substeps=4096)      # settled fill (see scenes.coupled)
     if name == "stirring":
         return scenes.stirring_tank(seed=0, n_substeps=4096)
     if name == "dam_break":
@@ -596,11 +598,19 @@ def run_ours(args):
     sc = _workload(args.workload)
     peaks, peak_kind = _peaks()
 
-    # neighbour statistics of the first substep (record run) for the algorithmic flop count
+    # first substep with the record flag: accelerations for the parity figure against the
+    # oracle (compared at the end, after the GPU timing); then the same scene on through
+    # the spin-up (the record flag does not change the dynamics) for the neighbour
+    # statistics of the stirred state, which give the algorithmic flop count
     rec = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_RECORD)
     rec.step(1)
+    acc_first = rec.state(record=True)["acc"]
+    rec.step(SPIN_UP_SUBSTEPS)
+    rec_domain = [0]
+    _reported(rec.sync, rec_domain, sph)
     nn = rec.state(record=True)["nnbr"]
     pairs = float(np.sum(nn, dtype=np.int64) + sc.n_total)   # density includes self
+    mean_nbrs = float(np.mean(nn))
     rec.close()
     del rec
 
@@ -619,6 +629,10 @@ def run_ours(args):
             flush.fill_(1)
 
     domain = [0]
+    # the stirred regime: the probe walks through the settled tank for SPIN_UP_SUBSTEPS
+    # untimed substeps before the warm-up and the timed steps
+    sim.step(SPIN_UP_SUBSTEPS)
+    _reported(sim.sync, domain, sph)
     for _ in range(args.warmup):
         flush_l2()
         sim.step(1)
@@ -650,7 +664,8 @@ def run_ours(args):
     dom = int(np.argmax(kmean))
     dom_name = sph.KERNELS[dom]
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12      # TFLOP/s
+    alu_nominal = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12      # TFLOP/s
+    alu_peak = sph.measure_fp32_fma(local)                                  # measured here
     t_dom = kmean[dom] / 1e3
     if dom_name == "force":
         flops = FORCE_FLOPS_PER_PAIR * (pairs - n_all)
@@ -663,8 +678,13 @@ def run_ours(args):
         roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": alu_peak,
                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
                     "traffic": _traffic(dom_name),
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz "
-                                   f"(sm_max_mhz of {peak_kind} peaks)"}
+                    "flops_per_pair": (DENSITY_FLOPS_PER_PAIR if dom_name == "density"
+                                       else FORCE_FLOPS_PER_PAIR),
+                    "pairs_per_launch": pairs if dom_name == "density" else pairs - n_all,
+                    "mean_neighbours": mean_nbrs,
+                    "peak_source": "measured: FP32 FMA probe kernel (sph_measure_fp32_fma, "
+                                   "full occupancy, best of 5, CUDA events)",
+                    "peak_nominal": alu_nominal}
     else:
         bytes_ = FORCE_BYTES_PER_PARTICLE * n_all
         achieved = bytes_ / t_dom / 1e9
@@ -672,6 +692,7 @@ def run_ours(args):
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                     "traffic": _traffic(dom_name)}
     force_hbm = FORCE_BYTES_PER_PARTICLE * n_all / (kmean[6] / 1e3) / 1e9
+    density_hbm = DENSITY_BYTES_PER_PARTICLE * n_all / (kmean[5] / 1e3) / 1e9
     step_hbm = BYTES_PER_PARTICLE_STEP * n_all / (ms_per_step / 1e3) / 1e9
 
     # end to end through the public API: host pose in, one substep, host wrench out
@@ -680,10 +701,11 @@ def run_ours(args):
     pose_h = torch.empty(13, dtype=torch.float32).pin_memory().numpy()
     wrench_h = np.zeros(6, np.float64)
     grab_id = sim.body_ids[sc.grab_body]
+    done = int(sim.info()[4])                 # substeps so far: the path continues from here
     for i in range(args.steps):
         flush_l2()
         torch.cuda.synchronize()
-        row = path[(args.warmup + args.steps + i) % path.shape[0]]
+        row = path[min(done + i, path.shape[0] - 1)]
         t0 = time.perf_counter()
         pose_h[:] = row
         try:
@@ -693,6 +715,9 @@ def run_ours(args):
                 raise
             domain[0] += 1
         e2e_s += time.perf_counter() - t0
+    if domain[0] or rec_domain[0]:
+        # a particle left the grid domain: the workload is not the one this line describes
+        raise RuntimeError(f"{domain[0] + rec_domain[0]} out-of-domain reports during the run")
     e2e_s = max_over_ranks(e2e_s)
     e2e_value = job_rate(sc.n_fluid * args.steps, world, e2e_s)
     sim.close()
@@ -702,6 +727,7 @@ def run_ours(args):
     # also the FP64 reference of the first substep's grab wrench.
     cpu = None
     wrench_err = None
+    acc_parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
@@ -717,6 +743,15 @@ def run_ours(args):
         kap = _cancellation(sc, out, m_sorted, sc.grab_body)
         wrench_err = {"force_rel": float(fe), "torque_rel": float(te),
                       "kappa_force": kap["kappa_force"], "kappa_torque": kap["kappa_torque"]}
+        # every particle's acceleration of the first substep against the oracle's
+        acc_ref = np.empty_like(out["acc"])
+        acc_ref[out["id"]] = out["acc"]
+        rel = (np.linalg.norm(acc_first.astype(np.float64) - acc_ref, axis=1)
+               / np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * 9.81))
+        acc_parity = {"bar": "|da| <= 1e-4 max(|a|, 0.1 g), every particle",
+                      "particles": int(rel.size), "frac_within": float(np.mean(rel <= 1e-4)),
+                      "max_rel": float(rel.max()), "what": "first substep, record flag, all "
+                      "particle kinds, against the FP64 grid oracle"}
 
     forms = {}
     if not args.no_forms:
@@ -748,6 +783,9 @@ def run_ours(args):
                            "particles_fluid": sc.n_fluid, "l2": "flushed between steps",
                            "parallelism": f"replicas x{world}",
                            "all_particle_steps_per_s": value * n_all / sc.n_fluid,
+                           "regime": f"stirred: timed after {SPIN_UP_SUBSTEPS + 1 + args.warmup} "
+                                     "untimed substeps of the probe's random walk from the "
+                                     "settled fill",
                            "out_of_domain_reports": domain[0]},
                 "gpu_launches": 8 * args.steps,
                 "kernel_ms": {k: float(v) for k, v in zip(sph.KERNELS, kmean)},
@@ -757,7 +795,10 @@ def run_ours(args):
                              "achieved_gbs": step_hbm, "peak_gbs": peaks["hbm_gbs"],
                              "frac": step_hbm / peaks["hbm_gbs"]},
                 "force_hbm_frac": force_hbm / peaks["hbm_gbs"],
+                "density_hbm": {"bytes_per_particle": DENSITY_BYTES_PER_PARTICLE,
+                                "achieved_gbs": density_hbm, "frac": density_hbm / peaks["hbm_gbs"]},
                 "grab_wrench_err_vs_oracle": wrench_err,
+                "acc_parity": acc_parity,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 64,
                         "d2h_bytes_per_step": 60,
                         "what": "sph_haptic_cycle: host pose and velocity in (as kernel "

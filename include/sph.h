@@ -506,14 +506,18 @@ sph_status sph_iso_polygonize(const float *d_field, const int32_t dims[3], const
  * builds from p (domain_lo/hi, cell; the other fields are ignored).
  *   d_keys[n]          cell key of each sorted slot
  *   d_order[n]         input index of the particle in each sorted slot (ties keep input
- *                      order)
+ *                      order in every cell of at most 512 particles; a cell holding more
+ *                      gets its members in an arbitrary order, without an error -- the
+ *                      keys stay ascending and d_order stays a permutation)
  *   d_cell_start[C+1]  first sorted slot of each cell, C = grid cells
  * It allocates nothing: the per-cell counters and per-particle ranks live in one fixed
  * file-scope device array of about 4.2 MB, reserved on every GPU that loads this library
  * until the process exits.  Limits: n <= SPH_NOALLOC_MAX_PARTICLES and C <=
  * SPH_NOALLOC_MAX_CELLS, else SPH_ERR_CAPACITY (nothing is launched).  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call shares the array:
+ * current; make that first call before any stream capture.  The address is kept per
+ * device for the life of the process: after cudaDeviceReset on a device this entry point
+ * must not be called on it again in the same process.  Every call shares the array:
  * calls whose work overlaps on the GPU (other streams, other threads) race -- serialise
  * them.  Enqueued on cuda_stream; particles outside the domain are clamped into the border
  * cells as in sph_step (not reported here).  Errors: SPH_ERR_ARG, SPH_ERR_CAPACITY,
@@ -524,6 +528,18 @@ sph_status sph_iso_polygonize(const float *d_field, const int32_t dims[3], const
 sph_status sph_cell_sort_noalloc(const sph_params *p, const float *d_xyzm, int32_t n,
                                  uint32_t *d_keys, int32_t *d_order, uint32_t *d_cell_start,
                                  void *cuda_stream);
+
+/*
+ * Measurement hook (not part of the method): enqueues on cuda_stream one kernel of
+ * `blocks` blocks of 256 threads, each thread running `iters` (a multiple of 16) steps of
+ * 8 independent FP32 FMA chains, and stores its FP32 flop count (2 per FMA) in
+ * *out_flops.  The caller times the launch with events on that stream; flops / time is
+ * the FP32 FMA throughput the density and force passes are reported against.  d_sink: a
+ * device buffer of at least 256 floats the kernel may write (it does not for these
+ * arguments).  Errors: SPH_ERR_ARG, SPH_ERR_CUDA.
+ */
+sph_status sph_measure_fp32_fma(void *cuda_stream, int32_t blocks, int32_t iters, float *d_sink,
+                                double *out_flops);
 
 /* Wait for the stream and report latched device errors. */
 sph_status sph_sync(sph_handle *h);

@@ -29,13 +29,15 @@ struct Layout {
 };
 
 // Grid of the FP32 cell hash: origin lo - cell, n = floor((hi - o) / cell) + 2 per axis.
+// Cells per axis; an axis whose cell count is not finite or exceeds 2^30 gets 0 (the
+// callers reject a grid with a zero axis), so the float is range-checked before the cast.
 void grid_dims(const sph_params &p, int dims[3], float o[3], float &inv)
 {
     inv = 1.0f / p.cell;
     for (int a = 0; a < 3; ++a) {
         o[a] = p.domain_lo[a] - p.cell;
-        float u = (p.domain_hi[a] - o[a]) * inv;
-        dims[a] = (int)std::floor(u) + 2;
+        const float u = (p.domain_hi[a] - o[a]) * inv;
+        dims[a] = (u >= 0.0f && u < 1073741824.0f) ? (int)std::floor(u) + 2 : 0;
     }
 }
 

@@ -444,12 +444,43 @@ __device__ __forceinline__ float diff_lo(float a, float b, float d)
 // the pressure the force pass needs: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000
 // (6e-5) into a pressure change that moves wall-adjacent accelerations by ~1e-4 m/s^2,
 // and every FP32 stage of the plain evaluation (r^2, sqrt, q, the cubic, the product with
-// m, the summation) costs about that much.  So each stage carries its rounding error:
-// r^2 = dx^2 + dy^2 + dz^2 from FMA product residuals and TwoSums, r = sqrt(r^2) and
-// q = r / h as float pairs (Newton residual, 1/h as a float pair), 6 w = t^3 - 4 u^3 with
-// t = 2 - q and u = max(1 - q, 0) as pairs and both cubes as pairs (Fast2Sum for the
-// difference, t^3 >= 4 u^3), the term m 6w as a pair, and the running sum by TwoSum; all
-// low parts are summed in L.  The value is S + L.
+// m, the summation) costs about that much.  So each stage carries its rounding error: q as
+// a float pair (pair_q), 6 w = t^3 - 4 u^3 with t = 2 - q and u = max(1 - q, 0) as pairs
+// and both cubes as pairs (Fast2Sum for the difference, t^3 >= 4 u^3), the term m 6w as a
+// pair, and the running sum by TwoSum; all low parts are summed in L.  The value is S + L.
+// q = |x_j - x_i| / h as an unevaluated float pair qh + ql (relative error ~1e-13): r^2 =
+// dx^2 + dy^2 + dz^2 from FMA product residuals and TwoSums, r = sqrt(r^2) from rsqrt, one
+// Newton step and the residual r2 - r^2 over 2r, q with 1/h as a float pair.  d = x_j - x_i
+// in FP32; r2x = the first-order r^2 correction 2 d . d_lo when a difference was not exact.
+struct PairQ {
+    float qh, ql;
+    float r2h;                 // r^2, high part
+    float rs;                  // ~ 1 / r (rsqrt of r2h)
+};
+__device__ __forceinline__ PairQ pair_q(const SimConst &c, float dx, float dy, float dz, float r2x)
+{
+    const float px = __fmul_rn(dx, dx), py = __fmul_rn(dy, dy), pz = __fmul_rn(dz, dz);
+    const float ex = __fmaf_rn(dx, dx, -px), ey = __fmaf_rn(dy, dy, -py);
+    const float ez = __fmaf_rn(dz, dz, -pz);
+    float e1, e2;
+    const float s1 = two_sum(px, py, e1);
+    const float r2h = two_sum(s1, pz, e2);
+    const float r2l = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), __fadd_rn(__fadd_rn(e1, e2), r2x));
+    // r: rsqrt, one Newton step, then the residual r2 - r^2 over 2r
+    const float rs = rsqrtf(fmaxf(r2h, 1e-30f));
+    const float hrs = __fmul_rn(0.5f, rs);
+    float r = __fmul_rn(r2h, rs);
+    r = __fmaf_rn(hrs, __fmaf_rn(-r, r, r2h), r);
+    const float rl = __fmul_rn(__fadd_rn(__fmaf_rn(-r, r, r2h), r2l), hrs);
+    // q = r (1/h)_hi + r (1/h)_lo + rl (1/h)_hi
+    PairQ o;
+    o.r2h = r2h;
+    o.rs = rs;
+    o.qh = __fmul_rn(r, c.invh_hi);
+    o.ql = __fadd_rn(__fmaf_rn(r, c.invh_hi, -o.qh), __fmaf_rn(r, c.invh_lo, __fmul_rn(rl, c.invh_hi)));
+    return o;
+}
+
 struct PairDensitySum {
     float S = 0.0f, L = 0.0f;
     int cnt = 0;
@@ -464,23 +495,8 @@ struct PairDensitySum {
     __device__ __forceinline__ void add(const SimConst &c, float mh, float ml, float dx, float dy,
                                         float dz, float r2x)
     {
-        const float px = __fmul_rn(dx, dx), py = __fmul_rn(dy, dy), pz = __fmul_rn(dz, dz);
-        const float ex = __fmaf_rn(dx, dx, -px), ey = __fmaf_rn(dy, dy, -py);
-        const float ez = __fmaf_rn(dz, dz, -pz);
-        float e1, e2;
-        const float s1 = two_sum(px, py, e1);
-        const float r2h = two_sum(s1, pz, e2);
-        const float r2l = __fadd_rn(__fadd_rn(__fadd_rn(ex, ey), ez), __fadd_rn(__fadd_rn(e1, e2), r2x));
-        // r: rsqrt, one Newton step, then the residual r2 - r^2 over 2r
-        const float rs = rsqrtf(fmaxf(r2h, 1e-30f));
-        const float hrs = __fmul_rn(0.5f, rs);
-        float r = __fmul_rn(r2h, rs);
-        r = __fmaf_rn(hrs, __fmaf_rn(-r, r, r2h), r);
-        const float rl = __fmul_rn(__fadd_rn(__fmaf_rn(-r, r, r2h), r2l), hrs);
-        // q = r (1/h)_hi + r (1/h)_lo + rl (1/h)_hi
-        const float qh = __fmul_rn(r, c.invh_hi);
-        const float ql = __fadd_rn(__fmaf_rn(r, c.invh_hi, -qh),
-                                   __fmaf_rn(r, c.invh_lo, __fmul_rn(rl, c.invh_hi)));
+        const PairQ pq = pair_q(c, dx, dy, dz, r2x);
+        const float qh = pq.qh, ql = pq.ql;
         // t = 2 - q: 2 - th and (2 - th) - qh are exact (Sterbenz); likewise u = 1 - q
         const float th = __fsub_rn(2.0f, qh);
         const float tl = __fsub_rn(__fsub_rn(__fsub_rn(2.0f, th), qh), ql);
@@ -512,18 +528,78 @@ struct PairDensitySum {
 // d = x_j - x_i with the first-order r^2 correction of inexact differences (only particles
 // within 2R of a coordinate plane through the origin can have them).
 __device__ __forceinline__ void pair_offset(float4 xi, float4 xj, bool near0, float &dx, float &dy,
-                                            float &dz, float &r2x)
+                                            float &dz, float &r2x, float &lx, float &ly, float &lz)
 {
     dx = __fsub_rn(xj.x, xi.x);
     dy = __fsub_rn(xj.y, xi.y);
     dz = __fsub_rn(xj.z, xi.z);
     r2x = 0.0f;
+    lx = 0.0f; ly = 0.0f; lz = 0.0f;
     if (near0) {
-        const float lx = diff_lo(xj.x, xi.x, dx), ly = diff_lo(xj.y, xi.y, dy);
-        const float lz = diff_lo(xj.z, xi.z, dz);
+        lx = diff_lo(xj.x, xi.x, dx);
+        ly = diff_lo(xj.y, xi.y, dy);
+        lz = diff_lo(xj.z, xi.z, dz);
         r2x = __fmul_rn(2.0f, __fmaf_rn(dx, lx, __fmaf_rn(dy, ly, __fmul_rn(dz, lz))));
     }
 }
+
+__device__ __forceinline__ void pair_offset(float4 xi, float4 xj, bool near0, float &dx, float &dy,
+                                            float &dz, float &r2x)
+{
+    float lx, ly, lz;
+    pair_offset(xi, xj, near0, dx, dy, dz, r2x, lx, ly, lz);
+}
+
+// w'(q) / q of the cubic spline as a float pair gh + gl from q = qh + ql:
+//   q < 1: -2 + 1.5 q;   1 <= q < 2: -0.5 (2 - q)^2 / q
+// (the two agree at q = 1).  The quotient takes an approximate 1/qh and one residual step,
+// so its error is second order in the reciprocal's.
+__device__ __forceinline__ float gradq_pair(float qh, float ql, float &gl)
+{
+    // inner piece: p = 1.5 qh as a pair, then Fast2Sum with -2 (|p| <= 1.5 < 2)
+    const float p = __fmul_rn(1.5f, qh), pe = __fmaf_rn(1.5f, qh, -p);
+    const float gi = __fadd_rn(-2.0f, p);
+    const float gil = __fadd_rn(__fsub_rn(p, __fadd_rn(gi, 2.0f)), __fmaf_rn(1.5f, ql, pe));
+    // outer piece: A = t^2 as a pair (t = 2 - q), divided by q
+    const float th = __fsub_rn(2.0f, qh);
+    const float tl = __fsub_rn(__fsub_rn(__fsub_rn(2.0f, th), qh), ql);
+    const float ah = __fmul_rn(th, th);
+    const float al = __fmaf_rn(__fmul_rn(2.0f, th), tl, __fmaf_rn(th, th, -ah));
+    const float iq = __fdividef(1.0f, qh);
+    const float g0 = __fmul_rn(ah, iq);
+    const float g1 = __fmul_rn(__fadd_rn(__fmaf_rn(-g0, qh, ah), __fmaf_rn(-g0, ql, al)), iq);
+    if (qh < 1.0f) {
+        gl = gil;
+        return gi;
+    }
+    gl = __fmul_rn(-0.5f, g1);
+    return __fmul_rn(-0.5f, g0);
+}
+
+// Sum over a particle's interaction partners of w_j (w'(q)/q) d_j, d_j = x_j - x_i, with
+// w'(q)/q as a float pair, every product's residual kept and each component summed by
+// TwoSum: a kernel-gradient sum that cancels (to ~0 for a full neighbourhood) is exact to
+// ~1e-13 of its terms.  The force pass multiplies it by the particle's own pressure term.
+struct PairGradSum {
+    float Sx = 0.0f, Sy = 0.0f, Sz = 0.0f, Lx = 0.0f, Ly = 0.0f, Lz = 0.0f;
+    __device__ __forceinline__ void add(float w, float gh, float gl, float dx, float dy, float dz,
+                                        float lx, float ly, float lz)
+    {
+        const float mh = __fmul_rn(w, gh);
+        const float ml = __fmaf_rn(w, gl, __fmaf_rn(w, gh, -mh));
+        add1(Sx, Lx, mh, ml, dx, lx);
+        add1(Sy, Ly, mh, ml, dy, ly);
+        add1(Sz, Lz, mh, ml, dz, lz);
+    }
+    static __device__ __forceinline__ void add1(float &S, float &L, float mh, float ml, float d, float dl)
+    {
+        const float th = __fmul_rn(mh, d);
+        const float tl = __fmaf_rn(mh, dl, __fmaf_rn(ml, d, __fmaf_rn(mh, d, -th)));
+        float e;
+        S = two_sum(S, th, e);
+        L = __fadd_rn(L, __fadd_rn(tl, e));
+    }
+};
 
 __device__ __forceinline__ bool near_origin_planes(const SimConst &c, float4 x)
 {
@@ -744,7 +820,16 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
         const bool skip = (kind == KIND_STATIC) && !(c.flags & FLAG_RECORD);
         constexpr bool vol = VOL;
         const float inv_mi = 1.0f / mi;
+        const bool near0 = near_origin_planes(c, xi);
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        // The pressure term sum_j m_j (P_i + P_j) gq_j d_j is split as
+        //   P_i * sum_j 2 m_j gq_j d_j  +  sum_j m_j (P_j - P_i) gq_j d_j :
+        // at depth every pair term is large (P ~ rho0 g d / rho^2) and the sum cancels to
+        // about the weight, so FP32 pair terms alone would carry errors of the order of the
+        // acceptance bar.  The first sum is purely geometric and taken exactly (float pairs,
+        // PairGradSum); the second has terms about (P_j - P_i) / P_i smaller (P_j - P_i is
+        // exact, Sterbenz) and stays FP32 together with the viscous term.
+        PairGradSum G;
         if (!skip) {
             // check_own: skip the particle's own rigid body (the neighbour list has no such
             // entries, so only the re-search needs the test)
@@ -754,16 +839,13 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                 if (check_own && (unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
                 const bool bi = xi.w < 0.0f, bj = xj.w < 0.0f;
                 if (vol && bi && bj) return;       // volume boundaries: no boundary pairs
-                float rinv = 0.0f;                 // coincident particles: no force
-                if (r2 > 0.0f) {
-                    rinv = rsqrtf(r2);
-                    rinv = rinv * __fmaf_rn(-0.5f * r2 * rinv, rinv, 1.5f);
-                }
-                float s = r2 * rinv;
-                s = __fmaf_rn(s, c.invh_hi, s * c.invh_lo);
-                float t = 2.0f - s;
-                // w'(q)/q of the cubic spline (finite at q -> 0)
-                float gq = s < 1.0f ? (-2.0f + 1.5f * s) : (-0.5f * t * t * c.h * rinv);
+                float r2x, lx, ly, lz;
+                pair_offset(xi, xj, near0, dx, dy, dz, r2x, lx, ly, lz);
+                const PairQ pq = pair_q(c, dx, dy, dz, r2x);
+                // w'(q)/q of the cubic spline as a float pair (finite at q -> 0; coincident
+                // particles have d = 0 and exert no force)
+                float gl;
+                const float gq = gradq_pair(pq.qh, pq.ql, gl);
                 // v_ij . x_ij with x_ij = -d
                 float vx = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
                 float coef;
@@ -773,10 +855,17 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                     const float rf = bi ? pj.x : pi.x, Pf = bi ? pj.y : pi.y;
                     const float w = bi ? fabsf(xj.w) * pi.x * inv_mi : pj.x;
                     const float visc = __fdividef(c.nu20 * vx, (rf + rf) * (r2 + c.eps_h2));
-                    coef = w * (visc - Pf) * gq;
+                    if (bi) {
+                        coef = w * (visc - Pf) * gq;
+                    } else {                       // fluid i: -P_i w gq d goes to G
+                        coef = w * visc * gq;
+                        G.add(w, gq, gl, dx, dy, dz, lx, ly, lz);
+                    }
                 } else {
+                    const float mj = fabsf(xj.w);
                     float visc = __fdividef(c.nu20 * vx, (pi.x + pj.x) * (r2 + c.eps_h2));
-                    coef = fabsf(xj.w) * (visc - (pi.y + pj.y)) * gq;
+                    coef = mj * (visc - __fsub_rn(pj.y, pi.y)) * gq;
+                    G.add(__fmul_rn(2.0f, mj), gq, gl, dx, dy, dz, lx, ly, lz);
                 }
                 ax -= coef * dx;
                 ay -= coef * dy;
@@ -841,6 +930,10 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
                     }
                 });
             }
+            // + P_i * G (G cancels to ~0 in a full neighbourhood, so one rounding suffices)
+            ax = __fmaf_rn(pi.y, __fadd_rn(G.Sx, G.Lx), ax);
+            ay = __fmaf_rn(pi.y, __fadd_rn(G.Sy, G.Ly), ay);
+            az = __fmaf_rn(pi.y, __fadd_rn(G.Sz, G.Lz), az);
             ax *= c.alpha_g;
             ay *= c.alpha_g;
             az *= c.alpha_g;

@@ -16,7 +16,7 @@
 #define SPH_DENSITY_MINB 2
 #endif
 #ifndef SPH_FORCE_MINB
-#define SPH_FORCE_MINB 5
+#define SPH_FORCE_MINB 4
 #endif
 constexpr int kDensityWideMin = 300000;   // ~ 2 x 152 SMs x 2 blocks x 512 threads
 

@@ -44,6 +44,8 @@ __global__ void k_na_scan_apply(SimConst c) { scan_apply_item(c, blockIdx.x); }
 __global__ void k_na_scatter(SimConst c) { scatter_item(c, blockIdx.x); }
 
 // Stable order inside each cell: particle e goes to cell_start + #{members with smaller e}.
+// A cell of more than kMaxCell (512) particles takes the atomic claim order instead: still
+// a permutation with the keys ascending, but ties in that cell are not in input order.
 __global__ void k_na_rank(SimConst c, uint32_t *keys_out, int *order_out)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -107,8 +109,12 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_params *p, const float *d_
     for (int a = 0; a < 3; ++a) {
         c.o[a] = p->domain_lo[a] - p->cell;
         if (!(p->domain_hi[a] > p->domain_lo[a])) return SPH_ERR_ARG;
-        dims[a] = (int)std::floor((p->domain_hi[a] - c.o[a]) * inv) + 2;
-        if (dims[a] <= 0 || dims[a] > SPH_NOALLOC_MAX_CELLS) return SPH_ERR_CAPACITY;
+        // range-checked in floating point before the conversion (a huge domain or a tiny
+        // cell gives a count beyond int, or infinity)
+        const float u = (p->domain_hi[a] - c.o[a]) * inv;
+        if (!(u >= 0.0f && u < (float)SPH_NOALLOC_MAX_CELLS)) return SPH_ERR_CAPACITY;
+        dims[a] = (int)std::floor(u) + 2;
+        if (dims[a] > SPH_NOALLOC_MAX_CELLS) return SPH_ERR_CAPACITY;
     }
     const long long ncell = (long long)dims[0] * dims[1] * dims[2];
     if (ncell > SPH_NOALLOC_MAX_CELLS) return SPH_ERR_CAPACITY;
@@ -128,8 +134,9 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_params *p, const float *d_
     c.perm = c.rank + SPH_NOALLOC_MAX_PARTICLES;
     c.status = c.perm + SPH_NOALLOC_MAX_PARTICLES;
     c.cell_start = d_cell_start;
-    // the counters keep the previous call's contents: start from zero
+    // the counters and the status words keep the previous call's contents: start from zero
     if (cudaMemsetAsync(c.cnt, 0, 4 * ((size_t)ncell + 1), st) != cudaSuccess) return SPH_ERR_CUDA;
+    if (cudaMemsetAsync(c.status, 0, 4 * 4, st) != cudaSuccess) return SPH_ERR_CUDA;
     const int nb = (n + kTile - 1) / kTile;
     if (n > 0) k_na_hash<<<nb, kTile, 0, st>>>(c);
     k_na_scan_tiles<<<c.n_scan_tiles, kTile, 0, st>>>(c);

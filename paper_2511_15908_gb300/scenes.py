@@ -156,11 +156,33 @@ def _box_inertia(mass, size):
     return (mass / 12.0) * np.diag([b * b + c * c, a * a + c * c, a * a + b * b]).astype(np.float32)
 
 
-def _fill_fluid(rng, cols, spacing, origin, count, carve):
-    """Fill columns bottom-up with a lattice, skip points that `carve` rejects, keep `count`."""
+def _settle_columns(pts, spacing, top, g_over_k):
+    """Move lattice layers down so that the layer spacing at depth d below the surface is
+    spacing / (1 + g d / k): the density a linear equation of state p = k (rho - rho0) needs
+    to carry the fluid's weight, p = rho0 g d.  Mass per unit height of the uncompressed
+    column is rho0, of the settled one rho0 (1 + g d / k), so an uncompressed depth zeta
+    maps to d with zeta = d + g d^2 / (2 k); the floor stays where it is."""
+    def depth(zeta):
+        return (np.sqrt(1.0 + 2.0 * g_over_k * zeta) - 1.0) / g_over_k
+    out = pts.copy()
+    z0 = out[:, 2].min() - 0.5 * spacing
+    zeta = np.maximum(top - out[:, 2], 0.0)
+    out[:, 2] = z0 + depth(top - z0) - depth(zeta)
+    return out
+
+
+def _fill_fluid(rng, cols, spacing, origin, count, carve, g_over_k=None):
+    """Fill columns bottom-up with a lattice, skip points that `carve` rejects, keep `count`.
+    With g_over_k (= |g| / k) the lattice starts settled under its own weight (see
+    _settle_columns) instead of at uniform rest density, which would first collapse."""
     nx, ny = cols
     nz = int(np.ceil(count / (nx * ny))) + 8
     pts = _lattice((nx, ny, nz), spacing, origin)
+    if g_over_k is not None:
+        # the surface of the uncompressed fill of `count` points, then settle and carve
+        kept = pts[~carve(pts)] if carve is not None else pts
+        top = kept[:count, 2].max() + 0.5 * spacing
+        pts = _settle_columns(pts, spacing, top, g_over_k)
     if carve is not None:
         pts = pts[~carve(pts)]
     if pts.shape[0] < count:
@@ -273,8 +295,12 @@ def stirring_tank(seed=0, n_fluid=250_000, cols=(125, 125), tank=(1.0, 1.0, 0.5)
 
 
 def coupled(seed=0, n_fluid=1_000_000, cols=(200, 100), tank=(2.0, 1.0, 0.6), n_substeps=1000,
-            spacing=0.01, probe_r=0.0964, soft_n=24, young=5e4, poisson=0.45):
-    """Coupled scene: fluid at 0.01 m, random-walk sphere probe, free soft cube."""
+            spacing=0.01, probe_r=0.0964, soft_n=24, young=5e4, poisson=0.45, settled=True,
+            wall_layers=2):
+    """Coupled scene: fluid at 0.01 m, random-walk sphere probe, free soft cube.  The fluid
+    starts settled under its own weight (layers closer near the floor); started at uniform
+    rest density, the 0.5 m column first collapses and the pressure overshoot pushes corner
+    particles through the two wall layers within ~250 substeps."""
     rng = np.random.default_rng(seed)
     s = spacing
     dt = 5e-4
@@ -292,8 +318,10 @@ def coupled(seed=0, n_fluid=1_000_000, cols=(200, 100), tank=(2.0, 1.0, 0.6), n_
         in_soft = np.all(np.abs(pts - soft_c) <= soft_half, axis=1)
         return in_probe | in_soft
 
-    fluid = _fill_fluid(rng, cols, s, (0.0, 0.0, 0.0), n_fluid, carve)
-    walls = Body(KIND_STATIC, wall_shell((0, 0, 0), tank, s), s)
+    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s), (tx + 3 * s, ty + 3 * s, 1.4 * tz))
+    g_over_k = 9.81 / params["k"] if settled else None
+    fluid = _fill_fluid(rng, cols, s, (0.0, 0.0, 0.0), n_fluid, carve, g_over_k)
+    walls = Body(KIND_STATIC, wall_shell((0, 0, 0), tank, s, layers=wall_layers), s)
     pmass = 1000.0 * probe_local.shape[0] * (s / 2) ** 3
     inertia = np.eye(3, dtype=np.float32) * np.float32(0.4 * pmass * probe_r ** 2)
     m = probe_r + 0.02
@@ -303,7 +331,6 @@ def coupled(seed=0, n_fluid=1_000_000, cols=(200, 100), tank=(2.0, 1.0, 0.6), n_
                  pose=traj[0, :7].copy(), vel=traj[0, 7:].copy())
     soft = Body(KIND_SOFT, soft_xyz, s, springs=lattice_springs(soft_dims), young=young,
                 poisson=poisson)
-    params = make_params(s, dt, (-3 * s, -3 * s, -3 * s), (tx + 3 * s, ty + 3 * s, 1.4 * tz))
     return Scene("coupled", params, fluid, np.zeros_like(fluid), s, [walls, probe, soft],
                  grab_body=1, trajectory=traj, n_substeps=n_substeps)
 

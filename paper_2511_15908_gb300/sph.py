@@ -38,7 +38,7 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc",
            "sph_iso_grid", "sph_iso_field", "sph_iso_workspace_bytes", "sph_iso_polygonize",
            "sph_set_anchors", "sph_cut_springs", "sph_checkpoint_bytes", "sph_checkpoint_save",
-           "sph_checkpoint_load", "sph_haptic_cycle"]
+           "sph_checkpoint_load", "sph_haptic_cycle", "sph_measure_fp32_fma"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -168,6 +168,9 @@ def load(path: str = LIB_PATH):
     L.sph_mlp_destroy.argtypes = [_vp]
     L.sph_cell_sort_noalloc.restype = st
     L.sph_cell_sort_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.sph_measure_fp32_fma.restype = st
+    L.sph_measure_fp32_fma.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp,
+                                       ctypes.POINTER(ctypes.c_double)]
     L.sph_haptic_cycle.restype = st
     L.sph_haptic_cycle.argtypes = [_vp, ctypes.c_int32, _f32p, _f32p, ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_double)]
@@ -638,6 +641,9 @@ def cell_sort_noalloc(params: dict, x_dev, stream=None, out=None):
     n = int(x_dev.shape[0])
     x_dev = x_dev.contiguous()
     ncell = int(np.prod(grid_dims(params)))
+    if n > NOALLOC_MAX_PARTICLES or ncell > NOALLOC_MAX_CELLS:
+        # the library refuses these sizes too; refuse before allocating the outputs
+        raise SphError(ERR_CAPACITY, "sph_cell_sort_noalloc: beyond the fixed scratch")
     if out is not None:
         keys, order, cs = out
         if keys.numel() < n or order.numel() < n or cs.numel() < ncell + 1:
@@ -652,6 +658,32 @@ def cell_sort_noalloc(params: dict, x_dev, stream=None, out=None):
     if r != OK:
         raise SphError(r, "sph_cell_sort_noalloc failed")
     return keys[:n], order[:n], cs
+
+
+def measure_fp32_fma(device=0, iters=65536, reps=5):
+    """FP32 FMA throughput of the GPU in TFLOP/s (best of `reps` launches of the library's
+    FMA probe kernel at full occupancy, CUDA events on one stream)."""
+    import torch
+    L = load()
+    props = torch.cuda.get_device_properties(device)
+    blocks = props.multi_processor_count * (props.max_threads_per_multi_processor // 256)
+    sink = torch.zeros(256, dtype=torch.float32, device=f"cuda:{device}")
+    s = torch.cuda.Stream(device=device)
+    flops = ctypes.c_double(0.0)
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        st = L.sph_measure_fp32_fma(ctypes.c_void_p(s.cuda_stream), blocks, iters, ctypes.c_void_p(sink.data_ptr()),
+                                    ctypes.byref(flops))
+        if st != OK:
+            raise SphError(st, "sph_measure_fp32_fma failed")
+        e1.record(s)
+        e1.synchronize()
+        if r > 0:
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+    return flops.value / best / 1e12
 
 
 def iso_grid(params: dict, cube: float):

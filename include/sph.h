@@ -319,6 +319,38 @@ sph_status sph_mlp_sync(sph_mlp *m);
 const char *sph_mlp_last_error(const sph_mlp *m);
 void sph_mlp_destroy(sph_mlp *m);
 
+/*
+ * The haptic tick on the device (Sec. 3.3: the engine hands the device a new force about
+ * every 60 Hz update cycle; the device wants one every millisecond).  At the start of an
+ * update cycle sph_surrogate_anchor records the last substep's descriptor and the grabbed
+ * body's exact FP64 wrench into the model (enqueued on the handle's stream; the model's
+ * stream waits for it).  Each tick, sph_surrogate_tick takes the grab pose and velocity at
+ * that instant (host, 13 floats: x y z qw qx qy qz vx vy vz wx wy wz) and the time since
+ * the anchor, builds the network's 269 scale-free inputs on the device, runs the network
+ * and returns the anchor's exact wrench plus the predicted change (host, 6 doubles, world
+ * frame, torque about the grab point).  Synchronises the model's stream.
+ *
+ * Inputs, in the anchor's body frame R_a (from its quaternion): R_a^T (x - x_a) / h,
+ * tau c / h, R_a^T (v - v_a) / c, R_a^T v / c, R_a^T w h / c, then per descriptor cell
+ * rho / rho0 - 1 (-1 when empty) and R_a^T v_cell / c; c = sqrt(k) is the sound speed of
+ * Eq. pressure.  The network's output is the wrench change since the anchor in that frame,
+ * forces over rho0 c^2 h^2, torques over rho0 c^2 h^3.  sph_surrogate_features and
+ * sph_surrogate_targets build the same inputs and outputs for n logged pairs (DEVICE
+ * arrays: ticks with tick_stride floats per row, anchors with anchor_stride >= 269, times
+ * since the anchor, wrenches n x 6 doubles) for training, with the scales of the scene
+ * given to sph_surrogate_set_scene (h, k, rho0; sph_surrogate_anchor sets them too).
+ * Errors: SPH_ERR_ARG, SPH_ERR_STATE (tick without an anchor; anchor without a grabbed
+ * body or before the first substep), SPH_ERR_CUDA, SPH_ERR_TIMEOUT.
+ */
+sph_status sph_surrogate_set_scene(sph_mlp *m, const sph_params *p);
+sph_status sph_surrogate_anchor(sph_handle *h, sph_mlp *m);
+sph_status sph_surrogate_tick(sph_mlp *m, const float pose_vel[13], float elapsed, double out[6]);
+sph_status sph_surrogate_features(sph_mlp *m, const float *d_ticks, int32_t tick_stride,
+                                  const float *d_anchors, int32_t anchor_stride, const float *d_elapsed,
+                                  int32_t n, float *d_x);
+sph_status sph_surrogate_targets(sph_mlp *m, const double *d_wrench, const double *d_anchor_wrench,
+                                 const float *d_anchors, int32_t anchor_stride, int32_t n, float *d_t);
+
 /* Counts: particles, fluid particles, grid cells (nx*ny*nz), bodies, substeps run. */
 sph_status sph_get_info(sph_handle *h, int64_t out[5]);
 

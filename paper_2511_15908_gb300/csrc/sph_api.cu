@@ -314,6 +314,17 @@ const sph_params *scene_params(sph_handle *h) { return &h->p; }
 
 }  // namespace sphgb
 
+namespace sphgb {
+void handle_surrogate_view(const sph_handle *h, cudaStream_t *stream, const SimConst **c, int *grab,
+                           long long *substeps)
+{
+    *stream = h->stream;
+    *c = &h->c;
+    *grab = h->grab;
+    *substeps = (long long)h->substeps;
+}
+}  // namespace sphgb
+
 extern "C" {
 
 size_t sph_workspace_bytes(const sph_params *p, const sph_capacity *cap)

@@ -116,3 +116,11 @@ cudaError_t launch_sorted_keys(const SimConst &c, cudaStream_t s, uint32_t *keys
 cudaError_t launch_descriptor(const SimConst &c, cudaStream_t s, int grab_body, float *d_out);
 
 }  // namespace sphgb
+
+struct sph_handle;
+namespace sphgb {
+// The surrogate's view of a handle (sph_api.cu): its stream, constants and grabbed body
+// (-1 if none), and the number of substeps run.
+void handle_surrogate_view(const sph_handle *h, cudaStream_t *stream, const SimConst **c, int *grab,
+                           long long *substeps);
+}  // namespace sphgb

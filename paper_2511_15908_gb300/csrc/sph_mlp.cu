@@ -205,6 +205,123 @@ cudaError_t launch_descriptor(const SimConst &c, cudaStream_t s, int grab_body, 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ scale-free tick inputs
+
+// The scene's scales: smoothing length h, sound speed c = sqrt(k) (the pressure constant of
+// Eq. pressure is c^2), rest density rho0.  Lengths are measured in h, velocities in c,
+// times in h / c, densities as rho / rho0 - 1, forces in rho0 c^2 h^2 and torques in
+// rho0 c^2 h^3, so that one network can read scenes of different resolution and body size.
+struct SurScale {
+    float h, c, rho0;
+};
+
+// R(q)^T v for q = (w, x, y, z) (the anchor's body frame), FP32.
+__device__ __forceinline__ void rot_t_apply(const float q[4], const float v[3], float o[3])
+{
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    const float R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                        2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                        2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    for (int i = 0; i < 3; ++i) o[i] = R[i] * v[0] + R[3 + i] * v[1] + R[6 + i] * v[2];
+}
+
+// The 269 network inputs of one tick.  t13: the grab pose and velocity at the tick (x y z
+// qw qx qy qz vx vy vz wx wy wz); a: the anchor's descriptor (sph_get_descriptor: the same 13
+// values at the anchor substep, then 64 cells x (density, velocity)); tau: time since the
+// anchor.  Output: R_a^T (x - x_a) / h, tau c / h, R_a^T (v - v_a) / c, R_a^T v / c,
+// R_a^T w h / c, then per cell rho / rho0 - 1 (-1 for an empty cell) and R_a^T v_cell / c.
+__device__ __forceinline__ void sur_features(const float *t13, const float *a, float tau,
+                                             const SurScale &s, float *out)
+{
+    const float ih = 1.0f / s.h, ic = 1.0f / s.c, irho = 1.0f / s.rho0;
+    const float qa[4] = {a[3], a[4], a[5], a[6]};
+    float d[3], o[3];
+    for (int i = 0; i < 3; ++i) d[i] = (t13[i] - a[i]) * ih;
+    rot_t_apply(qa, d, o);
+    for (int i = 0; i < 3; ++i) out[i] = o[i];
+    out[3] = tau * s.c * ih;
+    for (int i = 0; i < 3; ++i) d[i] = (t13[7 + i] - a[7 + i]) * ic;
+    rot_t_apply(qa, d, o);
+    for (int i = 0; i < 3; ++i) out[4 + i] = o[i];
+    for (int i = 0; i < 3; ++i) d[i] = t13[7 + i] * ic;
+    rot_t_apply(qa, d, o);
+    for (int i = 0; i < 3; ++i) out[7 + i] = o[i];
+    for (int i = 0; i < 3; ++i) d[i] = t13[10 + i] * s.h * ic;
+    rot_t_apply(qa, d, o);
+    for (int i = 0; i < 3; ++i) out[10 + i] = o[i];
+    for (int k = 0; k < 64; ++k) {
+        const float *cell = a + 13 + 4 * k;
+        out[13 + 4 * k] = cell[0] * irho - 1.0f;
+        for (int i = 0; i < 3; ++i) d[i] = cell[1 + i] * ic;
+        rot_t_apply(qa, d, o);
+        for (int i = 0; i < 3; ++i) out[14 + 4 * k + i] = o[i];
+    }
+}
+
+// One row per thread: ticks (stride tick_stride floats), anchors (stride anchor_stride),
+// times since the anchor; out n x 269.
+__global__ void k_sur_features(const float *ticks, int tick_stride, const float *anchors,
+                               int anchor_stride, const float *taus, int n, SurScale s, float *out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    sur_features(ticks + (size_t)r * tick_stride, anchors + (size_t)r * anchor_stride, taus[r], s,
+                 out + (size_t)r * 269);
+}
+
+// Training targets: the wrench change since the anchor in the anchor's body frame, in the
+// force and torque scales (FP64 difference, then FP32).
+__global__ void k_sur_targets(const double *w, const double *wa, const float *anchors, int anchor_stride,
+                              int n, SurScale s, float *out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float *a = anchors + (size_t)r * anchor_stride;
+    const float qa[4] = {a[3], a[4], a[5], a[6]};
+    const double fs = (double)s.rho0 * s.c * s.c * s.h * s.h;
+    for (int part = 0; part < 2; ++part) {
+        const double sc = part == 0 ? fs : fs * s.h;
+        float d[3], o[3];
+        for (int i = 0; i < 3; ++i)
+            d[i] = (float)((w[(size_t)r * 6 + 3 * part + i] - wa[(size_t)r * 6 + 3 * part + i]) / sc);
+        rot_t_apply(qa, d, o);
+        for (int i = 0; i < 3; ++i) out[(size_t)r * 6 + 3 * part + i] = o[i];
+    }
+}
+
+// The tick's inputs from its pose and velocity (kernel arguments) and the stored anchor.
+__global__ void k_sur_tick_features(float t0, float t1, float t2, float t3, float t4, float t5, float t6,
+                                    float t7, float t8, float t9, float t10, float t11, float t12,
+                                    float tau, const float *anchor, SurScale s, float *out)
+{
+    if (threadIdx.x != 0) return;
+    const float t13[13] = {t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12};
+    sur_features(t13, anchor, tau, s, out);
+}
+
+// The tick's wrench: the anchor's exact FP64 wrench plus the network's correction, taken out
+// of the standardised, scale-free, body-frame output.
+__global__ void k_sur_tick_output(const float *y, const float *ymean, const float *ystd, const float *anchor,
+                                  const double *wa, SurScale s, double *out)
+{
+    if (threadIdx.x != 0) return;
+    const float qa[4] = {anchor[3], anchor[4], anchor[5], anchor[6]};
+    const float w = qa[0], x = qa[1], yq = qa[2], z = qa[3];
+    const float R[9] = {1 - 2 * (yq * yq + z * z), 2 * (x * yq - w * z), 2 * (x * z + w * yq),
+                        2 * (x * yq + w * z), 1 - 2 * (x * x + z * z), 2 * (yq * z - w * x),
+                        2 * (x * z - w * yq), 2 * (yq * z + w * x), 1 - 2 * (x * x + yq * yq)};
+    const double fs = (double)s.rho0 * s.c * s.c * s.h * s.h;
+    for (int part = 0; part < 2; ++part) {
+        const double sc = part == 0 ? fs : fs * s.h;
+        float b[3];
+        for (int i = 0; i < 3; ++i) b[i] = y[3 * part + i] * ystd[3 * part + i] + ymean[3 * part + i];
+        for (int i = 0; i < 3; ++i) {
+            const float wv = R[3 * i] * b[0] + R[3 * i + 1] * b[1] + R[3 * i + 2] * b[2];
+            out[3 * part + i] = wa[3 * part + i] + (double)wv * sc;
+        }
+    }
+}
+
 }  // namespace sphgb
 
 using namespace sphgb;
@@ -221,6 +338,15 @@ struct sph_mlp {
     float *dW1, *dW2, *dW3, *dW4t, *db1, *db2, *db3, *db4;
     double *loss;
     unsigned *status;
+    // the haptic tick: anchor descriptor (269), anchor wrench (6 doubles), the tick's input
+    // row (269) and result (6 doubles); scales; pinned host copy of the result; the event
+    // that orders the anchor (handle's stream) before the ticks (model's stream)
+    float *anchor, *tick_x;
+    double *anchor_w, *tick_w;
+    SurScale scale = {0.0f, 0.0f, 0.0f};
+    double *pin = nullptr;
+    cudaEvent_t anchored = nullptr;
+    bool has_anchor = false;
     std::string err;
 };
 
@@ -266,6 +392,10 @@ size_t mlp_sizes(int B, size_t *sz)
     sz[i++] = 4 * (size_t)kOutPad;            // db4
     sz[i++] = 8;                              // loss
     sz[i++] = 16;                             // status
+    sz[i++] = 4 * (size_t)kIn;                // anchor
+    sz[i++] = 4 * (size_t)kIn;                // tick_x
+    sz[i++] = 8 * (size_t)kOut;               // anchor_w
+    sz[i++] = 8 * (size_t)kOut;               // tick_w
     return (size_t)i;
 }
 
@@ -419,9 +549,18 @@ sph_status sph_mlp_create(void *d_workspace, size_t bytes, void *cuda_stream, in
     m->db1 = f(); m->db2 = f(); m->db3 = f(); m->db4 = f();
     m->loss = reinterpret_cast<double *>(ws + L.off[i++]);
     m->status = reinterpret_cast<unsigned *>(ws + L.off[i++]);
+    m->anchor = f(); m->tick_x = f();
+    m->anchor_w = reinterpret_cast<double *>(ws + L.off[i++]);
+    m->tick_w = reinterpret_cast<double *>(ws + L.off[i++]);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.total, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) { delete m; return SPH_ERR_CUDA; }
+    if (e == cudaSuccess) e = cudaHostAlloc(&m->pin, 8 * kOut, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->anchored, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        if (m->pin) cudaFreeHost(m->pin);
+        delete m;
+        return SPH_ERR_CUDA;
+    }
     *out = m;
     return SPH_OK;
 }
@@ -517,7 +656,92 @@ void sph_mlp_destroy(sph_mlp *m)
 {
     if (!m) return;
     cudaStreamSynchronize(m->stream);
+    if (m->anchored) cudaEventDestroy(m->anchored);
+    if (m->pin) cudaFreeHost(m->pin);
     delete m;
+}
+
+static SurScale scale_of(const sph_params *p)
+{
+    SurScale s;
+    s.h = p->h;
+    s.c = std::sqrt(p->k);
+    s.rho0 = p->rho0;
+    return s;
+}
+
+sph_status sph_surrogate_set_scene(sph_mlp *m, const sph_params *p)
+{
+    if (!m || !p || !(p->h > 0.0f) || !(p->k > 0.0f) || !(p->rho0 > 0.0f)) return SPH_ERR_ARG;
+    m->scale = scale_of(p);
+    return SPH_OK;
+}
+
+sph_status sph_surrogate_features(sph_mlp *m, const float *d_ticks, int32_t tick_stride, const float *d_anchors,
+                                  int32_t anchor_stride, const float *d_elapsed, int32_t n, float *d_x)
+{
+    if (!m || n < 0 || (n > 0 && (!d_ticks || !d_anchors || !d_elapsed || !d_x))) return SPH_ERR_ARG;
+    if (tick_stride < 13 || anchor_stride < kIn || !(m->scale.h > 0.0f)) return SPH_ERR_ARG;
+    if (n == 0) return SPH_OK;
+    k_sur_features<<<(n + 127) / 128, 128, 0, m->stream>>>(d_ticks, tick_stride, d_anchors, anchor_stride,
+                                                           d_elapsed, n, m->scale, d_x);
+    MLP_CUDA(m, cudaGetLastError());
+    return SPH_OK;
+}
+
+sph_status sph_surrogate_targets(sph_mlp *m, const double *d_wrench, const double *d_anchor_wrench,
+                                 const float *d_anchors, int32_t anchor_stride, int32_t n, float *d_t)
+{
+    if (!m || n < 0 || (n > 0 && (!d_wrench || !d_anchor_wrench || !d_anchors || !d_t))) return SPH_ERR_ARG;
+    if (anchor_stride < kIn || !(m->scale.h > 0.0f)) return SPH_ERR_ARG;
+    if (n == 0) return SPH_OK;
+    k_sur_targets<<<(n + 127) / 128, 128, 0, m->stream>>>(d_wrench, d_anchor_wrench, d_anchors, anchor_stride,
+                                                          n, m->scale, d_t);
+    MLP_CUDA(m, cudaGetLastError());
+    return SPH_OK;
+}
+
+sph_status sph_surrogate_anchor(sph_handle *h, sph_mlp *m)
+{
+    if (!h || !m) return SPH_ERR_ARG;
+    cudaStream_t hs;
+    const SimConst *c;
+    int grab;
+    long long substeps;
+    handle_surrogate_view(h, &hs, &c, &grab, &substeps);
+    if (grab < 0 || substeps == 0) return mfail(m, SPH_ERR_STATE, "no grabbed body or no substep run");
+    sph_params p;
+    std::memset(&p, 0, sizeof p);
+    p.h = c->h;
+    p.k = c->k;
+    p.rho0 = c->rho0;
+    m->scale = scale_of(&p);
+    MLP_CUDA(m, launch_descriptor(*c, hs, grab, m->anchor));
+    MLP_CUDA(m, cudaMemcpyAsync(m->anchor_w, c->wrench + 6 * grab, 8 * kOut, cudaMemcpyDeviceToDevice, hs));
+    MLP_CUDA(m, cudaEventRecord(m->anchored, hs));
+    MLP_CUDA(m, cudaStreamWaitEvent(m->stream, m->anchored, 0));
+    m->has_anchor = true;
+    return SPH_OK;
+}
+
+sph_status sph_surrogate_tick(sph_mlp *m, const float pose_vel[13], float elapsed, double out[6])
+{
+    if (!m || !pose_vel || !out || !(elapsed >= 0.0f)) return SPH_ERR_ARG;
+    if (!m->has_anchor) return mfail(m, SPH_ERR_STATE, "no anchor: call sph_surrogate_anchor first");
+    const float *t = pose_vel;
+    k_sur_tick_features<<<1, 32, 0, m->stream>>>(t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9],
+                                                 t[10], t[11], t[12], elapsed, m->anchor, m->scale, m->tick_x);
+    MLP_CUDA(m, cudaGetLastError());
+    sph_status st = mlp_forward(m, m->tick_x, 1);
+    if (st != SPH_OK) return st;
+    const float *ymean = m->norm + 2 * kIn, *ystd = m->norm + 2 * kIn + kOut;
+    k_sur_tick_output<<<1, 32, 0, m->stream>>>(m->y, ymean, ystd, m->anchor, m->anchor_w, m->scale, m->tick_w);
+    MLP_CUDA(m, cudaGetLastError());
+    MLP_CUDA(m, cudaMemcpyAsync(m->pin, m->tick_w, 8 * kOut, cudaMemcpyDeviceToHost, m->stream));
+    st = mlp_status(m);                         // synchronises the model's stream
+    if (st != SPH_OK) return st;
+    std::memcpy(out, m->pin, 8 * kOut);
+    return SPH_OK;
 }
 
 }  // extern "C"

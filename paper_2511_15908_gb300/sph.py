@@ -38,7 +38,9 @@ SYMBOLS = ["sph_workspace_bytes", "sph_create", "sph_add_rigid", "sph_add_soft",
            "sph_mlp_sync", "sph_mlp_last_error", "sph_mlp_destroy", "sph_cell_sort_noalloc",
            "sph_iso_grid", "sph_iso_field", "sph_iso_workspace_bytes", "sph_iso_polygonize",
            "sph_set_anchors", "sph_cut_springs", "sph_checkpoint_bytes", "sph_checkpoint_save",
-           "sph_checkpoint_load", "sph_haptic_cycle", "sph_measure_fp32_fma"]
+           "sph_checkpoint_load", "sph_haptic_cycle", "sph_measure_fp32_fma",
+           "sph_surrogate_set_scene", "sph_surrogate_anchor", "sph_surrogate_tick",
+           "sph_surrogate_features", "sph_surrogate_targets"]
 KERNELS = ["hash", "scan_tiles", "scan_apply", "scatter", "rank_gather", "density", "force",
            "wrench"]
 
@@ -168,6 +170,16 @@ def load(path: str = LIB_PATH):
     L.sph_mlp_destroy.argtypes = [_vp]
     L.sph_cell_sort_noalloc.restype = st
     L.sph_cell_sort_noalloc.argtypes = [ctypes.POINTER(Params), _vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+    L.sph_surrogate_set_scene.restype = st
+    L.sph_surrogate_set_scene.argtypes = [_vp, ctypes.POINTER(Params)]
+    L.sph_surrogate_anchor.restype = st
+    L.sph_surrogate_anchor.argtypes = [_vp, _vp]
+    L.sph_surrogate_tick.restype = st
+    L.sph_surrogate_tick.argtypes = [_vp, _f32p, ctypes.c_float, _f64p]
+    L.sph_surrogate_features.restype = st
+    L.sph_surrogate_features.argtypes = [_vp, _vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp]
+    L.sph_surrogate_targets.restype = st
+    L.sph_surrogate_targets.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp]
     L.sph_measure_fp32_fma.restype = st
     L.sph_measure_fp32_fma.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp,
                                        ctypes.POINTER(ctypes.c_double)]
@@ -613,6 +625,67 @@ class Surrogate:
 
     def sync(self):
         self._check(self.L.sph_mlp_sync(self.m))
+
+    # -- the haptic tick (sph_surrogate_*)
+    def _keep_scales(self, params: dict):
+        # the FP32 scales the library computes (h, c = sqrt(k), rho0), for the caller's records
+        self._scales = {"h": float(np.float32(params["h"])),
+                        "c": float(np.sqrt(np.float32(params["k"]), dtype=np.float32)),
+                        "rho0": float(np.float32(params["rho0"]))}
+
+    def set_scene(self, params: dict):
+        P = make_params(params, 1.0)
+        self._check(self.L.sph_surrogate_set_scene(self.m, ctypes.byref(P)))
+        self._keep_scales(params)
+
+    def scales(self) -> dict:
+        return dict(self._scales)
+
+    def anchor(self, sim: "Simulation"):
+        """The last substep of `sim` becomes the start of an update cycle."""
+        self._check(self.L.sph_surrogate_anchor(sim.h, self.m))
+        self._keep_scales(sim.scene.params)
+
+    def tick(self, pose_vel, elapsed: float, out=None) -> np.ndarray:
+        """Wrench at a haptic tick: anchor wrench + predicted change (host, 6 doubles)."""
+        pv = np.ascontiguousarray(pose_vel, np.float32)
+        out = np.zeros(6, np.float64) if out is None else out
+        self._check(self.L.sph_surrogate_tick(self.m, _ptr(pv, ctypes.c_float), float(elapsed),
+                                              _ptr(out, ctypes.c_double)))
+        return out
+
+    def features(self, ticks_dev, anchors_dev, elapsed_dev):
+        """Scale-free inputs of n (tick, anchor) pairs: ticks (n, >= 13), anchors (n, >= 269)
+        and elapsed (n) CUDA float tensors; returns (n, 269)."""
+        import torch
+        n = int(ticks_dev.shape[0])
+        out = torch.empty((max(n, 1), 269), dtype=torch.float32, device=self.device)
+        ticks_dev, anchors_dev, elapsed_dev = ticks_dev.contiguous(), anchors_dev.contiguous(), elapsed_dev.contiguous()
+        cur = self._enter()
+        self._check(self.L.sph_surrogate_features(self.m, ticks_dev.data_ptr(), int(ticks_dev.shape[1]),
+                                                  anchors_dev.data_ptr(), int(anchors_dev.shape[1]),
+                                                  elapsed_dev.data_ptr(), n, out.data_ptr()))
+        for t in (ticks_dev, anchors_dev, elapsed_dev):
+            t.record_stream(self.stream)
+        self._leave(cur)
+        return out[:n]
+
+    def targets(self, wrench_dev, anchor_wrench_dev, anchors_dev):
+        """Training targets of n pairs: the wrench change since the anchor in the anchor's
+        body frame and the scene's force and torque scales; CUDA tensors in, (n, 6) out."""
+        import torch
+        n = int(wrench_dev.shape[0])
+        out = torch.empty((max(n, 1), 6), dtype=torch.float32, device=self.device)
+        wrench_dev, anchor_wrench_dev, anchors_dev = (wrench_dev.contiguous(), anchor_wrench_dev.contiguous(),
+                                                      anchors_dev.contiguous())
+        cur = self._enter()
+        self._check(self.L.sph_surrogate_targets(self.m, wrench_dev.data_ptr(), anchor_wrench_dev.data_ptr(),
+                                                 anchors_dev.data_ptr(), int(anchors_dev.shape[1]), n,
+                                                 out.data_ptr()))
+        for t in (wrench_dev, anchor_wrench_dev, anchors_dev):
+            t.record_stream(self.stream)
+        self._leave(cur)
+        return out[:n]
 
     def close(self):
         if getattr(self, "m", None):

@@ -3,17 +3,20 @@
 The haptic device needs a force every millisecond, while the engine's update cycle -- the
 rate at which the paper's method hands the device a new (rolling-averaged) coupling force
 (Sec. 3.3) -- is about 60 Hz.  The surrogate fills the gap: at every 1 kHz tick it predicts
-the grabbed body's wrench as the exact wrench of the last update cycle plus a learned
-correction.  The correction is the network's output for 269 inputs: 13 kinematic values
-relative to the last cycle -- the grab point's displacement since the cycle (3), the time
-since the cycle started (1), the change of linear velocity since the cycle (3), the current
-linear and angular velocity (6) -- and the pooled fluid grid of the cycle (256).  The exact FP64 coupling
-reduction of the substep is therefore both the anchor (fallback) and the reference.
+the grabbed body's wrench as the exact wrench of the last update cycle (the anchor) plus a
+learned correction.  The network reads 269 scale-free inputs that the library builds on
+the device from the tick's grab pose and velocity and the anchor's descriptor (pose,
+velocity and the pooled fluid grid around the grab point): see sph_surrogate_tick.  The
+exact FP64 coupling reduction of the substep is both the anchor (fallback) and the
+reference.
 
-Everything numerical runs in the library's kernels (descriptor, MLP forward/backward/Adam,
-the substep itself); this module only schedules calls, selects rows and moves arrays.
+Everything numerical runs in the library's kernels (descriptor, features, targets, MLP
+forward/backward/Adam, the tick, the substep itself); this module only schedules calls,
+selects rows and moves arrays.
 """
 from __future__ import annotations
+
+import time
 
 import numpy as np
 
@@ -51,28 +54,29 @@ def log_run(sim: "sph.Simulation", n_substeps: int, chunk: int = 2048):
     return desc.cpu().numpy(), np.concatenate(wr)
 
 
-def cycle_start(n: int, cycle: int) -> np.ndarray:
-    return (np.arange(n) // cycle) * cycle
+def cycle_start(n: int, cycle: int, first: int = 0) -> np.ndarray:
+    """Anchor substep of every substep: the first substep of its update cycle."""
+    t = np.arange(n)
+    return first + ((t - first) // cycle) * cycle
 
 
-def lagged_inputs(desc: np.ndarray, cycle: int, dt: float) -> np.ndarray:
-    """Input of substep t relative to the first substep c of its update cycle (the last SPH
-    state the haptic loop has seen): displacement x_t - x_c, time (t - c) dt, velocity change
-    v_t - v_c, current v_t and w_t, and the fluid grid of substep c."""
+def pairs(model: "sph.Surrogate", desc: np.ndarray, wrench: np.ndarray, cycle: int, dt: float,
+          rows=None):
+    """Network inputs and targets (CUDA tensors) of the logged substeps `rows` (default: all),
+    each against the first substep of its update cycle, built by the library
+    (sph_surrogate_features / sph_surrogate_targets)."""
+    import torch
     n = desc.shape[0]
-    c = cycle_start(n, cycle)
-    x = np.empty_like(desc)
-    x[:, 0:3] = desc[:, 0:3] - desc[c, 0:3]
-    x[:, 3] = (np.arange(n) - c) * dt
-    x[:, 4:7] = desc[:, 7:10] - desc[c, 7:10]
-    x[:, 7:13] = desc[:, 7:13]
-    x[:, 13:] = desc[c, 13:]
-    return x
-
-
-def residual_targets(wrench: np.ndarray, cycle: int) -> np.ndarray:
-    """Target of substep t: its exact wrench minus the exact wrench of substep c."""
-    return wrench - wrench[cycle_start(wrench.shape[0], cycle)]
+    t = np.arange(n) if rows is None else np.asarray(rows)
+    c = cycle_start(n, cycle)[t]
+    dev = model.device
+    ticks = torch.tensor(np.ascontiguousarray(desc[t, :13]), device=dev)
+    anchors = torch.tensor(np.ascontiguousarray(desc[c]), device=dev)
+    tau = torch.tensor(((t - c) * dt).astype(np.float32), device=dev)
+    x = model.features(ticks, anchors, tau)
+    y = model.targets(torch.tensor(np.ascontiguousarray(wrench[t]), device=dev),
+                      torch.tensor(np.ascontiguousarray(wrench[c]), device=dev), anchors)
+    return x, y
 
 
 def standardisation(x: np.ndarray, y: np.ndarray) -> np.ndarray:
@@ -84,86 +88,140 @@ def standardisation(x: np.ndarray, y: np.ndarray) -> np.ndarray:
     return np.concatenate([xm, xs, ym, ys]).astype(np.float32)
 
 
-def fit(model: "sph.Surrogate", x: np.ndarray, y: np.ndarray, steps: int = 3000, batch: int = 1024,
-        lr: float = 1e-3, seed: int = 0, init_seed: int = 0):
-    """Train from seeded initial weights with Adam on random minibatches (device gathers)."""
+def fit(model: "sph.Surrogate", x, y, steps: int = 3000, batch: int = 1024, lr: float = 1e-3,
+        seed: int = 0, init_seed: int = 0):
+    """Train from seeded initial weights with Adam on random minibatches (device gathers);
+    x, y: CUDA tensors (n, 269) and (n, 6)."""
     import torch
-    model.set_params(scenes.mlp_init_params(init_seed), standardisation(x, y))
-    xd = torch.tensor(np.ascontiguousarray(x, np.float32), device=model.device)
-    yd = torch.tensor(np.ascontiguousarray(y, np.float32), device=model.device)
+    model.set_params(scenes.mlp_init_params(init_seed),
+                     standardisation(x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)))
     g = torch.Generator(device=model.device)
     g.manual_seed(seed)
     losses = []
-    n = xd.shape[0]
+    n = x.shape[0]
     for s in range(steps):
         idx = torch.randint(0, n, (min(batch, n),), device=model.device, generator=g)
         lr_s = lr * (0.1 ** (s / max(1, steps)))          # exponential decay to lr / 10
         want = (s % 100 == 0) or s == steps - 1
-        loss = model.train_step(xd[idx], yd[idx], lr_s, want_loss=want)
+        loss = model.train_step(x[idx], y[idx], lr_s, want_loss=want)
         if want:
             losses.append((s, loss))
     model.sync()
     return losses
 
 
-def predict(model: "sph.Surrogate", x: np.ndarray) -> np.ndarray:
-    import torch
-    out = []
-    xd = torch.tensor(np.ascontiguousarray(x, np.float32), device=model.device)
-    for a in range(0, xd.shape[0], model.max_batch):
-        out.append(model.forward(xd[a:a + model.max_batch]).cpu().numpy())
-    return np.concatenate(out).astype(np.float64)
+def _rel(p, exact, part):
+    sl = slice(0, 3) if part == "force" else slice(3, 6)
+    return float(np.sqrt(np.mean(np.sum((p[:, sl] - exact[:, sl]) ** 2, 1)))
+                 / max(np.sqrt(np.mean(np.sum(exact[:, sl] ** 2, 1))), 1e-30))
 
 
-def haptic_errors(desc: np.ndarray, wrench: np.ndarray, model: "sph.Surrogate", cycle: int,
-                  tick: int, dt: float, window: int = 20):
-    """Relative RMS errors at haptic ticks (every `tick` substeps) against the exact wrench:
-    hold (last update cycle's wrench), rolling mean of the last `window` cycle wrenches
-    (the paper's smoothing) and the surrogate."""
-    n = desc.shape[0]
-    t = np.arange(0, n, tick)
-    c = (t // cycle) * cycle
-    exact = wrench[t]
-    hold = wrench[c]
-    cyc_w = wrench[::cycle]
-    k = t // cycle
-    roll = np.stack([cyc_w[max(0, i - window + 1):i + 1].mean(0) for i in k])
-    pred = hold + predict(model, lagged_inputs(desc, cycle, dt)[t])
-
-    def rel(p, part):
-        sl = slice(0, 3) if part == "force" else slice(3, 6)
-        return float(np.sqrt(np.mean(np.sum((p[:, sl] - exact[:, sl]) ** 2, 1)))
-                     / max(np.sqrt(np.mean(np.sum(exact[:, sl] ** 2, 1))), 1e-30))
-
+def haptic_loop(sim: "sph.Simulation", model: "sph.Surrogate", path: np.ndarray, n_cycles: int,
+                cycle: int, tick: int, dt: float, window: int = 20):
+    """The haptic loop run live: at the start of every update cycle the last substep becomes
+    the anchor (sph_surrogate_anchor); the cycle's substeps run; the 1 kHz ticks of the
+    cycle (every `tick` substeps) each call sph_surrogate_tick with the grab path's pose and
+    velocity at that substep.  Relative RMS errors against the exact wrench of the tick's
+    substep: the surrogate, holding the anchor's wrench, and the rolling mean of the last
+    `window` anchor wrenches (the paper's smoothing).  Also the host time of a tick call."""
+    exact, hold, roll, pred = [], [], [], []
+    anchors = []
+    t_tick, n_tick = 0.0, 0
+    base = int(sim.info()[4])                 # substeps already run; the path continues here
+    for k in range(n_cycles):
+        sim.step(1)
+        model.anchor(sim)
+        sim.step(cycle - 1)
+        w = sim.wrench_log(cycle)             # exact wrench of the cycle's substeps
+        anchors.append(w[0])
+        a0 = w[0]
+        r = np.mean(anchors[-window:], axis=0)
+        for j in range(0, cycle, tick):
+            row = path[min(base + k * cycle + j, path.shape[0] - 1)]
+            t0 = time.perf_counter()
+            p = model.tick(row, j * dt)
+            t_tick += time.perf_counter() - t0
+            n_tick += 1
+            exact.append(w[j])
+            hold.append(a0)
+            roll.append(r)
+            pred.append(p)
+    exact, hold, roll, pred = (np.asarray(a) for a in (exact, hold, roll, pred))
     out = {}
     for name, p in (("hold", hold), ("rolling", roll), ("surrogate", pred)):
-        out[name] = {"force": rel(p, "force"), "torque": rel(p, "torque")}
+        out[name] = {"force": _rel(p, exact, "force"), "torque": _rel(p, exact, "torque")}
+    out["gain_vs_hold"] = out["hold"]["force"] / max(out["surrogate"]["force"], 1e-30)
+    out["ticks"] = int(n_tick)
+    out["tick_host_us"] = 1e6 * t_tick / max(n_tick, 1)
+    return out
+
+
+def offline_errors(model: "sph.Surrogate", desc: np.ndarray, wrench: np.ndarray, cycle: int, tick: int,
+                   dt: float, window: int = 20):
+    """The same errors from logged substeps (network inputs and outputs through the library's
+    batched feature and forward calls; the prediction is taken back to the world frame and
+    the wrench units here, in FP64)."""
+    import torch
+    n = desc.shape[0]
+    t = np.arange(0, n, tick)
+    c = cycle_start(n, cycle)[t]
+    x, _ = pairs(model, desc, wrench, cycle, dt, rows=t)
+    y = []
+    for a in range(0, x.shape[0], model.max_batch):
+        y.append(model.forward(x[a:a + model.max_batch]).cpu().numpy())
+    y = np.concatenate(y).astype(np.float64)
+    sc = model.scales()
+    fs = sc["rho0"] * sc["c"] ** 2 * sc["h"] ** 2
+    q = desc[c, 3:7].astype(np.float64)
+    w_, x_, y_, z_ = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    R = np.stack([np.stack([1 - 2 * (y_ * y_ + z_ * z_), 2 * (x_ * y_ - w_ * z_), 2 * (x_ * z_ + w_ * y_)], -1),
+                  np.stack([2 * (x_ * y_ + w_ * z_), 1 - 2 * (x_ * x_ + z_ * z_), 2 * (y_ * z_ - w_ * x_)], -1),
+                  np.stack([2 * (x_ * z_ - w_ * y_), 2 * (y_ * z_ + w_ * x_), 1 - 2 * (x_ * x_ + y_ * y_)], -1)], 1)
+    dF = np.einsum("nij,nj->ni", R, y[:, :3]) * fs
+    dT = np.einsum("nij,nj->ni", R, y[:, 3:]) * fs * sc["h"]
+    exact = wrench[t]
+    hold = wrench[c]
+    pred = hold + np.concatenate([dF, dT], 1)
+    cyc_w = wrench[::cycle]
+    roll = np.stack([cyc_w[max(0, i - window + 1):i + 1].mean(0) for i in t // cycle])
+    out = {}
+    for name, p in (("hold", hold), ("rolling", roll), ("surrogate", pred)):
+        out[name] = {"force": _rel(p, exact, "force"), "torque": _rel(p, exact, "torque")}
     out["gain_vs_hold"] = out["hold"]["force"] / max(out["surrogate"]["force"], 1e-30)
     out["ticks"] = int(t.size)
     return out
 
 
-def inference_latency_us(sim: "sph.Simulation", model: "sph.Surrogate", reps: int = 200) -> float:
-    """Device time of one haptic tick: descriptor + batch-1 forward (CUDA events)."""
+def jitter_floor(wrench: np.ndarray, half: int = 2):
+    """Relative RMS of the part of the exact wrench that changes faster than a centred
+    moving average over 2 half + 1 substeps: wrench content no input that varies smoothly
+    in time (pose, velocity, a lagged fluid grid) can predict.  Force and torque."""
+    k = 2 * half + 1
+    ker = np.ones(k) / k
+    sm = np.stack([np.convolve(wrench[:, a], ker, mode="same") for a in range(6)], 1)
+    sl = slice(half, wrench.shape[0] - half)
+    return {"force": _rel(sm[sl], wrench[sl], "force"), "torque": _rel(sm[sl], wrench[sl], "torque")}
+
+
+def inference_latency_us(sim: "sph.Simulation", model: "sph.Surrogate", path: np.ndarray,
+                         reps: int = 200) -> dict:
+    """Latency of the haptic tick: the device time of anchor + tick kernels (CUDA events on
+    the model's stream around one sph_surrogate_tick, anchor excluded) and the host time of
+    the whole call (pose in, wrench out)."""
     import torch
-    d = torch.empty((1, N_IN), dtype=torch.float32, device=sim.device)
-    y = torch.empty((1, N_OUT), dtype=torch.float32, device=sim.device)
-    s = model.stream
-    sim.sync()
+    sim.step(1)
+    model.anchor(sim)
+    row = path[0]
+    for _ in range(5):
+        model.tick(row, 1e-3)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(s):
-        for _ in range(5):
-            sim.descriptor_into(d[0])
-            torch.cuda.current_stream().wait_stream(sim.stream)
-            model.forward(d, y)
-    torch.cuda.synchronize()
-    total = 0.0
+    dev, host = 0.0, 0.0
     for _ in range(reps):
-        ev0.record(sim.stream)
-        sim.descriptor_into(d[0])
-        s.wait_stream(sim.stream)
-        model.forward(d, y)
-        ev1.record(s)
+        ev0.record(model.stream)
+        t0 = time.perf_counter()
+        model.tick(row, 1e-3)
+        host += time.perf_counter() - t0
+        ev1.record(model.stream)
         ev1.synchronize()
-        total += ev0.elapsed_time(ev1)
-    return 1e3 * total / reps
+        dev += ev0.elapsed_time(ev1)
+    return {"device_us": 1e3 * dev / reps, "host_us": 1e6 * host / reps}

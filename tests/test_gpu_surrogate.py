@@ -59,8 +59,13 @@ def test_gradients_match_oracle(sph):
               128 * 272 + 32768, 128 * 272 + 32768 + 768, omlp.param_count()]
     for a, b in zip(bounds[:-1], bounds[1:]):
         ga, gb = g[a:b].astype(np.float64), gref[a:b]
-        rel = np.linalg.norm(ga - gb) / np.linalg.norm(gb)
-        assert rel <= 1e-2, (a, b, rel)
+        # element by element: both sides round to BF16 at the same points, so they differ
+        # only where an FP32 tensor-core sum and the FP64 sum round an activation or a
+        # back-propagated value to neighbouring BF16 numbers (one unit: 2^-8 relative)
+        rms = np.sqrt(np.mean(gb * gb))
+        ratio = np.abs(ga - gb) / (2.0 ** -6 * np.abs(gb) + 2.0 ** -8 * rms)
+        print(f"block [{a}, {b}): max |dg| / (2^-6 |g| + 2^-8 rms) = {ratio.max():.3f}")
+        assert ratio.max() <= 1.0, (a, b, ratio.max())
     m.close()
 
 
@@ -111,31 +116,93 @@ def test_descriptor_matches_oracle(sph):
     sim.close()
 
 
+def _rot(q):
+    w, x, y, z = (float(v) for v in q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def test_haptic_tick_matches_oracle_network(sph):
+    # sph_surrogate_tick: scale-free inputs from the tick's pose and the anchor's descriptor,
+    # the network, and the anchor's exact wrench plus the prediction, all on the device;
+    # checked against the inputs restated here in FP64 from the documented formulas, the
+    # oracle's network (BF16 at the same rounding points) and the anchor's wrench
+    import torch
+    sc = scenes.with_velocity_noise(
+        scenes.stirring_tank(seed=3, n_fluid=30_000, cols=(50, 50), tank=(0.4, 0.4, 0.3), n_substeps=40,
+                             paddle=(0.02, 0.1, 0.2)), seed=3, sigma=0.2)
+    sim = sph.Simulation(sc)
+    sim.step(5)
+    params, norm, _, _ = _data(1, seed=4)
+    m = sph.Surrogate(max_batch=64)
+    m.set_params(params, norm)
+    m.anchor(sim)
+    anchor = sim.descriptor()                  # the same descriptor the anchor recorded
+    w_a = sim.grab_wrench()
+    h = float(np.float32(sc.params["h"]))
+    c = float(np.sqrt(np.float32(sc.params["k"]), dtype=np.float32))
+    rho0 = float(np.float32(sc.params["rho0"]))
+    fs = rho0 * c * c * h * h
+    R = _rot(anchor[3:7])
+    for j, row in enumerate(sc.trajectory[6:12]):
+        tau = float(np.float32((j + 1) * 5e-4))
+        got = m.tick(row, tau)
+        a = anchor.astype(np.float64)
+        t = row.astype(np.float64)
+        x = np.empty(269)
+        x[0:3] = R.T @ (t[0:3] - a[0:3]) / h
+        x[3] = tau * c / h
+        x[4:7] = R.T @ (t[7:10] - a[7:10]) / c
+        x[7:10] = R.T @ t[7:10] / c
+        x[10:13] = R.T @ t[10:13] * h / c
+        cells = a[13:].reshape(64, 4)
+        x[13::4] = cells[:, 0] / rho0 - 1.0
+        v = (R.T @ cells[:, 1:].T).T / c
+        x[14::4], x[15::4], x[16::4] = v[:, 0], v[:, 1], v[:, 2]
+        y = omlp.forward(params, norm, x[None, :].astype(np.float32), bf=True)[0]
+        want = np.concatenate([w_a[:3] + R @ y[:3] * fs, w_a[3:] + R @ y[3:] * fs * h])
+        dif = np.abs(got - want)
+        scale = np.concatenate([np.full(3, np.abs(R @ y[:3] * fs).max()), np.full(3, np.abs(R @ y[3:] * fs * h).max())])
+        assert np.all(dif <= 2e-3 * scale + 1e-9 * np.abs(w_a)), (j, got, want)
+    with pytest.raises(sph.SphError):
+        m2 = sph.Surrogate(max_batch=8)
+        try:
+            m2.tick(sc.trajectory[0], 0.0)           # no anchor yet
+        finally:
+            m2.close()
+    sim.close()
+    m.close()
+
+
 def test_surrogate_beats_the_update_cycle_hold_at_1khz(sph):
     """What the trained network gains over the method without it: at 1 kHz haptic ticks on
-    held-out substeps of a stirring run, the surrogate (exact wrench of the last ~60 Hz
-    update cycle + learned correction) against holding that exact wrench, and against the
-    paper's rolling average over 20 update cycles."""
+    substeps after the training ones, run live through the library's tick (anchor at every
+    ~60 Hz update cycle), the surrogate (exact wrench of the last update cycle + learned
+    correction) against holding that exact wrench, and against the paper's rolling average
+    over 20 update cycles."""
     from paper_2511_15908_gb300 import surrogate
-    n, n_train = 20000, 15000
-    sc = scenes.stirring_tank(seed=4, n_fluid=40_000, cols=(50, 50), tank=(0.4, 0.4, 0.3), n_substeps=n,
-                              paddle=(0.02, 0.1, 0.2))
+    n_train, n_cycles = 15000, 150
+    sc = scenes.stirring_tank(seed=4, n_fluid=40_000, cols=(50, 50), tank=(0.4, 0.4, 0.3),
+                              n_substeps=n_train + 40 * n_cycles, paddle=(0.02, 0.1, 0.2))
     sim = sph.Simulation(sc)
-    desc, wr = surrogate.log_run(sim, n)
+    desc, wr = surrogate.log_run(sim, n_train)
     dt = float(np.float32(sc.params["dt"]))
     cycle, tick = 33, 2                     # dt 5e-4 s: 16.5 ms update cycle, 1 ms tick
-    x = surrogate.lagged_inputs(desc, cycle, dt)
-    y = surrogate.residual_targets(wr, cycle)
     model = sph.Surrogate(max_batch=2048)
-    losses = surrogate.fit(model, x[:n_train], y[:n_train], steps=800, batch=1024, lr=1e-3)
+    model.set_scene(sc.params)
+    x, y = surrogate.pairs(model, desc, wr, cycle, dt)
+    losses = surrogate.fit(model, x, y, steps=2000, batch=1024, lr=1e-3)
     assert losses[-1][1] < losses[0][1]
-    ev = surrogate.haptic_errors(desc[n_train:], wr[n_train:], model, cycle, tick, dt)
+    ev = surrogate.haptic_loop(sim, model, sc.trajectory, n_cycles, cycle, tick, dt)
     print("haptic errors:", ev)
     assert ev["surrogate"]["force"] < ev["hold"]["force"]
     assert ev["surrogate"]["force"] < ev["rolling"]["force"]
+    assert ev["surrogate"]["torque"] < ev["hold"]["torque"]
     assert ev["surrogate"]["force"] <= 0.05          # the form's 5 % target
-    lat = surrogate.inference_latency_us(sim, model)
-    print("latency per tick us:", lat)
-    assert lat < 1000.0
+    assert ev["surrogate"]["torque"] <= 0.05
+    lat = surrogate.inference_latency_us(sim, model, sc.trajectory)
+    print("tick latency:", lat)
+    assert lat["host_us"] < 1000.0
     sim.close()
     model.close()

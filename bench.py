@@ -278,40 +278,67 @@ def run_reference(args):
     return 0
 
 
-def batched_form(args, flush_l2_factory):
-    """Batched scenes: 64 stirring scenes of log-uniform fluid counts (8k-256k) in one persistent
-    graph-captured launch per substep, the launch structure autotuned (persistent kernel,
-    one kernel per phase, or the scenes' own kernels as graph branches); against stepping
-    them one by one."""
-    import torch
-    from paper_2511_15908_gb300 import scenes, sph
-    scs = scenes.batched(seed=0, n_substeps=args.steps + args.warmup + 64)
+def _batch_run(scs, args, tune=True):
+    """Batch of `scs` (autotuned launch structure unless tune is False), warmed up; returns
+    (sims, batch, choice, substeps advanced)."""
+    from paper_2511_15908_gb300 import sph
     sims = [sph.Simulation(sc) for sc in scs]
     batch = sph.Batch(sims)
-    bps, chunk = batch.tune(substeps_per_trial=1)
-    # 8 M particles (about 1 GB of state and lists) is far more than L2 holds, so the steps
-    # run back to back between two device events, for both launch structures
+    choice = batch.tune(substeps_per_trial=2) if tune else None
     for _ in range(args.warmup):
         batch.step(1)
     batch.sync()
-    torch.cuda.synchronize()
-    advanced = int(sims[0].info()[4])        # substeps behind every scene (tuner + warm-up)
+    return sims, batch, choice, int(sims[0].info()[4])
+
+
+def batched_set(name, make, args, cells=(1.001, 2.002)):
+    """One set of independent scenes: the project's autotuner picks the grid cell edge (over
+    `cells`, in h; each candidate's scenes built and tuned) and, for it, the launch structure
+    (persistent cooperative kernel at 1..max resident blocks per SM x 1/2/4 tiles per fetch,
+    one kernel per phase, or every scene's kernels as graph branches; sph_batch_tune).  The
+    batch then runs args.steps substeps back to back between device events, against the same
+    scenes stepped one by one (graph replay per scene, one stream each) from the same state."""
+    import torch
+    from paper_2511_15908_gb300 import sph
+    k = max(args.steps, 10)
+    trials = {}
+    best = None
+    for cell in cells:
+        scs = make(cell)
+        sims, batch, choice, _ = _batch_run(scs, args)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(batch.stream)
+        batch.step(5)
+        e1.record(batch.stream)
+        batch.sync()
+        ms = e0.elapsed_time(e1) / 5
+        trials[f"{cell}h"] = {"ms_per_step": ms, "blocks_per_sm": choice[0], "tiles_per_fetch": choice[1]}
+        for x in sims:
+            x.close()
+        batch.close()
+        if best is None or ms < best[1]:
+            best = (cell, ms, choice)
+    cell, _, choice = best
+    scs = make(cell)
+    sims, batch, _, _ = _batch_run(scs, args, tune=False)
+    batch.configure(*choice)
+    for _ in range(3):
+        batch.step(1)
+    batch.sync()
+    advanced = int(sims[0].info()[4])
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(batch.stream)
-    for i in range(args.steps):
+    for _ in range(k):
         batch.step(1)
     ev1.record(batch.stream)
     batch.sync()
     t_b = ev0.elapsed_time(ev1) / 1e3
     nf = sum(sc.n_fluid for sc in scs)
     na = sum(sc.n_total for sc in scs)
-    # the same scenes stepped one by one (plain path, graph replay per scene, one stream each)
-    # from the same state: the scenes first advance as many substeps as the batch's had
     solo = [sph.Simulation(sc) for sc in scs]
     for s_ in solo:
         s_.step(advanced)
     torch.cuda.synchronize()
-    k = args.steps
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(solo[0].stream)
     for s_ in solo[1:]:
@@ -327,37 +354,44 @@ def batched_form(args, flush_l2_factory):
     e1.synchronize()
     t_seq = e0.elapsed_time(e1) / 1e3
     # batched and one-by-one stepping of the same scenes give identical wrenches
-    ref = [sph.Simulation(sc) for sc in scs[:4]]
-    chk = [sph.Simulation(sc) for sc in scs[:4]]
-    b2 = sph.Batch(chk)
-    b2.step(3)
-    b2.sync()
     werr = 0.0
-    for a, b in zip(ref, chk):
-        a.step(3)
+    for a, b in zip(sims[:4], solo[:4]):
         wa, wb = a.grab_wrench(), b.grab_wrench()
         werr = max(werr, float(np.linalg.norm(wa - wb) / max(np.linalg.norm(wa), 1e-30)))
     info = batch.info()
-    out = {"workload": f"{len(scs)} stirring scenes, fluid counts log-uniform 8k-256k (seed 0): "
-                       f"{nf} fluid / {na} particles", "scenes": len(scs),
-           "value": nf * args.steps / t_b, "unit": UNIT, "ms_per_step": 1e3 * t_b / args.steps,
-           "all_particle_steps_per_s": na * args.steps / t_b,
+    bps = info["blocks_per_sm"]
+    out = {"workload": f"{name}: {len(scs)} stirring scenes, {nf} fluid / {na} particles",
+           "scenes": len(scs), "value": nf * k / t_b, "unit": UNIT, "ms_per_step": 1e3 * t_b / k,
+           "all_particle_steps_per_s": na * k / t_b,
            "one_by_one_ms_per_step": 1e3 * t_seq / k,
-           "speedup_vs_one_by_one": (t_seq / k) / (t_b / args.steps),
-           "l2": "inputs larger than L2 (8 M particles); steps back to back between device events",
-           "autotuned": {"blocks_per_sm": bps, "tiles_per_fetch": chunk, "sms": info["sms"]},
-           "grab_wrench_rel_diff_vs_single_scene": werr,
-           "gpu_launches_per_step": (8 if info["blocks_per_sm"] == 0 else
-                                     8 * len(scs) if info["blocks_per_sm"] < 0 else 1),
-           "launch_structure": ("one kernel per phase over all scenes" if info["blocks_per_sm"] == 0
-                                else "every scene's own kernels as branches of one graph"
-                                if info["blocks_per_sm"] < 0
-                                else "one persistent cooperative kernel")}
-    for x in sims + solo + ref + chk:
+           "speedup_vs_one_by_one": (t_seq / k) / (t_b / k),
+           "autotuned": {"cell_over_h": cell, "blocks_per_sm": bps, "tiles_per_fetch": info["tiles_per_fetch"],
+                         "sms": info["sms"], "candidates": trials},
+           "grab_wrench_rel_diff_vs_one_by_one": werr,
+           "gpu_launches_per_step": (9 if bps == 0 else 8 * len(scs) if bps < 0 else 1),
+           "launch_structure": ("one kernel per phase over all scenes" if bps == 0
+                                else "every scene's own kernels as branches of one graph" if bps < 0
+                                else "one persistent cooperative kernel"),
+           "timing": f"{k} substeps back to back between device events, both sides from the same state"}
+    for x in sims + solo:
         x.close()
     batch.close()
-    b2.close()
     return out
+
+
+def batched_form(args, flush_l2_factory):
+    """Batched scenes: (a) the configuration named for the form -- 64 stirring scenes of
+    log-uniform fluid counts 8k-256k (8 M particles, compute-bound); (b) a launch-bound set --
+    256 compact stirring scenes of 2k-8k fluid (2.7 M particles, 6.5k-17k per scene)."""
+    from paper_2511_15908_gb300 import scenes
+    n_sub = args.steps + args.warmup + 200
+    return {"stirring_64_8k_256k": batched_set(
+                "64 scenes, fluid log-uniform 8k-256k (seed 0)",
+                lambda cell: scenes.batched(seed=0, n_substeps=n_sub, cell_over_h=cell), args),
+            "stirring_256_compact_2k_8k": batched_set(
+                "256 compact scenes, fluid log-uniform 2k-8k (seed 1)",
+                lambda cell: scenes.batched(seed=1, n_scenes=256, lo=2000, hi=8000, compact=True,
+                                            n_substeps=n_sub, cell_over_h=cell), args)}
 
 
 def variant_form(args, sc, flush_l2_factory, flag, what):

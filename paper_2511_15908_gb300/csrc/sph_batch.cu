@@ -83,7 +83,7 @@ __device__ __forceinline__ int scene_of(const int *prefix, int n, int item)
 }
 
 #ifndef SPH_BATCH_MINB
-#define SPH_BATCH_MINB 4      // resident blocks per SM the persistent kernel is built for
+#define SPH_BATCH_MINB 3      // resident blocks per SM the persistent kernel is built for
 #endif
 
 // The scene's constants are staged in shared memory for each tile: read through a global
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
     __shared__ int s_item;
     __shared__ __align__(16) SimConst s_c;
     static_assert(sizeof(SimConst) % 16 == 0, "SimConst is copied as int4");
+    int staged = -1;                  // the scene whose constants s_c holds (block-uniform)
     for (int sub = 0; sub < n_substeps; ++sub) {
         for (int ph = 0; ph < kPhases; ++ph) {
             const int *pre = b.prefix + ph * (b.n_scenes + 1);
@@ -107,11 +108,15 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
                 for (int it = base; it < end; ++it) {
                     const int s = scene_of(pre, b.n_scenes, it);
                     const int blk = it - pre[s];
-                    {
+                    // consecutive tiles mostly belong to one scene: stage its constants only
+                    // when the scene changes (a substep's counter lives in global memory,
+                    // so the staged copy stays valid across phases and substeps)
+                    if (s != staged) {
                         const int4 *src = reinterpret_cast<const int4 *>(b.scenes + s);
                         int4 *dst = reinterpret_cast<int4 *>(&s_c);
                         for (int w = threadIdx.x; w < (int)(sizeof(SimConst) / 16); w += kTile)
                             dst[w] = __ldg(src + w);
+                        staged = s;
                     }
                     __syncthreads();
                     const SimConst &c = s_c;

@@ -1122,27 +1122,23 @@ static __device__ void rigid_update(const SimConst &c, DevBody &B, const Pose &P
     }
     cross3d(arm, F, tc);
     for (int a = 0; a < 3; ++a) tc[a] += W[3 + a];
-    // I_w = R I_b R^T and I_w^-1 = R I_b^-1 R^T (the body-frame inverse is precomputed)
-    double Iw[9], inv[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0, si = 0.0;
-            for (int k = 0; k < 3; ++k)
-                for (int l = 0; l < 3; ++l) {
-                    s += R[3 * i + k] * (double)B.inertia[3 * k + l] * R[3 * j + l];
-                    si += R[3 * i + k] * (double)B.inertia_inv[3 * k + l] * R[3 * j + l];
-                }
-            Iw[3 * i + j] = s;
-            inv[3 * i + j] = si;
-        }
-    double L[3], gyro[3], wn[3];
-    for (int i = 0; i < 3; ++i) L[i] = Iw[3 * i] * w[0] + Iw[3 * i + 1] * w[1] + Iw[3 * i + 2] * w[2];
+    // I_w = R I_b R^T and I_w^-1 = R I_b^-1 R^T (the body-frame inverse is precomputed),
+    // applied as matrix-vector products through the body frame (no 3 x 3 world matrices
+    // are formed, which keeps the batched persistent kernel's register budget small)
+    double wb[3], Lb[3], L[3], gyro[3], rb[3], ab[3], wn[3];
+    for (int k = 0; k < 3; ++k) wb[k] = R[k] * w[0] + R[3 + k] * w[1] + R[6 + k] * w[2];
+    for (int k = 0; k < 3; ++k)
+        Lb[k] = (double)B.inertia[3 * k] * wb[0] + (double)B.inertia[3 * k + 1] * wb[1] +
+                (double)B.inertia[3 * k + 2] * wb[2];
+    for (int i = 0; i < 3; ++i) L[i] = R[3 * i] * Lb[0] + R[3 * i + 1] * Lb[1] + R[3 * i + 2] * Lb[2];
     cross3d(w, L, gyro);
-    for (int i = 0; i < 3; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < 3; ++j) s += inv[3 * i + j] * (tc[j] - gyro[j]);
-        wn[i] = w[i] + s * dt;
-    }
+    for (int k = 0; k < 3; ++k)
+        rb[k] = R[k] * (tc[0] - gyro[0]) + R[3 + k] * (tc[1] - gyro[1]) + R[6 + k] * (tc[2] - gyro[2]);
+    for (int k = 0; k < 3; ++k)
+        ab[k] = (double)B.inertia_inv[3 * k] * rb[0] + (double)B.inertia_inv[3 * k + 1] * rb[1] +
+                (double)B.inertia_inv[3 * k + 2] * rb[2];
+    for (int i = 0; i < 3; ++i)
+        wn[i] = w[i] + (R[3 * i] * ab[0] + R[3 * i + 1] * ab[1] + R[3 * i + 2] * ab[2]) * dt;
     double qv[3] = {P.q[1], P.q[2], P.q[3]}, wq[3], qn[4], nq = 0.0;
     cross3d(wn, qv, wq);
     double dq0 = -(wn[0] * qv[0] + wn[1] * qv[1] + wn[2] * qv[2]);

@@ -340,17 +340,23 @@ def batched_counts(seed=0, n_scenes=64, lo=8_000, hi=256_000):
     return np.exp(rng.uniform(np.log(lo), np.log(hi), n_scenes)).astype(np.int64)
 
 
-def batched(seed=0, n_scenes=64, n_substeps=200, lo=8_000, hi=256_000):
-    """Independent stirring scenes with log-uniform fluid counts (depth 16 layers at 0.008 m)."""
+def batched(seed=0, n_scenes=64, n_substeps=200, lo=8_000, hi=256_000, compact=False,
+            cell_over_h=1.001):
+    """Independent stirring scenes with log-uniform fluid counts (depth 16 layers at 0.008 m).
+    compact: small tanks for small counts (side from 12 columns, 0.2 m walls, a 0.15 m
+    paddle) instead of at least 40 columns and 0.5 m walls, so that walls do not dwarf the
+    fluid of a scene of a few thousand particles.  cell_over_h: the grid's cell edge."""
     counts = batched_counts(seed, n_scenes, lo, hi)
     scenes = []
     for i, c in enumerate(counts):
         side = int(np.ceil(np.sqrt(c / 16.0)))
-        side = max(side, 40)
-        tank = (side * 0.008, side * 0.008, 0.5)
-        paddle = (0.02, min(0.2, 0.25 * side * 0.008), 0.3)
-        scenes.append(stirring_tank(seed=1000 + i, n_fluid=int(c), cols=(side, side), tank=tank,
-                                    n_substeps=n_substeps, paddle=paddle))
+        side = max(side, 12 if compact else 40)
+        tank = (side * 0.008, side * 0.008, 0.2 if compact else 0.5)
+        paddle = (0.02, min(0.2, 0.25 * side * 0.008), 0.15 if compact else 0.3)
+        sc = stirring_tank(seed=1000 + i, n_fluid=int(c), cols=(side, side), tank=tank,
+                           n_substeps=n_substeps, paddle=paddle)
+        sc.params["cell"] = float(np.float32(cell_over_h * sc.params["h"]))
+        scenes.append(sc)
     return scenes
 
 

@@ -1,0 +1,115 @@
+"""Slab decomposition of one scene across ranks (one rank per GPU) -- a prototype.
+
+The substep shards by spatial slabs along the tank's long axis x: rank r owns the particles
+whose x lies in [e_r, e_{r+1}).  Before a substep each rank receives from its two
+neighbours their owned particles within `halo` of its own slab (the ghosts); the per-rank
+substep then computes the owned particles' densities and forces from owned + ghost
+particles, and integrates only the owned ones; after it each body's coupling wrench, summed
+by every rank over the body particles it owns, is summed over ranks (an allreduce of 6
+doubles per body).  With a halo of twice the support radius the ghosts' own densities are
+complete where the owned particles need them (every ghost within R of the slab has all of
+its neighbours among owned + ghosts), so one exchange of positions and velocities per
+substep replaces a second exchange of ghost densities before the force pass.  Particles
+change owner when they cross a slab edge: after the substep every rank keeps the particles
+now in its slab and hands the others to their new owner (the same neighbour exchange).
+
+This module holds the decomposition and the data movement only; the exchanges go through
+torch.distributed (gloo on CPU, NCCL between GPUs; no multicast, no library kernel on peer
+memory).  The per-rank substep is the caller's.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+class Slabs:
+    """Equal slabs of [x_lo, x_hi) along x for `world` ranks; the outer slabs extend to
+    infinity (particles outside the tank still have an owner)."""
+
+    def __init__(self, x_lo: float, x_hi: float, world: int, halo: float):
+        if world < 1 or not (x_hi > x_lo) or not (halo > 0.0):
+            raise ValueError("bad slab decomposition")
+        self.world = world
+        self.halo = float(halo)
+        self.edges = np.linspace(x_lo, x_hi, world + 1)
+        self.edges[0], self.edges[-1] = -np.inf, np.inf
+
+    def owner(self, x: np.ndarray) -> np.ndarray:
+        """Owning rank of each particle (positions (n, 3))."""
+        return np.searchsorted(self.edges[1:-1], np.asarray(x)[:, 0], side="right").astype(np.int64)
+
+    def ghost_masks(self, x: np.ndarray, rank: int):
+        """Of the particles rank owns, those within `halo` of the left and of the right
+        neighbour's slab (the ghosts it sends them); (left, right) boolean masks, all False
+        where the neighbour does not exist."""
+        x0 = np.asarray(x)[:, 0]
+        left = (x0 < self.edges[rank] + self.halo) if rank > 0 else np.zeros(x0.shape, bool)
+        right = (x0 >= self.edges[rank + 1] - self.halo) if rank < self.world - 1 else np.zeros(x0.shape, bool)
+        return left, right
+
+
+def _swap(rows, rank: int, peer: int):
+    """Send `rows` (a float64 tensor (n, k)) to `peer` and receive its rows (blocking; the
+    lower rank sends first so the pair cannot deadlock)."""
+    import torch
+    import torch.distributed as dist
+    k = rows.shape[1]
+    n_out = torch.tensor([rows.shape[0]], dtype=torch.int64)
+    n_in = torch.zeros(1, dtype=torch.int64)
+    if rank < peer:
+        dist.send(n_out, peer)
+        dist.recv(n_in, peer)
+    else:
+        dist.recv(n_in, peer)
+        dist.send(n_out, peer)
+    got = torch.zeros((int(n_in.item()), k), dtype=torch.float64)
+    if rank < peer:
+        if rows.shape[0]:
+            dist.send(rows.contiguous(), peer)
+        if got.shape[0]:
+            dist.recv(got, peer)
+    else:
+        if got.shape[0]:
+            dist.recv(got, peer)
+        if rows.shape[0]:
+            dist.send(rows.contiguous(), peer)
+    return got
+
+
+def neighbour_exchange(rows: np.ndarray, to_left: np.ndarray, to_right: np.ndarray, rank: int,
+                       world: int) -> np.ndarray:
+    """Rows (float64 (n, k)) selected by the masks go to the left / right neighbour; returns
+    the rows received from both neighbours (left's first)."""
+    import torch
+    parts = []
+    rows_t = torch.from_numpy(np.ascontiguousarray(rows, np.float64))
+    # pair (r, r+1) exchanges first for even r, then for odd r: no rank waits on a cycle
+    for phase in (0, 1):
+        for peer, mask in ((rank - 1, to_left), (rank + 1, to_right)):
+            if peer < 0 or peer >= world or (min(rank, peer) % 2) != phase:
+                continue
+            got = _swap(rows_t[torch.from_numpy(np.asarray(mask))], rank, peer)
+            parts.append((peer, got.numpy()))
+    parts.sort(key=lambda p: p[0])
+    k = rows.shape[1]
+    return np.concatenate([p[1] for p in parts]) if parts else np.zeros((0, k))
+
+
+def pack(x: np.ndarray, v: np.ndarray, ids: np.ndarray) -> np.ndarray:
+    """(x, v, id) rows as float64 (FP32 values and int32 ids are exact in FP64)."""
+    return np.concatenate([np.asarray(x, np.float64), np.asarray(v, np.float64),
+                           np.asarray(ids, np.float64)[:, None]], 1)
+
+
+def unpack(rows: np.ndarray):
+    return (rows[:, 0:3].astype(np.float32), rows[:, 3:6].astype(np.float32),
+            rows[:, 6].astype(np.int64))
+
+
+def allreduce_wrench(w: np.ndarray) -> np.ndarray:
+    """Sum of the per-rank wrenches (bodies x 6, FP64) over all ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.from_numpy(np.ascontiguousarray(w, np.float64))
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return t.numpy()

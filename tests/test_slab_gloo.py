@@ -1,0 +1,149 @@
+"""Slab decomposition across ranks (two gloo ranks on CPU, no GPU): each rank owns the
+particles of its x-slab, receives the ghosts within twice the support radius from its
+neighbour through torch.distributed, computes one substep of its owned particles from owned
++ ghosts, and the grabbed body's wrench is the allreduce of the ranks' partial sums.  The
+per-rank substep here is the FP64 oracle, so the test checks the decomposition and its data
+movement: keys bit-equal, densities, accelerations and the wrench equal to one undivided
+oracle substep of the whole scene (to FP64 summation order)."""
+import os
+
+import numpy as np
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import oracle
+from paper_2511_15908_gb300 import scenes, slab
+
+
+def _scene():
+    return scenes.with_velocity_noise(scenes.held_cube_tank(seed=3, n=(14, 10, 12), cube_cells=6),
+                                      seed=3, sigma=0.3)
+
+
+def _positions(sc):
+    """FP32 positions of every particle in id order at the substep's start (rigid particles
+    placed from the pose as the method places them)."""
+    xs = [np.asarray(sc.fluid_x, np.float32)]
+    for b in sc.bodies:
+        if b.kind == scenes.KIND_RIGID:
+            pose = sc.trajectory[0, :7] if sc.bodies.index(b) == sc.grab_body else b.pose
+            R = oracle.rot_f32(np.asarray(pose[3:7], np.float32))
+            xs.append(np.stack([oracle.body_point_f32(R, np.asarray(pose[:3], np.float32), l)
+                                for l in np.asarray(b.xyz, np.float32)]))
+        else:
+            xs.append(np.asarray(b.xyz, np.float32))
+    return np.concatenate(xs)
+
+
+def _sub_scene(sc, ids, x, v):
+    """The scene restricted to particles `ids` (global ids; x, v rows of those particles)."""
+    nf = sc.n_fluid
+    fl = ids < nf
+    bodies, first, grab = [], nf, -1
+    for bi, b in enumerate(sc.bodies):
+        sel = (ids >= first) & (ids < first + b.n)
+        local = ids[sel] - first
+        first += b.n
+        if not sel.any():
+            continue
+        order = np.argsort(local)
+        nb = scenes.Body(b.kind, np.asarray(b.xyz, np.float32)[local[order]], b.spacing, mass=b.mass,
+                         inertia=b.inertia, pose=b.pose, vel=b.vel, grab_local=b.grab_local)
+        if bi == sc.grab_body:
+            grab = len(bodies)
+        bodies.append((nb, ids[sel][order]))
+    fo = np.argsort(ids[fl])
+    sub = scenes.Scene("sub", sc.params, np.ascontiguousarray(x[fl][fo]), np.ascontiguousarray(v[fl][fo]),
+                       sc.fluid_spacing, [b for b, _ in bodies], grab_body=grab, trajectory=sc.trajectory,
+                       n_substeps=sc.n_substeps)
+    sub_ids = np.concatenate([ids[fl][fo]] + [g for _, g in bodies])     # sub id -> global id
+    return sub, sub_ids
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    oracle.set_threads(1)
+    sc = _scene()
+    n = sc.n_total
+    x_all = _positions(sc)
+    v_all = np.zeros((n, 3), np.float32)
+    v_all[:sc.n_fluid] = sc.fluid_v
+    ids_all = np.arange(n)
+    R = 2.0 * float(np.float32(sc.params["h"]))
+    tank_x = 14 * sc.fluid_spacing
+    sl = slab.Slabs(0.0, tank_x, world, halo=2.0 * R)
+    own = sl.owner(x_all) == rank
+    x, v, ids = x_all[own], v_all[own], ids_all[own]
+    left, right = sl.ghost_masks(x, rank)
+    gx, gv, gid = slab.unpack(slab.neighbour_exchange(slab.pack(x, v, ids), left, right, rank, world))
+    sub, sub_ids = _sub_scene(sc, np.concatenate([ids, gid]), np.concatenate([x, gx]), np.concatenate([v, gv]))
+    res = oracle.System(sub, mode=1).substep()
+    gids = sub_ids[res["id"]]                     # global id of each sorted slot
+    mine = np.isin(gids, ids)
+    # the wrench: this rank's owned body particles, pair force m a, torque about the grab point
+    first = sc.n_fluid + sum(b.n for b in sc.bodies[:sc.grab_body])
+    body = sc.bodies[sc.grab_body]
+    in_body = mine & (gids >= first) & (gids < first + body.n)
+    sysm = oracle.System(sub, mode=1)
+    m_sorted = np.abs(sysm.m[res["src"]].astype(np.float64))
+    f = m_sorted[in_body, None] * res["acc"][in_body]
+    xg = sc.trajectory[0, :3].astype(np.float64)            # grab point: the centre (local 0)
+    tau = np.cross(res["x_new"][in_body] - xg, f)
+    w = np.zeros((1, 6))
+    w[0, :3], w[0, 3:] = f.sum(0), tau.sum(0)
+    w_all = slab.allreduce_wrench(w)
+    out[rank] = dict(ids=gids[mine], key=res["key"][mine], rho=res["rho"][mine], acc=res["acc"][mine],
+                     wrench=w_all[0], n_own=int(own.sum()), n_ghost=int(gid.size))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_equal_one_undivided_substep():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = 31000 + os.getpid() % 2000
+        ps = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+        for p in ps:
+            p.start()
+        for p in ps:
+            p.join(300)
+            assert p.exitcode == 0
+        res = dict(out)
+    sc = _scene()
+    ref = oracle.System(sc, mode=1).substep()
+    rid = ref["id"]
+    by_id = lambda k: dict(zip(rid, ref[k]))            # noqa: E731
+    key, rho = by_id("key"), by_id("rho")
+    acc = dict(zip(rid, ref["acc"]))
+    seen = np.concatenate([res[r]["ids"] for r in range(2)])
+    assert np.array_equal(np.sort(seen), np.arange(sc.n_total))     # every particle owned once
+    for r in range(2):
+        d = res[r]
+        assert d["n_ghost"] > 0 and d["n_own"] > 0
+        np.testing.assert_array_equal(d["key"], [key[i] for i in d["ids"]])
+        rr = np.array([rho[i] for i in d["ids"]])
+        assert np.max(np.abs(d["rho"] - rr) / rr) <= 1e-12
+        aa = np.array([acc[i] for i in d["ids"]])
+        scale = np.maximum(np.linalg.norm(aa, axis=1), 0.981)
+        assert np.max(np.linalg.norm(d["acc"] - aa, axis=1) / scale) <= 1e-10
+    wref = ref["wrench"][sc.grab_body]
+    for r in range(2):
+        np.testing.assert_allclose(res[r]["wrench"][:3], wref[:3], rtol=1e-9, atol=1e-12 * np.abs(wref[:3]).max())
+        np.testing.assert_allclose(res[r]["wrench"][3:], wref[3:], rtol=1e-7,
+                                   atol=1e-9 * np.abs(wref[3:]).max() + 1e-14)
+
+
+def test_slab_owner_and_ghost_masks():
+    sl = slab.Slabs(0.0, 1.0, 4, halo=0.1)
+    x = np.array([[-5.0, 0, 0], [0.1, 0, 0], [0.25, 0, 0], [0.3, 0, 0], [0.99, 0, 0], [7.0, 0, 0]])
+    np.testing.assert_array_equal(sl.owner(x), [0, 0, 1, 1, 3, 3])
+    left, right = sl.ghost_masks(x, 1)
+    np.testing.assert_array_equal(left, x[:, 0] < 0.35)
+    np.testing.assert_array_equal(right, x[:, 0] >= 0.4)
+    left0, _ = sl.ghost_masks(x, 0)
+    assert not left0.any()
+    _, right3 = sl.ghost_masks(x, 3)
+    assert not right3.any()

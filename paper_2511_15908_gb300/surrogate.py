@@ -37,14 +37,7 @@ def log_run(sim: "sph.Simulation", n_substeps: int, chunk: int = 2048):
         for i in range(k):
             sim.step(1)
             sim.descriptor_into(desc[done + i])
-        try:
-            wr.append(sim.wrench_log(k))
-        except sph.SphError as e:
-            # particles that splash out of the grid are reported once and clamped; the
-            # coupling wrench is still exact for the particles in the domain
-            if e.status != sph.ERR_DOMAIN:
-                raise
-            wr.append(sim.wrench_log(k))
+        wr.append(_wrench_log(sim, k))
         done += k
     try:
         sim.sync()
@@ -52,6 +45,18 @@ def log_run(sim: "sph.Simulation", n_substeps: int, chunk: int = 2048):
         if e.status != sph.ERR_DOMAIN:
             raise
     return desc.cpu().numpy(), np.concatenate(wr)
+
+
+def _wrench_log(sim: "sph.Simulation", n: int) -> np.ndarray:
+    """The last n substeps' exact grab wrenches; a latched out-of-domain report (particles
+    that splashed out of the grid are clamped into border cells; the coupling wrench is
+    still exact for the particles in the domain) is read once and the log read again."""
+    try:
+        return sim.wrench_log(n)
+    except sph.SphError as e:
+        if e.status != sph.ERR_DOMAIN:
+            raise
+        return sim.wrench_log(n)
 
 
 def cycle_start(n: int, cycle: int, first: int = 0) -> np.ndarray:
@@ -132,7 +137,7 @@ def haptic_loop(sim: "sph.Simulation", model: "sph.Surrogate", path: np.ndarray,
         sim.step(1)
         model.anchor(sim)
         sim.step(cycle - 1)
-        w = sim.wrench_log(cycle)             # exact wrench of the cycle's substeps
+        w = _wrench_log(sim, cycle)           # exact wrench of the cycle's substeps
         anchors.append(w[0])
         a0 = w[0]
         r = np.mean(anchors[-window:], axis=0)

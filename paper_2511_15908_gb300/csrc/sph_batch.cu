@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
                     case P_SCATTER: scatter_item(c, blk); break;
                     case P_GATHER: rank_gather_item(c, blk); break;
                     case P_VOLUME: boundary_volume_item(c, blk); break;
-                    case P_DENSITY: density_item(c, blk); break;
+                    case P_DENSITY: density_item<kTile>(c, blk); break;
                     case P_FORCE: force_item(c, blk); break;
                     default: wrench_item(c, blk); break;
                     }
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kTile, batch_phase_minb<PH>()) k_batch_phase(B
     case P_SCATTER: scatter_item(c, blk); break;
     case P_GATHER: rank_gather_item(c, blk); break;
     case P_VOLUME: boundary_volume_item(c, blk); break;
-    case P_DENSITY: density_item(c, blk); break;
+    case P_DENSITY: density_item<kTile>(c, blk); break;
     case P_FORCE: force_item(c, blk); break;
     default: wrench_item(c, blk); break;
     }

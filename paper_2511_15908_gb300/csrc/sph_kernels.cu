@@ -29,9 +29,9 @@ __global__ void __launch_bounds__(kTile) k_scatter(SimConst c) { scatter_item(c,
 __global__ void __launch_bounds__(kTile) k_rank_gather(SimConst c) { rank_gather_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(SPH_DENSITY_THREADS, SPH_DENSITY_MINB) k_density(SimConst c)
 {
-    density_item(c, blockIdx.x);
+    density_item<SPH_DENSITY_THREADS>(c, blockIdx.x);
 }
-__global__ void __launch_bounds__(kTile, 4) k_density_narrow(SimConst c) { density_item(c, blockIdx.x); }
+__global__ void __launch_bounds__(kTile, 4) k_density_narrow(SimConst c) { density_item<kTile>(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_boundary_volume(SimConst c) { boundary_volume_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force(SimConst c) { force_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_wrench(SimConst c) { wrench_item(c, blockIdx.x); }

@@ -226,25 +226,17 @@ def _oracle_modes():
     return out
 
 
-def _reference_sample(seed=0):
-    """A bounded sample of the coupled workload for the CPU oracle: the same tank height,
-    spacing, probe and soft cube, on a 1/4-length slab (250k fluid particles)."""
-    from paper_2511_15908_gb300 import scenes
-    return scenes.coupled(seed=seed, n_fluid=250_000, cols=(50, 100), tank=(0.5, 1.0, 0.6),
-                          n_substeps=16)
-
-
 def _workload_name(name, sc):
     return (f"{name} scene: {sc.n_fluid} fluid + {sc.n_total - sc.n_fluid} boundary/soft "
             f"particles, dt {sc.params['dt']}")
 
 
-def _reference_config(args):
-    """The same workload line as the CUDA arm's; the oracle times a bounded sample of it."""
-    full = _workload(args.workload)
+def _reference_config(args, full):
+    """The same workload line as the CUDA arm's."""
     return {"workload": _workload_name(args.workload, full), "particles_all": full.n_total,
             "particles_fluid": full.n_fluid, "parallelism": "host cores (oracle)",
-            "sample": "250k-fluid slab of the same tank (same spacing, probe, soft cube)"}
+            "sample": "the full scene's first substeps from its settled fill (the CUDA arm "
+                      "times the stirred state after a 300-substep spin-up)"}
 
 
 def run_reference(args):
@@ -254,7 +246,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    sc = _reference_sample()
+    sc = _workload(args.workload, args.fluid)
     sysm = oracle.System(sc, mode=1)
     for _ in range(args.warmup):
         sysm.substep()
@@ -268,10 +260,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _reference_config(args),
+            "config": _reference_config(args, sc),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} substeps of a 250k-fluid slab "
-                                       f"({sc.n_total} particles) of the coupled scene"},
+                             "sample": f"{args.steps} substeps (after {args.warmup} untimed) of the "
+                                       f"full scene ({sc.n_total} particles), FP64 uniform-grid "
+                                       "oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

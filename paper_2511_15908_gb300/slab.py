@@ -113,3 +113,71 @@ def allreduce_wrench(w: np.ndarray) -> np.ndarray:
     t = torch.from_numpy(np.ascontiguousarray(w, np.float64))
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return t.numpy()
+
+
+def particle_positions(scene) -> np.ndarray:
+    """Positions (id order) used to assign owners: fluid and static / soft particles as
+    given, rigid particles placed from the body's pose at the first substep (FP64, then
+    FP32; the substep itself places them again)."""
+    xs = [np.asarray(scene.fluid_x, np.float32)]
+    for bi, b in enumerate(scene.bodies):
+        if b.kind == 2:                               # rigid
+            pose = (scene.trajectory[0, :7] if bi == scene.grab_body and scene.trajectory is not None
+                    else b.pose).astype(np.float64)
+            w, x, y, z = pose[3:7] / np.linalg.norm(pose[3:7])
+            R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                          [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                          [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+            xs.append((np.asarray(b.xyz, np.float64) @ R.T + pose[:3]).astype(np.float32))
+        else:
+            xs.append(np.asarray(b.xyz, np.float32))
+    return np.concatenate(xs)
+
+
+def particle_velocities(scene) -> np.ndarray:
+    v = np.zeros((scene.n_total, 3), np.float32)
+    v[:scene.n_fluid] = scene.fluid_v
+    return v
+
+
+def sub_scene(scene, ids: np.ndarray, x: np.ndarray, v: np.ndarray):
+    """The scene restricted to the particles `ids` (global ids; x, v their rows): fluid
+    particles as fluid, each body's particles as that body (rigid: their body-frame
+    offsets with the body's pose); returns (scene, sub_ids) with sub_ids[k] the global id
+    of the sub-scene's particle k."""
+    from . import scenes as _sc
+    nf = scene.n_fluid
+    fl = ids < nf
+    bodies, first, grab = [], nf, -1
+    for bi, b in enumerate(scene.bodies):
+        if b.springs is not None and len(b.springs):
+            raise NotImplementedError("soft-body springs across slabs are not handled")
+        sel = (ids >= first) & (ids < first + b.n)
+        local = ids[sel] - first
+        first += b.n
+        if not sel.any():
+            continue
+        order = np.argsort(local)
+        nb = _sc.Body(b.kind, np.asarray(b.xyz, np.float32)[local[order]], b.spacing, mass=b.mass,
+                      inertia=b.inertia, pose=b.pose, vel=b.vel, grab_local=b.grab_local)
+        if bi == scene.grab_body:
+            grab = len(bodies)
+        bodies.append((nb, ids[sel][order]))
+    fo = np.argsort(ids[fl])
+    sub = _sc.Scene("slab", scene.params, np.ascontiguousarray(x[fl][fo]), np.ascontiguousarray(v[fl][fo]),
+                    scene.fluid_spacing, [b for b, _ in bodies], grab_body=grab, trajectory=scene.trajectory,
+                    n_substeps=scene.n_substeps)
+    sub_ids = np.concatenate([ids[fl][fo]] + [g for _, g in bodies]).astype(np.int64)
+    return sub, sub_ids
+
+
+def owned_and_ghosts(scene, slabs: "Slabs", rank: int, world: int):
+    """This rank's owned particles and the ghosts its neighbours send it (one exchange):
+    (owned ids, x, v), (ghost ids, x, v)."""
+    x_all, v_all = particle_positions(scene), particle_velocities(scene)
+    own = slabs.owner(x_all) == rank
+    ids = np.nonzero(own)[0]
+    x, v = x_all[own], v_all[own]
+    left, right = slabs.ghost_masks(x, rank)
+    gx, gv, gid = unpack(neighbour_exchange(pack(x, v, ids), left, right, rank, world))
+    return (ids, x, v), (gid, gx, gv)

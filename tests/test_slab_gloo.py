@@ -21,64 +21,18 @@ def _scene():
                                       seed=3, sigma=0.3)
 
 
-def _positions(sc):
-    """FP32 positions of every particle in id order at the substep's start (rigid particles
-    placed from the pose as the method places them)."""
-    xs = [np.asarray(sc.fluid_x, np.float32)]
-    for b in sc.bodies:
-        if b.kind == scenes.KIND_RIGID:
-            pose = sc.trajectory[0, :7] if sc.bodies.index(b) == sc.grab_body else b.pose
-            R = oracle.rot_f32(np.asarray(pose[3:7], np.float32))
-            xs.append(np.stack([oracle.body_point_f32(R, np.asarray(pose[:3], np.float32), l)
-                                for l in np.asarray(b.xyz, np.float32)]))
-        else:
-            xs.append(np.asarray(b.xyz, np.float32))
-    return np.concatenate(xs)
-
-
-def _sub_scene(sc, ids, x, v):
-    """The scene restricted to particles `ids` (global ids; x, v rows of those particles)."""
-    nf = sc.n_fluid
-    fl = ids < nf
-    bodies, first, grab = [], nf, -1
-    for bi, b in enumerate(sc.bodies):
-        sel = (ids >= first) & (ids < first + b.n)
-        local = ids[sel] - first
-        first += b.n
-        if not sel.any():
-            continue
-        order = np.argsort(local)
-        nb = scenes.Body(b.kind, np.asarray(b.xyz, np.float32)[local[order]], b.spacing, mass=b.mass,
-                         inertia=b.inertia, pose=b.pose, vel=b.vel, grab_local=b.grab_local)
-        if bi == sc.grab_body:
-            grab = len(bodies)
-        bodies.append((nb, ids[sel][order]))
-    fo = np.argsort(ids[fl])
-    sub = scenes.Scene("sub", sc.params, np.ascontiguousarray(x[fl][fo]), np.ascontiguousarray(v[fl][fo]),
-                       sc.fluid_spacing, [b for b, _ in bodies], grab_body=grab, trajectory=sc.trajectory,
-                       n_substeps=sc.n_substeps)
-    sub_ids = np.concatenate([ids[fl][fo]] + [g for _, g in bodies])     # sub id -> global id
-    return sub, sub_ids
-
-
 def _rank(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     oracle.set_threads(1)
     sc = _scene()
-    n = sc.n_total
-    x_all = _positions(sc)
-    v_all = np.zeros((n, 3), np.float32)
-    v_all[:sc.n_fluid] = sc.fluid_v
-    ids_all = np.arange(n)
     R = 2.0 * float(np.float32(sc.params["h"]))
     tank_x = 14 * sc.fluid_spacing
     sl = slab.Slabs(0.0, tank_x, world, halo=2.0 * R)
-    own = sl.owner(x_all) == rank
-    x, v, ids = x_all[own], v_all[own], ids_all[own]
-    left, right = sl.ghost_masks(x, rank)
-    gx, gv, gid = slab.unpack(slab.neighbour_exchange(slab.pack(x, v, ids), left, right, rank, world))
-    sub, sub_ids = _sub_scene(sc, np.concatenate([ids, gid]), np.concatenate([x, gx]), np.concatenate([v, gv]))
+    (ids, x, v), (gid, gx, gv) = slab.owned_and_ghosts(sc, sl, rank, world)
+    own = np.zeros(sc.n_total, bool)
+    own[ids] = True
+    sub, sub_ids = slab.sub_scene(sc, np.concatenate([ids, gid]), np.concatenate([x, gx]), np.concatenate([v, gv]))
     res = oracle.System(sub, mode=1).substep()
     gids = sub_ids[res["id"]]                     # global id of each sorted slot
     mine = np.isin(gids, ids)

@@ -5,8 +5,15 @@
 //
 // Parameters (FP32 master copy, logical layout, 68,358 values):
 //   W1[128][269] b1[128] W2[128][128] b2[128] W3[128][128] b3[128] W4[6][128] b4[6]
-// The GEMMs read zero-padded BF16 copies W1b[128][272], W2b, W3b[128][128], W4b[16][128].
+// The GEMMs read zero-padded BF16 copies W1b[128][272], W2b, W3b[128][128], W4b[16][128] and,
+// for the backward pass, their transposes W2t, W3t[128][128], W4t[128][16]: every GEMM operand
+// is K-contiguous, as the TMA-fed tensor-core GEMM wants.  For the same reason the forward and
+// backward passes also write column-major copies ([feature][batch], leading dimension the
+// batch capacity rounded up to 8) of the activations and gradients the weight gradients
+// contract over the batch.  The weight gradients are split over kSplit K slices (batch
+// ranges) and summed, slice by slice in a fixed order, when the gradient vector is gathered.
 // Inputs are standardised ((x - mean) / std) and outputs de-standardised in the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -19,6 +26,7 @@
 namespace sphgb {
 
 constexpr int kIn = 269, kInPad = 272, kHid = 128, kOut = 6, kOutPad = 16;
+constexpr int kSplit = 8;      // K slices of a weight-gradient GEMM (at most)
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
               kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid,
               kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kOut * kHid, kParams = kOffB4 + kOut;
@@ -27,7 +35,8 @@ static_assert(kParams == 68358, "parameter count");
 // ------------------------------------------------------------------ small kernels
 
 __global__ void k_refresh_bf16(const float *master, __nv_bfloat16 *w1, __nv_bfloat16 *w2,
-                               __nv_bfloat16 *w3, __nv_bfloat16 *w4, float *b4pad)
+                               __nv_bfloat16 *w3, __nv_bfloat16 *w4, float *b4pad, __nv_bfloat16 *w2t,
+                               __nv_bfloat16 *w3t, __nv_bfloat16 *w4t)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < kHid * kInPad) {
@@ -37,22 +46,43 @@ __global__ void k_refresh_bf16(const float *master, __nv_bfloat16 *w1, __nv_bflo
     if (t < kHid * kHid) {
         w2[t] = __float2bfloat16_rn(master[kOffW2 + t]);
         w3[t] = __float2bfloat16_rn(master[kOffW3 + t]);
+        const int i = t / kHid, o = t % kHid;          // transposes: [input][output]
+        w2t[t] = __float2bfloat16_rn(master[kOffW2 + o * kHid + i]);
+        w3t[t] = __float2bfloat16_rn(master[kOffW3 + o * kHid + i]);
     }
     if (t < kOutPad * kHid) {
         int r = t / kHid;
         w4[t] = __float2bfloat16_rn(r < kOut ? master[kOffW4 + t] : 0.0f);
+        const int i = t / kOutPad, o = t % kOutPad;    // W4t[hidden][output]
+        w4t[t] = __float2bfloat16_rn(o < kOut ? master[kOffW4 + o * kHid + i] : 0.0f);
     }
     if (t < kOutPad) b4pad[t] = t < kOut ? master[kOffB4 + t] : 0.0f;
 }
 
+// Standardised BF16 input rows xb[b][c] (zero-padded to 272 columns) and, when xbT is given,
+// the column-major copy xbT[c][b]: a 32 x 32 tile per block, transposed through shared memory
+// so that both copies are written along their contiguous dimension.
 __global__ void k_prep_input(const float *x, int B, const float *mean, const float *inv_std,
-                             __nv_bfloat16 *xb)
+                             __nv_bfloat16 *xb, __nv_bfloat16 *xbT, int ldt)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= B * kInPad) return;
-    int b = t / kInPad, c = t % kInPad;
-    float v = c < kIn ? (x[(size_t)b * kIn + c] - mean[c]) * inv_std[c] : 0.0f;
-    xb[t] = __float2bfloat16_rn(v);
+    __shared__ __nv_bfloat16 tile[32][33];
+    const int c0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += blockDim.y) {
+        const int b = b0 + r, c = c0 + tx;
+        if (b < B && c < kInPad) {
+            const float v = c < kIn ? (x[(size_t)b * kIn + c] - mean[c]) * inv_std[c] : 0.0f;
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            xb[(size_t)b * kInPad + c] = h;
+            tile[r][tx] = h;
+        }
+    }
+    if (!xbT) return;
+    __syncthreads();
+    for (int r = ty; r < 32; r += blockDim.y) {
+        const int c = c0 + r, b = b0 + tx;
+        if (b < B && c < kInPad) xbT[(size_t)c * ldt + b] = tile[tx][r];
+    }
 }
 
 __global__ void k_output(const float *y, int B, const float *mean, const float *std_, float *out)
@@ -63,74 +93,152 @@ __global__ void k_output(const float *y, int B, const float *mean, const float *
     out[t] = y[(size_t)b * kOutPad + j] * std_[j] + mean[j];
 }
 
-// MSE on standardised outputs: L = mean over B x 6 of (y - tn)^2; dY = 2 (y - tn) / (6 B).
-// One block; the loss is summed in a fixed order (deterministic).
-__global__ void k_loss_grad(const float *y, const float *t, int B, const float *mean,
-                            const float *inv_std, float *dyf, __nv_bfloat16 *dyb, double *loss)
+// MSE on standardised outputs: L = mean over B x 6 of (y - tn)^2; dY = 2 (y - tn) / (6 B),
+// written row-major (the A operand of dZ3 = dY W4) and column-major (the B operand of dW4)
+// in BF16.  One element per thread (16 rows of 16 columns per block); each block writes its
+// FP64 share of the squared error and its FP32 column sums of the unrounded dY (the bias
+// gradient db4), both added in a fixed order here and, block by block, by the gather.
+constexpr int kLossThreads = 256;
+__global__ void k_loss_grad(const float *y, const float *t, int B, const float *mean, const float *inv_std,
+                            __nv_bfloat16 *dyb, __nv_bfloat16 *dybT, int ldt, double *loss_part, float *db4_part)
 {
-    __shared__ double s[1024];
+    __shared__ double s[kLossThreads];
+    __shared__ float sg[kLossThreads];
+    const int i = blockIdx.x * kLossThreads + threadIdx.x;
     double acc = 0.0;
-    for (int i = threadIdx.x; i < B * kOutPad; i += blockDim.x) {
-        int b = i / kOutPad, j = i % kOutPad;
+    if (i < B * kOutPad) {
+        const int b = i / kOutPad, j = i % kOutPad;
         float g = 0.0f;
         if (j < kOut) {
-            float tn = (t[(size_t)b * kOut + j] - mean[j]) * inv_std[j];
-            float d = y[i] - tn;
-            acc += (double)d * d;
+            const float tn = (t[(size_t)b * kOut + j] - mean[j]) * inv_std[j];
+            const float d = y[i] - tn;
+            acc = (double)d * d;
             g = 2.0f * d / (float)(kOut * B);
         }
-        dyf[i] = g;
-        dyb[i] = __float2bfloat16_rn(g);
+        const __nv_bfloat16 h = __float2bfloat16_rn(g);
+        dyb[i] = h;
+        dybT[(size_t)j * ldt + b] = h;
+        sg[threadIdx.x] = g;
+    } else {
+        sg[threadIdx.x] = 0.0f;
     }
     s[threadIdx.x] = acc;
     __syncthreads();
-    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < kOutPad) {               // column j = threadIdx.x of the block's 16 rows
+        float c = 0.0f;
+        for (int r = 0; r < kLossThreads / kOutPad; ++r) c += sg[r * kOutPad + threadIdx.x];
+        db4_part[(size_t)blockIdx.x * kOutPad + threadIdx.x] = c;
+    }
+    for (int st = kLossThreads / 2; st > 0; st >>= 1) {
         if ((int)threadIdx.x < st) s[threadIdx.x] += s[threadIdx.x + st];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *loss = s[0] / (double)(kOut * B);
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = s[0];
 }
 
-// Column sums of an [B][ld] FP32 matrix (bias gradients), fixed order.
-__global__ void k_colsum(const float *g, int B, int ld, int ncols, float *out)
+// Where the gather finds the gradients: the weight-gradient GEMMs' K-slice partials
+// (dW1 [128][272], dW2, dW3 [128][128], dW4^T [128][16] per slice) and the bias-gradient
+// partials, per 128-row tile of the dZ GEMMs (column sums of the unrounded dZ, [tile][128])
+// and per block of the loss kernel (dY, [block][16]).
+struct GradSrc {
+    const float *dW1, *dW2, *dW3, *dW4t;
+    int slices;
+    const float *db1, *db2, *db3;
+    int tiles;
+    const float *db4;
+    int blocks;
+};
+
+// Gradient of logical parameter t: its partials summed in order.
+__device__ __forceinline__ float grad_of(const GradSrc &g, int t)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncols) return;
-    float s = 0.0f;
-    for (int b = 0; b < B; ++b) s += g[(size_t)b * ld + c];
-    out[c] = s;
+    const float *p;
+    size_t idx, stride;
+    int n;
+    if (t < kOffB1) {
+        p = g.dW1; idx = (size_t)(t / kIn) * kInPad + t % kIn; stride = (size_t)kHid * kInPad; n = g.slices;
+    } else if (t < kOffW2) {
+        p = g.db1; idx = t - kOffB1; stride = kHid; n = g.tiles;
+    } else if (t < kOffB2) {
+        p = g.dW2; idx = t - kOffW2; stride = (size_t)kHid * kHid; n = g.slices;
+    } else if (t < kOffW3) {
+        p = g.db2; idx = t - kOffB2; stride = kHid; n = g.tiles;
+    } else if (t < kOffB3) {
+        p = g.dW3; idx = t - kOffW3; stride = (size_t)kHid * kHid; n = g.slices;
+    } else if (t < kOffW4) {
+        p = g.db3; idx = t - kOffB3; stride = kHid; n = g.tiles;
+    } else if (t < kOffB4) {
+        const int q = t - kOffW4;
+        p = g.dW4t; idx = (size_t)(q % kHid) * kOutPad + q / kHid; stride = (size_t)kHid * kOutPad; n = g.slices;
+    } else {
+        p = g.db4; idx = t - kOffB4; stride = kOutPad; n = g.blocks;
+    }
+    float v = 0.0f;
+    for (int k = 0; k < n; ++k) v += p[k * stride + idx];
+    return v;
 }
 
-// Assemble the logical gradient vector from the GEMM outputs.
-__global__ void k_gather_grads(const float *dW1, const float *db1, const float *dW2, const float *db2,
-                               const float *dW3, const float *db3, const float *dW4t, const float *db4,
-                               float *grad)
+__device__ __forceinline__ void finish_loss(const double *loss_part, int nblk, int B, double *loss)
+{
+    double l = 0.0;
+    for (int k = 0; k < nblk; ++k) l += loss_part[k];
+    *loss = l / (double)(kOut * B);
+}
+
+// The logical gradient vector (and the loss).
+__global__ void k_gather_grads(GradSrc src, float *grad, const double *loss_part, int nblk, int B, double *loss)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) finish_loss(loss_part, nblk, B, loss);
+    if (t < kParams) grad[t] = grad_of(src, t);
+}
+
+// BF16 images of the updated weight value w of logical parameter t (biases 1-3 are read
+// from the FP32 master copy; the zero padding never changes)
+struct Images {
+    __nv_bfloat16 *w1, *w2, *w3, *w4, *w2t, *w3t, *w4t;
+    float *b4pad;
+};
+__device__ __forceinline__ void write_images(const Images &im, int t, float w)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(w);
+    if (t < kOffB1) {
+        im.w1[(t / kIn) * kInPad + t % kIn] = h;
+    } else if (t >= kOffW2 && t < kOffB2) {
+        const int q = t - kOffW2;
+        im.w2[q] = h;
+        im.w2t[(q % kHid) * kHid + q / kHid] = h;
+    } else if (t >= kOffW3 && t < kOffB3) {
+        const int q = t - kOffW3;
+        im.w3[q] = h;
+        im.w3t[(q % kHid) * kHid + q / kHid] = h;
+    } else if (t >= kOffW4 && t < kOffB4) {
+        const int q = t - kOffW4;
+        im.w4[q] = h;
+        im.w4t[(q % kHid) * kOutPad + q / kHid] = h;
+    } else if (t >= kOffB4) {
+        im.b4pad[t - kOffB4] = w;
+    }
+}
+
+// One training update per parameter: gather its gradient, take the Adam step on the FP32
+// master copy and refresh the BF16 images the next forward pass reads.
+__global__ void k_train_update(GradSrc src, float *w, float *m, float *v, float *grad, float lr, float b1, float b2,
+                               float eps, float c1, float c2, Images im, const double *loss_part, int nblk, int B,
+                               double *loss)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) finish_loss(loss_part, nblk, B, loss);
     if (t >= kParams) return;
-    float v;
-    if (t < kOffB1) { int r = t / kIn, c = t % kIn; v = dW1[r * kInPad + c]; }
-    else if (t < kOffW2) v = db1[t - kOffB1];
-    else if (t < kOffB2) v = dW2[t - kOffW2];
-    else if (t < kOffW3) v = db2[t - kOffB2];
-    else if (t < kOffB3) v = dW3[t - kOffW3];
-    else if (t < kOffW4) v = db3[t - kOffB3];
-    else if (t < kOffB4) { int q = t - kOffW4, j = q / kHid, i = q % kHid; v = dW4t[i * kOutPad + j]; }
-    else v = db4[t - kOffB4];
-    grad[t] = v;
-}
-
-__global__ void k_adam(float *w, float *m, float *v, const float *g, int n, float lr, float b1, float b2,
-                       float eps, float c1, float c2)
-{
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    float gi = g[t];
-    float mi = b1 * m[t] + (1.0f - b1) * gi;
-    float vi = b2 * v[t] + (1.0f - b2) * gi * gi;
+    const float gi = grad_of(src, t);
+    grad[t] = gi;
+    const float mi = b1 * m[t] + (1.0f - b1) * gi;
+    const float vi = b2 * v[t] + (1.0f - b2) * gi * gi;
     m[t] = mi;
     v[t] = vi;
-    w[t] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    const float wn = w[t] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    w[t] = wn;
+    write_images(im, t, wn);
 }
 
 // ------------------------------------------------------------- pooled descriptor
@@ -334,10 +442,16 @@ struct sph_mlp {
     __nv_bfloat16 *w1b, *w2b, *w3b, *w4b;
     float *b4pad;
     __nv_bfloat16 *xb, *h1, *h2, *h3, *dyb, *dz3, *dz2, *dz1;
-    float *z1, *z2, *z3, *y, *dyf, *dz3f, *dz2f, *dz1f, *out;
-    float *dW1, *dW2, *dW3, *dW4t, *db1, *db2, *db3, *db4;
-    double *loss;
+    float *z1, *z2, *z3, *y, *out;
+    float *dW1, *dW2, *dW3, *dW4t;     // K-slice partials of the augmented weight gradients
+    double *loss, *loss_part;
+    float *db4_part, *db3_part, *db2_part, *db1_part;   // bias-gradient partials
     unsigned *status;
+    // K-contiguous operands of the backward GEMMs: weight transposes, and column-major
+    // ([feature][batch], leading dimension ldt) copies of the input, activations and gradients
+    __nv_bfloat16 *w2t, *w3t, *w4t;
+    __nv_bfloat16 *xbT, *h1T, *h2T, *h3T, *dybT, *dz3T, *dz2T, *dz1T;
+    int ldt = 0;
     // the haptic tick: anchor descriptor (269), anchor wrench (6 doubles), the tick's input
     // row (269) and result (6 doubles); scales; pinned host copy of the result; the event
     // that orders the anchor (handle's stream) before the ticks (model's stream)
@@ -355,9 +469,11 @@ namespace {
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct MlpLayout {
-    size_t off[48];
+    size_t off[64];
     size_t total;
 };
+
+int ldt_of(int B) { return (B + 7) & ~7; }
 
 // Every buffer of the surrogate, in order; sizes in bytes for batch capacity B.
 size_t mlp_sizes(int B, size_t *sz)
@@ -379,30 +495,37 @@ size_t mlp_sizes(int B, size_t *sz)
     for (int k = 0; k < 3; ++k) sz[i++] = 2 * (size_t)B * kHid;   // dz3 dz2 dz1
     for (int k = 0; k < 3; ++k) sz[i++] = 4 * (size_t)B * kHid;   // z1 z2 z3
     sz[i++] = 4 * (size_t)B * kOutPad;        // y
-    sz[i++] = 4 * (size_t)B * kOutPad;        // dyf
-    for (int k = 0; k < 3; ++k) sz[i++] = 4 * (size_t)B * kHid;   // dz3f dz2f dz1f
     sz[i++] = 4 * (size_t)B * kOut;           // out
-    sz[i++] = 4 * (size_t)kHid * kInPad;      // dW1
-    sz[i++] = 4 * (size_t)kHid * kHid;        // dW2
-    sz[i++] = 4 * (size_t)kHid * kHid;        // dW3
-    sz[i++] = 4 * (size_t)kHid * kOutPad;     // dW4t
-    sz[i++] = 4 * (size_t)kHid;               // db1
-    sz[i++] = 4 * (size_t)kHid;               // db2
-    sz[i++] = 4 * (size_t)kHid;               // db3
-    sz[i++] = 4 * (size_t)kOutPad;            // db4
+    sz[i++] = 4 * (size_t)kSplit * kHid * kInPad;   // dW1 (K slices)
+    sz[i++] = 4 * (size_t)kSplit * kHid * kHid;     // dW2
+    sz[i++] = 4 * (size_t)kSplit * kHid * kHid;     // dW3
+    sz[i++] = 4 * (size_t)kSplit * kHid * kOutPad;  // dW4t
     sz[i++] = 8;                              // loss
+    const size_t nblk = (size_t)(B * kOutPad + kLossThreads - 1) / kLossThreads;
+    const size_t tiles = (size_t)(B + kTcM - 1) / kTcM;
+    sz[i++] = 8 * nblk;                       // loss_part
+    sz[i++] = 4 * nblk * kOutPad;             // db4_part
+    for (int k = 0; k < 3; ++k) sz[i++] = 4 * tiles * kHid;   // db3_part db2_part db1_part
     sz[i++] = 16;                             // status
     sz[i++] = 4 * (size_t)kIn;                // anchor
     sz[i++] = 4 * (size_t)kIn;                // tick_x
     sz[i++] = 8 * (size_t)kOut;               // anchor_w
     sz[i++] = 8 * (size_t)kOut;               // tick_w
+    sz[i++] = 2 * (size_t)kHid * kHid;        // w2t
+    sz[i++] = 2 * (size_t)kHid * kHid;        // w3t
+    sz[i++] = 2 * (size_t)kHid * kOutPad;     // w4t
+    const size_t lt = (size_t)ldt_of(B);
+    sz[i++] = 2 * (size_t)kInPad * lt;        // xbT
+    for (int k = 0; k < 3; ++k) sz[i++] = 2 * (size_t)kHid * lt;   // h1T h2T h3T
+    sz[i++] = 2 * (size_t)kOutPad * lt;       // dybT
+    for (int k = 0; k < 3; ++k) sz[i++] = 2 * (size_t)kHid * lt;   // dz3T dz2T dz1T
     return (size_t)i;
 }
 
 MlpLayout mlp_layout(int B)
 {
     MlpLayout L;
-    size_t sz[48];
+    size_t sz[64];
     size_t n = mlp_sizes(B, sz), off = 0;
     for (size_t k = 0; k < n; ++k) { L.off[k] = off; off = a256(off + sz[k]); }
     L.total = off;
@@ -422,81 +545,95 @@ sph_status mfail(sph_mlp *m, sph_status s, const std::string &msg)
             return mfail((m), SPH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-TcGemm gemm(const void *A, int lda, int akc, int af32, const void *B, int ldb, int bkc, int bf32, int M,
-            int N, int K, float *C, int ldc, unsigned *status)
+// C[M][N] = A[M][K] B[N][K]^T with K-contiguous BF16 operands
+TcGemm gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M, int N, int K, float *C,
+            int ldc, unsigned *status)
 {
     TcGemm g;
     std::memset(&g, 0, sizeof g);
-    g.A = A; g.lda = lda; g.a_kcontig = akc; g.a_f32 = af32;
-    g.B = B; g.ldb = ldb; g.b_kcontig = bkc; g.b_f32 = bf32;
+    g.A = A; g.lda = lda;
+    g.B = B; g.ldb = ldb;
     g.M = M; g.N = N; g.K = K; g.C = C; g.ldc = ldc;
     g.epilogue = TC_STORE;
+    g.ksplit = 1;
     g.status = status;
     return g;
 }
 
-sph_status mlp_forward(sph_mlp *m, const float *d_x, int B)
+// Forward pass of a batch of B rows; `train` also writes the column-major copies the
+// backward pass contracts over the batch.
+sph_status mlp_forward(sph_mlp *m, const float *d_x, int B, bool train)
 {
     cudaStream_t s = m->stream;
     const float *xmean = m->norm, *xinv = m->norm + kIn;
-    k_prep_input<<<(B * kInPad + 255) / 256, 256, 0, s>>>(d_x, B, xmean, xinv, m->xb);
+    k_prep_input<<<dim3((kInPad + 31) / 32, (B + 31) / 32), dim3(32, 8), 0, s>>>(d_x, B, xmean, xinv, m->xb,
+                                                                                train ? m->xbT : nullptr, m->ldt);
     MLP_CUDA(m, cudaGetLastError());
     const __nv_bfloat16 *in[3] = {m->xb, m->h1, m->h2};
     const __nv_bfloat16 *w[3] = {m->w1b, m->w2b, m->w3b};
     __nv_bfloat16 *hout[3] = {m->h1, m->h2, m->h3};
+    __nv_bfloat16 *hT[3] = {m->h1T, m->h2T, m->h3T};
     float *z[3] = {m->z1, m->z2, m->z3};
     const int kdim[3] = {kInPad, kHid, kHid};
     const int boff[3] = {kOffB1, kOffB2, kOffB3};
     for (int l = 0; l < 3; ++l) {
-        TcGemm g = gemm(in[l], kdim[l], 1, 0, w[l], kdim[l], 1, 0, B, kHid, kdim[l], z[l], kHid, m->status);
+        TcGemm g = gemm(in[l], kdim[l], w[l], kdim[l], B, kHid, kdim[l], z[l], kHid, m->status);
         g.epilogue = TC_BIAS_GELU;
         g.bias = m->master + boff[l];
         g.aux_out = hout[l];
         g.ldaux = kHid;
+        if (train) { g.aux_out_t = hT[l]; g.ldaux_t = m->ldt; }
         MLP_CUDA(m, tc_gemm(g, s));
     }
-    TcGemm g = gemm(m->h3, kHid, 1, 0, m->w4b, kHid, 1, 0, B, kOutPad, kHid, m->y, kOutPad, m->status);
+    TcGemm g = gemm(m->h3, kHid, m->w4b, kHid, B, kOutPad, kHid, m->y, kOutPad, m->status);
     g.epilogue = TC_BIAS;
     g.bias = m->b4pad;
     MLP_CUDA(m, tc_gemm(g, s));
     return SPH_OK;
 }
 
-sph_status mlp_backward(sph_mlp *m, const float *d_t, int B)
+// Backward pass: loss, dY, the dZ chain and the weight-gradient K slices; `src` and `nblk`
+// say where the gradient gather finds them.
+sph_status mlp_backward(sph_mlp *m, const float *d_t, int B, GradSrc &src, int &nblk)
 {
     cudaStream_t s = m->stream;
     const float *ymean = m->norm + 2 * kIn, *yinv = m->norm + 2 * kIn + 2 * kOut;
-    k_loss_grad<<<1, 1024, 0, s>>>(m->y, d_t, B, ymean, yinv, m->dyf, m->dyb, m->loss);
+    const int lt = m->ldt;
+    nblk = (B * kOutPad + kLossThreads - 1) / kLossThreads;
+    k_loss_grad<<<nblk, kLossThreads, 0, s>>>(m->y, d_t, B, ymean, yinv, m->dyb, m->dybT, lt, m->loss_part,
+                                              m->db4_part);
     MLP_CUDA(m, cudaGetLastError());
-    // layer 4: dW4^T = H3^T dY (rows = 128 inputs, K = batch); db4 = colsum(dY)
-    MLP_CUDA(m, tc_gemm(gemm(m->h3, kHid, 0, 0, m->dyb, kOutPad, 0, 0, kHid, kOutPad, B, m->dW4t, kOutPad,
-                             m->status), s));
-    k_colsum<<<1, 32, 0, s>>>(m->dyf, B, kOutPad, kOutPad, m->db4);
-    // dZ3 = (dY W4) * gelu'(Z3)
-    {
-        TcGemm g = gemm(m->dyb, kOutPad, 1, 0, m->w4b, kHid, 0, 0, B, kHid, kOutPad, m->dz3f, kHid, m->status);
-        g.epilogue = TC_GELU_GRAD; g.aux_in = m->z3; g.aux_out = m->dz3; g.ldaux = kHid;
-        MLP_CUDA(m, tc_gemm(g, s));
-    }
-    // layers 3 and 2: dW = dZ^T H_prev, db = colsum(dZ), dZ_prev = (dZ W) * gelu'(Z_prev)
-    struct L { __nv_bfloat16 *dz; float *dzf; const __nv_bfloat16 *hprev; __nv_bfloat16 *w; float *dW, *db;
-               float *zprev; __nv_bfloat16 *dzprev; float *dzprevf; };
-    L layers[2] = {{m->dz3, m->dz3f, m->h2, m->w3b, m->dW3, m->db3, m->z2, m->dz2, m->dz2f},
-                   {m->dz2, m->dz2f, m->h1, m->w2b, m->dW2, m->db2, m->z1, m->dz1, m->dz1f}};
-    for (const L &l : layers) {
-        MLP_CUDA(m, tc_gemm(gemm(l.dz, kHid, 0, 0, l.hprev, kHid, 0, 0, kHid, kHid, B, l.dW, kHid, m->status), s));
-        k_colsum<<<1, kHid, 0, s>>>(l.dzf, B, kHid, kHid, l.db);
-        TcGemm g = gemm(l.dz, kHid, 1, 0, l.w, kHid, 0, 0, B, kHid, kHid, l.dzprevf, kHid, m->status);
-        g.epilogue = TC_GELU_GRAD; g.aux_in = l.zprev; g.aux_out = l.dzprev; g.ldaux = kHid;
-        MLP_CUDA(m, tc_gemm(g, s));
-    }
-    // layer 1: dW1 = dZ1^T Xb (N = 272 -> two column tiles), db1
-    MLP_CUDA(m, tc_gemm(gemm(m->dz1, kHid, 0, 0, m->xb, kInPad, 0, 0, kHid, kInPad, B, m->dW1, kInPad,
-                             m->status), s));
-    k_colsum<<<1, kHid, 0, s>>>(m->dz1f, B, kHid, kHid, m->db1);
-    k_gather_grads<<<(kParams + 255) / 256, 256, 0, s>>>(m->dW1, m->db1, m->dW2, m->db2, m->dW3, m->db3,
-                                                         m->dW4t, m->db4, m->grad);
-    MLP_CUDA(m, cudaGetLastError());
+    // weight gradients contract over the batch: K = B, split into `slices` batch ranges
+    const int slices = std::min(kSplit, (B + kTcKChunk - 1) / kTcKChunk);
+    auto wgrad = [&](const __nv_bfloat16 *AT, int M, const __nv_bfloat16 *BT, int N, float *dW) {
+        TcGemm g = gemm(AT, lt, BT, lt, M, N, B, dW, N, m->status);
+        g.ksplit = slices;
+        g.split_stride = (size_t)M * N;
+        return tc_gemm(g, s);
+    };
+    // dZ = (dZ_next W) * gelu'(Z): BF16 row-major and column-major, and the column sums of
+    // the unrounded dZ per 128-row tile (the bias gradient's partials)
+    auto dzgemm = [&](const __nv_bfloat16 *dn, int kn, const __nv_bfloat16 *wt, const float *z,
+                      __nv_bfloat16 *dz, __nv_bfloat16 *dzT, float *db_part) {
+        TcGemm g = gemm(dn, kn, wt, kn, B, kHid, kn, nullptr, kHid, m->status);
+        g.epilogue = TC_GELU_GRAD; g.aux_in = z; g.aux_out = dz; g.ldaux = kHid;
+        g.aux_out_t = dzT; g.ldaux_t = lt;
+        g.colsum = db_part; g.ld_colsum = kHid;
+        return tc_gemm(g, s);
+    };
+    // layer 4: dW4^T = H3^T dY (rows = 128 inputs, K = batch)
+    MLP_CUDA(m, wgrad(m->h3T, kHid, m->dybT, kOutPad, m->dW4t));
+    // dZ3 = (dY W4) * gelu'(Z3): B operand W4^T [128][16]
+    MLP_CUDA(m, dzgemm(m->dyb, kOutPad, m->w4t, m->z3, m->dz3, m->dz3T, m->db3_part));
+    // layers 3 and 2: dW = dZ^T H_prev, dZ_prev = (dZ W) * gelu'(Z_prev)
+    MLP_CUDA(m, wgrad(m->dz3T, kHid, m->h2T, kHid, m->dW3));
+    MLP_CUDA(m, dzgemm(m->dz3, kHid, m->w3t, m->z2, m->dz2, m->dz2T, m->db2_part));
+    MLP_CUDA(m, wgrad(m->dz2T, kHid, m->h1T, kHid, m->dW2));
+    MLP_CUDA(m, dzgemm(m->dz2, kHid, m->w2t, m->z1, m->dz1, m->dz1T, m->db1_part));
+    // layer 1: dW1 = dZ1^T Xb (N = 272)
+    MLP_CUDA(m, wgrad(m->dz1T, kHid, m->xbT, kInPad, m->dW1));
+    src = GradSrc{m->dW1, m->dW2, m->dW3, m->dW4t, slices,
+                  m->db1_part, m->db2_part, m->db3_part, (B + kTcM - 1) / kTcM, m->db4_part, nblk};
     return SPH_OK;
 }
 
@@ -543,15 +680,19 @@ sph_status sph_mlp_create(void *d_workspace, size_t bytes, void *cuda_stream, in
     m->w1b = h(); m->w2b = h(); m->w3b = h(); m->w4b = h(); m->b4pad = f();
     m->xb = h(); m->h1 = h(); m->h2 = h(); m->h3 = h(); m->dyb = h();
     m->dz3 = h(); m->dz2 = h(); m->dz1 = h();
-    m->z1 = f(); m->z2 = f(); m->z3 = f(); m->y = f(); m->dyf = f();
-    m->dz3f = f(); m->dz2f = f(); m->dz1f = f(); m->out = f();
+    m->z1 = f(); m->z2 = f(); m->z3 = f(); m->y = f(); m->out = f();
     m->dW1 = f(); m->dW2 = f(); m->dW3 = f(); m->dW4t = f();
-    m->db1 = f(); m->db2 = f(); m->db3 = f(); m->db4 = f();
     m->loss = reinterpret_cast<double *>(ws + L.off[i++]);
+    m->loss_part = reinterpret_cast<double *>(ws + L.off[i++]);
+    m->db4_part = f(); m->db3_part = f(); m->db2_part = f(); m->db1_part = f();
     m->status = reinterpret_cast<unsigned *>(ws + L.off[i++]);
     m->anchor = f(); m->tick_x = f();
     m->anchor_w = reinterpret_cast<double *>(ws + L.off[i++]);
     m->tick_w = reinterpret_cast<double *>(ws + L.off[i++]);
+    m->w2t = h(); m->w3t = h(); m->w4t = h();
+    m->xbT = h(); m->h1T = h(); m->h2T = h(); m->h3T = h(); m->dybT = h();
+    m->dz3T = h(); m->dz2T = h(); m->dz1T = h();
+    m->ldt = ldt_of(max_batch);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.total, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e == cudaSuccess) e = cudaHostAlloc(&m->pin, 8 * kOut, cudaHostAllocDefault);
@@ -584,7 +725,8 @@ sph_status sph_mlp_set_params(sph_mlp *m, const float *h_params, const float *h_
     MLP_CUDA(m, cudaMemsetAsync(m->v, 0, 4 * (size_t)kParams, m->stream));
     m->adam_t = 0;
     k_refresh_bf16<<<(kHid * kInPad + 255) / 256, 256, 0, m->stream>>>(m->master, m->w1b, m->w2b, m->w3b,
-                                                                       m->w4b, m->b4pad);
+                                                                       m->w4b, m->b4pad, m->w2t, m->w3t,
+                                                                       m->w4t);
     MLP_CUDA(m, cudaGetLastError());
     MLP_CUDA(m, cudaStreamSynchronize(m->stream));
     return SPH_OK;
@@ -600,7 +742,7 @@ sph_status sph_mlp_get_params(sph_mlp *m, float *h_params)
 sph_status sph_mlp_forward(sph_mlp *m, const float *d_x, int32_t batch, float *d_y)
 {
     if (!m || !d_x || !d_y || batch < 1 || batch > m->max_batch) return SPH_ERR_ARG;
-    sph_status st = mlp_forward(m, d_x, batch);
+    sph_status st = mlp_forward(m, d_x, batch, false);
     if (st != SPH_OK) return st;
     const float *ymean = m->norm + 2 * kIn, *ystd = m->norm + 2 * kIn + kOut;
     k_output<<<(batch * kOut + 255) / 256, 256, 0, m->stream>>>(m->y, batch, ymean, ystd, d_y);
@@ -612,9 +754,13 @@ sph_status sph_mlp_gradients(sph_mlp *m, const float *d_x, const float *d_t, int
                              double *h_loss)
 {
     if (!m || !d_x || !d_t || batch < 1 || batch > m->max_batch) return SPH_ERR_ARG;
-    sph_status st = mlp_forward(m, d_x, batch);
-    if (st == SPH_OK) st = mlp_backward(m, d_t, batch);
+    GradSrc src;
+    int nblk = 0;
+    sph_status st = mlp_forward(m, d_x, batch, true);
+    if (st == SPH_OK) st = mlp_backward(m, d_t, batch, src, nblk);
     if (st != SPH_OK) return st;
+    k_gather_grads<<<(kParams + 255) / 256, 256, 0, m->stream>>>(src, m->grad, m->loss_part, nblk, batch, m->loss);
+    MLP_CUDA(m, cudaGetLastError());
     if (h_grad)
         MLP_CUDA(m, cudaMemcpyAsync(h_grad, m->grad, 4 * (size_t)kParams, cudaMemcpyDeviceToHost, m->stream));
     if (h_loss) MLP_CUDA(m, cudaMemcpyAsync(h_loss, m->loss, 8, cudaMemcpyDeviceToHost, m->stream));
@@ -625,17 +771,19 @@ sph_status sph_mlp_train_step(sph_mlp *m, const float *d_x, const float *d_t, in
                               double *h_loss)
 {
     if (!m || !d_x || !d_t || batch < 1 || batch > m->max_batch || !(lr > 0.0f)) return SPH_ERR_ARG;
-    sph_status st = mlp_forward(m, d_x, batch);
-    if (st == SPH_OK) st = mlp_backward(m, d_t, batch);
+    GradSrc src;
+    int nblk = 0;
+    sph_status st = mlp_forward(m, d_x, batch, true);
+    if (st == SPH_OK) st = mlp_backward(m, d_t, batch, src, nblk);
     if (st != SPH_OK) return st;
     m->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f / (1.0f - std::pow(b1, (float)m->adam_t));
     const float c2 = 1.0f / (1.0f - std::pow(b2, (float)m->adam_t));
-    k_adam<<<(kParams + 255) / 256, 256, 0, m->stream>>>(m->master, m->m, m->v, m->grad, kParams, lr, b1, b2,
-                                                         1e-8f, c1, c2);
-    k_refresh_bf16<<<(kHid * kInPad + 255) / 256, 256, 0, m->stream>>>(m->master, m->w1b, m->w2b, m->w3b,
-                                                                       m->w4b, m->b4pad);
+    const Images im{m->w1b, m->w2b, m->w3b, m->w4b, m->w2t, m->w3t, m->w4t, m->b4pad};
+    k_train_update<<<(kParams + 255) / 256, 256, 0, m->stream>>>(src, m->master, m->m, m->v, m->grad, lr, b1, b2,
+                                                                 1e-8f, c1, c2, im, m->loss_part, nblk, batch,
+                                                                 m->loss);
     MLP_CUDA(m, cudaGetLastError());
     if (h_loss) {
         MLP_CUDA(m, cudaMemcpyAsync(h_loss, m->loss, 8, cudaMemcpyDeviceToHost, m->stream));
@@ -732,7 +880,7 @@ sph_status sph_surrogate_tick(sph_mlp *m, const float pose_vel[13], float elapse
     k_sur_tick_features<<<1, 32, 0, m->stream>>>(t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9],
                                                  t[10], t[11], t[12], elapsed, m->anchor, m->scale, m->tick_x);
     MLP_CUDA(m, cudaGetLastError());
-    sph_status st = mlp_forward(m, m->tick_x, 1);
+    sph_status st = mlp_forward(m, m->tick_x, 1, false);
     if (st != SPH_OK) return st;
     const float *ymean = m->norm + 2 * kIn, *ystd = m->norm + 2 * kIn + kOut;
     k_sur_tick_output<<<1, 32, 0, m->stream>>>(m->y, ymean, ystd, m->anchor, m->anchor_w, m->scale, m->tick_w);

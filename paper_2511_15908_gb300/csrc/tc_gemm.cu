@@ -1,4 +1,7 @@
-// tc_gemm.cu -- tcgen05 BF16 GEMM with fused epilogues (see tc_gemm.cuh for the layout).
+// tc_gemm.cu -- tcgen05 BF16 GEMM fed by TMA through an mbarrier ring, with fused
+// epilogues (see tc_gemm.cuh for the roles and the layout).
+#include <cuda.h>
+
 #include "sph_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -6,27 +9,31 @@ namespace sphgb {
 
 namespace {
 
-constexpr int kABytes = kTcM * kTcKChunk * 2;          // 16 KB
-constexpr int kBBytes = kTcMaxN * kTcKChunk * 2;       // 32 KB
-// The tile uses 48 KB; the launch reserves a larger window so that every address an
-// operand descriptor can form stays inside this CTA's shared memory.
-constexpr int kSmemBytes = 160 * 1024;
+constexpr int kStageA = kTcM * kTcKChunk * 2;          // 16 KB: 128 rows x 128 B
+constexpr int kStageB = kTcMaxN * kTcKChunk * 2;       // 32 KB: up to 256 rows x 128 B
+constexpr int kStageBytes = kStageA + kStageB;
+// the ring, 1 KB of slack to align it to the 1024-byte swizzle period, and the barriers
+constexpr int kSmemBytes = kTcStages * kStageBytes + 1024 + 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory matrix descriptor, canonical K-major layout without swizzle:
-// start address, LBO (core-matrix stride along K) and SBO (stride between 8-row groups),
-// all in 16-byte units; descriptor version 1; layout type 0 (no swizzle).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+// Shared-memory matrix descriptor of a K-major operand written by TMA with the 128-byte
+// swizzle: rows of 128 bytes (64 BF16 of K), 8-row groups 1024 bytes apart (SBO); the
+// leading-byte offset is unused for a swizzled K-major operand whose K step stays inside
+// one 128-byte row (encoded as 1); descriptor version 1 (bit 46); swizzle mode 2 = 128 B.
+// The K = 16 steps inside a chunk advance the start address by 32 bytes: the hardware
+// applies the swizzle to the absolute address bits, so the offset composes with it.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
     return d;
 }
 
@@ -45,10 +52,9 @@ __device__ __forceinline__ uint32_t instr_desc(int n)
 __device__ __forceinline__ void mbar_init(uint32_t addr)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(addr));
-    asm volatile("fence.mbarrier_init.release.cluster;");
 }
 
-// Bounded wait for the given phase parity; false when it gave up.
+// Bounded wait for the completion of the phase with the given parity; false when it gave up.
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
 {
     for (unsigned it = 0; it < kTcSpin; ++it) {
@@ -64,87 +70,60 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ float load_elem(const void *p, int f32, size_t idx)
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes)
 {
-    if (f32) return __ldg(reinterpret_cast<const float *>(p) + idx);
-    return __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[idx]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
 }
 
-// Canonical K-major offset (bytes) of element (r, k) inside a [rows x 64] chunk.
-__device__ __forceinline__ uint32_t kmajor_off(int r, int k)
+// 2-D tiled TMA load of the box at (x = k, y = row) into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
 {
-    return (uint32_t)((((r >> 3) * (kTcKChunk / 8) + (k >> 3)) * 128) + (r & 7) * 16 + (k & 7) * 2);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
 }
 
-// Load rows [r0, r0 + rows) x K-chunk [k0, k0 + 64) of an operand into shared memory.
-// A K-contiguous BF16 operand whose rows start on 16-byte boundaries moves 8 elements (one
-// core-matrix row) per 16-byte load, and rows past the operand's end are zero-filled
-// without a load; other operands go element by element.  Both write the same bytes.
-__device__ __forceinline__ void load_chunk(unsigned char *dst, const void *src, int ld, int kcontig,
-                                           int f32, int r0, int rows, int nrows, int k0, int K)
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
 {
-    if (kcontig && !f32 && (ld & 7) == 0 && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-        const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(src);
-        constexpr int kGroups = kTcKChunk / 8;
-        for (int idx = threadIdx.x; idx < rows * kGroups; idx += kTcThreads) {
-            const int r = idx / kGroups, k = (idx % kGroups) * 8;
-            const int gr = r0 + r, gk = k0 + k;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gr < nrows && gk < K) {
-                const __nv_bfloat16 *row = b + (size_t)gr * ld + gk;
-                if (gk + 8 <= K) {
-                    v = __ldg(reinterpret_cast<const uint4 *>(row));
-                } else {
-                    __align__(16) __nv_bfloat16 e[8];
-                    for (int j = 0; j < 8; ++j) e[j] = gk + j < K ? row[j] : __float2bfloat16_rn(0.0f);
-                    v = *reinterpret_cast<const uint4 *>(e);
-                }
-            }
-            *reinterpret_cast<uint4 *>(dst + kmajor_off(r, k)) = v;
-        }
-        return;
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// The fused per-element operation of one accumulator value at (row, col); returns the value
+// the transposed copy (if any) receives.
+__device__ __forceinline__ float epilogue_value(int ep, float acc, float bias, float zin, float &c_out)
+{
+    switch (ep) {
+    case TC_BIAS_GELU: {
+        const float z = acc + bias;
+        c_out = z;
+        return gelu_f(z);
     }
-    if (!kcontig && !f32 && (ld & 7) == 0 && (r0 & 7) == 0 && (rows & 7) == 0 &&
-        (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-        // row-contiguous BF16: 8 rows of one k per 16-byte load, scattered into 8 core-matrix rows
-        const __nv_bfloat16 *b = reinterpret_cast<const __nv_bfloat16 *>(src);
-        const int groups = rows / 8;
-        for (int idx = threadIdx.x; idx < groups * kTcKChunk; idx += kTcThreads) {
-            const int r = (idx % groups) * 8, k = idx / groups;
-            const int gr = r0 + r, gk = k0 + k;
-            __align__(16) __nv_bfloat16 e[8];
-            if (gk < K && gr + 8 <= nrows) {
-                *reinterpret_cast<uint4 *>(e) = __ldg(reinterpret_cast<const uint4 *>(b + (size_t)gk * ld + gr));
-            } else {
-                for (int j = 0; j < 8; ++j)
-                    e[j] = (gk < K && gr + j < nrows) ? b[(size_t)gk * ld + gr + j] : __float2bfloat16_rn(0.0f);
-            }
-            for (int j = 0; j < 8; ++j)
-                *reinterpret_cast<__nv_bfloat16 *>(dst + kmajor_off(r + j, k)) = e[j];
-        }
-        return;
+    case TC_GELU_GRAD: {
+        const float gz = acc * gelu_grad_f(zin);
+        c_out = gz;
+        return gz;
     }
-    const int total = rows * kTcKChunk;
-    for (int idx = threadIdx.x; idx < total; idx += kTcThreads) {
-        int r, k;
-        if (kcontig) { r = idx / kTcKChunk; k = idx % kTcKChunk; }
-        else { k = idx / rows; r = idx % rows; }
-        const int gr = r0 + r, gk = k0 + k;
-        float v = 0.0f;
-        if (gr < nrows && gk < K)
-            v = load_elem(src, f32, kcontig ? (size_t)gr * ld + gk : (size_t)gk * ld + gr);
-        *reinterpret_cast<__nv_bfloat16 *>(dst + kmajor_off(r, k)) = __float2bfloat16_rn(v);
+    case TC_BIAS: c_out = acc + bias; return 0.0f;
+    default: c_out = acc; return 0.0f;
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(TcGemm g, int ntile)
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcGemm g,
+              int ntile, int box_b, int chunks_per_split)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sA = smem;
-    unsigned char *sB = smem + kABytes;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kABytes + kBBytes);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + kABytes + kBBytes + 16);
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
+    __shared__ float s_cs[kTcThreads / 32][16];
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const uint32_t bar = base + kTcStages * kStageBytes;   // full[S], empty[S], done
+    auto full = [&](int s) { return bar + 8u * (uint32_t)s; };
+    auto empty = [&](int s) { return bar + 8u * (uint32_t)(kTcStages + s); };
+    const uint32_t done = bar + 16u * kTcStages;
 
     const int m0 = blockIdx.x * kTcM;
     const int n0 = blockIdx.y * ntile;
@@ -153,58 +132,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(TcGemm g, int ntile)
     int ncols = 32;
     while (ncols < nt) ncols <<= 1;                  // TMEM allocation: power of two >= 32
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (g.K + kTcKChunk - 1) / kTcKChunk;
+    const int kc0 = blockIdx.z * chunks_per_split;
+    const int kc1 = min(nk, kc0 + chunks_per_split);
+    const int row = m0 + warp * 32 + lane;
+    float *C = g.C ? g.C + (size_t)blockIdx.z * g.split_stride : nullptr;
+
+    if (kc0 >= kc1) {
+        // an empty K slice (more slices than chunks): its partial sum is zero
+        if (C && row < g.M)
+            for (int j = 0; j < nt_raw; ++j) C[(size_t)row * g.ldc + n0 + j] = 0.0f;
+        return;
+    }
 
     if (threadIdx.x == 0) {
         s_fail = 0;
-        mbar_init(smem_u32(mbar));
+        for (int s = 0; s < 2 * kTcStages + 1; ++s) mbar_init(bar + 8u * (uint32_t)s);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"(ncols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = *tslot;
-    const uint32_t idesc = instr_desc(nt);
+    const uint32_t tmem = s_tmem;
 
-    uint32_t phase = 0;
-    const int nk = (g.K + kTcKChunk - 1) / kTcKChunk;
-    for (int kc = 0; kc < nk; ++kc) {
-        const int k0 = kc * kTcKChunk;
-        load_chunk(sA, g.A, g.lda, g.a_kcontig, g.a_f32, m0, kTcM, g.M, k0, g.K);
-        load_chunk(sB, g.B, g.ldb, g.b_kcontig, g.b_f32, n0, nt, g.N, k0, g.K);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
+        // producer: chunk i goes to stage i % S once the MMAs of chunk i - S have read it
+        const uint32_t tx = (uint32_t)(kTcM + box_b) * kTcKChunk * 2;
+        for (int kc = kc0, i = 0; kc < kc1; ++kc, ++i) {
+            const int s = i % kTcStages;
+            if (i >= kTcStages && !mbar_wait(empty(s), ((i / kTcStages) & 1) ^ 1)) {
+                s_fail = 1;
+                break;
+            }
+            const uint32_t sa = base + (uint32_t)s * kStageBytes;
+            mbar_expect_tx(full(s), tx);
+            tma_load_2d(sa, &tmA, kc * kTcKChunk, m0, full(s));
+            tma_load_2d(sa + kStageA, &tmB, kc * kTcKChunk, n0, full(s));
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer: four K = 16 steps per chunk into the TMEM accumulator
+        const uint32_t idesc = instr_desc(nt);
+        for (int kc = kc0, i = 0; kc < kc1; ++kc, ++i) {
+            const int s = i % kTcStages;
+            if (!mbar_wait(full(s), (i / kTcStages) & 1)) {
+                s_fail = 1;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int ksteps = min(kTcKChunk, ((g.K - k0) + 15) & ~15) / 16;
-            for (int j = 0; j < ksteps; ++j) {
-                const uint64_t ad = smem_desc(smem_u32(sA) + j * 256, 128, 1024);
-                const uint64_t bd = smem_desc(smem_u32(sB) + j * 256, 128, 1024);
-                const uint32_t acc = (kc > 0 || j > 0) ? 1u : 0u;
+            const uint32_t sa = base + (uint32_t)s * kStageBytes, sb = sa + kStageA;
+#pragma unroll
+            for (int j = 0; j < kTcKChunk / 16; ++j) {
+                const uint64_t ad = smem_desc_sw128(sa + 32u * (uint32_t)j);
+                const uint64_t bd = smem_desc_sw128(sb + 32u * (uint32_t)j);
+                const uint32_t acc = (i > 0 || j > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
                     "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(mbar)));
+            mma_commit(empty(s));
         }
-        if (!mbar_wait(smem_u32(mbar), phase)) {
-            s_fail = 1;
-            if (g.status) atomicOr(g.status, (unsigned)ST_TIMEOUT);
-        }
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-        if (s_fail) break;
+        mma_commit(done);                            // fires once every issued MMA completed
     }
-
-    if (!s_fail) {
+    __syncwarp();
+    if (!mbar_wait(done, 0)) s_fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0 && g.status) atomicOr(g.status, (unsigned)ST_TIMEOUT);
+    } else {
         // epilogue: thread = tile row (TMEM lane 32 warp + lane), 16 columns per load
-        const int row = m0 + warp * 32 + lane;
+        const int ep = g.epilogue;
+        const bool vec_c = C && (g.ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15u) == 0;
+        const bool vec_aux = (g.ldaux & 7) == 0 && (reinterpret_cast<uintptr_t>(g.aux_out) & 15u) == 0 &&
+                             (reinterpret_cast<uintptr_t>(g.aux_in) & 15u) == 0 && (g.ldaux & 3) == 0;
         for (int c0 = 0; c0 < nt; c0 += 16) {
             uint32_t r[16];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
@@ -216,29 +222,87 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(TcGemm g, int ntile)
                   "=r"(r[14]), "=r"(r[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < g.M) {
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col >= g.N || c0 + j >= nt_raw) break;
-                    float acc = __uint_as_float(r[j]);
-                    switch (g.epilogue) {
-                    case TC_BIAS_GELU: {
-                        float z = acc + g.bias[col];
-                        g.C[(size_t)row * g.ldc + col] = z;
-                        g.aux_out[(size_t)row * g.ldaux + col] = __float2bfloat16_rn(gelu_f(z));
-                        break;
+            float cv[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) cv[j] = 0.0f;
+            if (row < g.M && c0 < nt_raw) {
+            const int col0 = n0 + c0;
+            const bool whole = c0 + 16 <= nt_raw;
+            float zin[16], hv[16];
+            if (ep == TC_GELU_GRAD) {
+                const float *zp = g.aux_in + (size_t)row * g.ldaux + col0;
+                if (whole && vec_aux) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(zp) + q);
+                        zin[4 * q] = v.x; zin[4 * q + 1] = v.y; zin[4 * q + 2] = v.z; zin[4 * q + 3] = v.w;
                     }
-                    case TC_GELU_GRAD: {
-                        float z = g.aux_in[(size_t)row * g.ldaux + col];
-                        float gz = acc * gelu_grad_f(z);
-                        if (g.C) g.C[(size_t)row * g.ldc + col] = gz;
-                        g.aux_out[(size_t)row * g.ldaux + col] = __float2bfloat16_rn(gz);
-                        break;
-                    }
-                    case TC_BIAS: g.C[(size_t)row * g.ldc + col] = acc + g.bias[col]; break;
-                    default: g.C[(size_t)row * g.ldc + col] = acc; break;
-                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) zin[j] = c0 + j < nt_raw ? zp[j] : 0.0f;
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float b = (ep == TC_BIAS_GELU || ep == TC_BIAS) && c0 + j < nt_raw ? __ldg(g.bias + col0 + j)
+                                                                                         : 0.0f;
+                hv[j] = epilogue_value(ep, __uint_as_float(r[j]), b, ep == TC_GELU_GRAD ? zin[j] : 0.0f, cv[j]);
+            }
+            if (C) {
+                float *cp = C + (size_t)row * g.ldc + col0;
+                if (whole && vec_c) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        reinterpret_cast<float4 *>(cp)[q] =
+                            make_float4(cv[4 * q], cv[4 * q + 1], cv[4 * q + 2], cv[4 * q + 3]);
+                } else {
+                    for (int j = 0; j < 16 && c0 + j < nt_raw; ++j) cp[j] = cv[j];
+                }
+            }
+            if (ep == TC_BIAS_GELU || ep == TC_GELU_GRAD) {
+                __nv_bfloat16 *hp = g.aux_out + (size_t)row * g.ldaux + col0;
+                __align__(16) __nv_bfloat16 hb[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) hb[j] = __float2bfloat16_rn(hv[j]);
+                if (whole && vec_aux) {
+                    reinterpret_cast<uint4 *>(hp)[0] = reinterpret_cast<const uint4 *>(hb)[0];
+                    reinterpret_cast<uint4 *>(hp)[1] = reinterpret_cast<const uint4 *>(hb)[1];
+                } else {
+                    for (int j = 0; j < 16 && c0 + j < nt_raw; ++j) hp[j] = hb[j];
+                }
+                if (g.aux_out_t) {
+                    // column-major copy: the lanes of a warp hold consecutive rows
+                    for (int j = 0; j < 16 && c0 + j < nt_raw; ++j)
+                        g.aux_out_t[(size_t)(col0 + j) * g.ldaux_t + row] = hb[j];
+                }
+            }
+            }
+            if (g.colsum && c0 < nt_raw) {
+                // the 16 column sums of the warp by a halving exchange: after the xor-16, -8,
+                // -4 and -2 steps each lane pair holds one column (lane bits 4..1 pick it)
+                const unsigned full = 0xffffffffu;
+                float v8[8], v4[4], v2[2];
+                const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    v8[k] = (h16 ? cv[k + 8] : cv[k]) + __shfl_xor_sync(full, h16 ? cv[k] : cv[k + 8], 16);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    v4[k] = (h8 ? v8[k + 4] : v8[k]) + __shfl_xor_sync(full, h8 ? v8[k] : v8[k + 4], 8);
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    v2[k] = (h4 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(full, h4 ? v4[k] : v4[k + 2], 4);
+                float v1 = (h2 ? v2[1] : v2[0]) + __shfl_xor_sync(full, h2 ? v2[0] : v2[1], 2);
+                v1 += __shfl_xor_sync(full, v1, 1);
+                const int col = (h16 ? 8 : 0) + (h8 ? 4 : 0) + (h4 ? 2 : 0) + (h2 ? 1 : 0);
+                if ((lane & 1) == 0) s_cs[warp][col] = v1;
+                __syncthreads();
+                if (threadIdx.x < 16 && c0 + (int)threadIdx.x < nt_raw) {
+                    float t = 0.0f;
+                    for (int w = 0; w < kTcThreads / 32; ++w) t += s_cs[w][threadIdx.x];
+                    g.colsum[(size_t)blockIdx.x * g.ld_colsum + n0 + c0 + threadIdx.x] = t;
+                }
+                __syncthreads();
             }
         }
     }
@@ -250,7 +314,68 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_gemm(TcGemm g, int ntile)
     }
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of a K-contiguous BF16 operand [rows][K] (leading dimension ld elements): boxes
+// of 64 K x box_rows rows with the 128-byte swizzle; out-of-range elements read as zero.
+bool operand_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K, int ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2u};
+    const cuuint32_t box[2] = {(cuuint32_t)kTcKChunk, (cuuint32_t)box_rows};
+    const cuuint32_t estride[2] = {1u, 1u};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(p), dims, strides, box, estride,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Columns per CTA tile: the widest of 256, 128, ..., 16 that still gives at least
+// kTcMinCtas CTAs (row tiles x column tiles x K slices).  These GEMMs are small: a CTA's
+// epilogue (one thread per row, one warp per SM sub-partition) is latency bound, so more,
+// narrower tiles finish sooner than few wide ones; A is re-read from L2 per column tile.
+int ntile_of(const TcGemm &g, int slices)
+{
+    const int mt = (g.M + kTcM - 1) / kTcM;
+    int nt = kTcMaxN;
+    while (nt > 16 && mt * ((g.N + nt - 1) / nt) * slices < kTcMinCtas) nt >>= 1;
+    return nt;
+}
+
+// (slices, chunks per slice) of the K split
+void split_of(const TcGemm &g, int &slices, int &cps)
+{
+    const int nk = (g.K + kTcKChunk - 1) / kTcKChunk;
+    const int want = (g.ksplit > 1 && g.epilogue == TC_STORE) ? g.ksplit : 1;
+    cps = (nk + want - 1) / want;
+    slices = want;
+}
+
 }  // namespace
+
+int tc_gemm_splits(const TcGemm &g)
+{
+    int slices, cps;
+    split_of(g, slices, cps);
+    return slices;
+}
 
 cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s)
 {
@@ -261,11 +386,18 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s)
         configured = true;
     }
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
-    // A single row tile (small batches, e.g. one haptic tick) spreads its columns over
-    // CTAs of 32, so that B is loaded by several SMs at once; larger M keeps wide tiles.
-    const int ntile = g.M <= kTcM ? kTcSmallN : kTcMaxN;
-    dim3 grid((g.M + kTcM - 1) / kTcM, (g.N + ntile - 1) / ntile);
-    k_tc_gemm<<<grid, kTcThreads, kSmemBytes, s>>>(g, ntile);
+    if (!g.A || !g.B || (g.lda & 7) || (g.ldb & 7) || g.lda < g.K || g.ldb < g.K ||
+        (reinterpret_cast<uintptr_t>(g.A) & 15u) || (reinterpret_cast<uintptr_t>(g.B) & 15u))
+        return cudaErrorInvalidValue;
+    int slices, cps;
+    split_of(g, slices, cps);
+    const int ntile = ntile_of(g, slices);
+    const int box_b = ntile;
+    CUtensorMap ma, mb;
+    if (!operand_map(&ma, g.A, g.M, g.K, g.lda, kTcM) || !operand_map(&mb, g.B, g.N, g.K, g.ldb, box_b))
+        return cudaErrorInvalidValue;
+    dim3 grid((g.M + kTcM - 1) / kTcM, (g.N + ntile - 1) / ntile, slices);
+    k_tc_gemm<<<grid, kTcThreads, kSmemBytes, s>>>(ma, mb, g, ntile, box_b, cps);
     return cudaGetLastError();
 }
 

@@ -1,20 +1,30 @@
-// tc_gemm.cuh -- BF16 tensor-core GEMM on sm_103a (tcgen05 + TMEM), FP32 accumulation.
+// tc_gemm.cuh -- BF16 tensor-core GEMM on sm_103a (tcgen05 + TMEM + TMA), FP32 accumulation.
 //
 //   C[M, N] = A[M, K] * B[N, K]^T      (both operands "row = output index, K = contraction")
 //
-// One CTA of 128 threads computes a 128 x Nt tile (Nt <= 256, multiple of 16; Nt = 32 when
-// M fits one row tile, so that small batches use several SMs).  For every
-// 64-wide K chunk the threads convert their part of A and B to BF16 and write it to shared
-// memory in the canonical no-swizzle K-major layout (8 x 8 core matrices of 128 bytes:
-// rows of a core matrix 16 B apart, core matrices along K 128 B apart = LBO, 8-row groups
-// 1024 B apart = SBO); one elected thread issues four K=16 tcgen05.mma into the TMEM
-// accumulator and commits them to an mbarrier, which every thread waits on with a bounded
-// spin.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31, i.e. tile rows) and applies a fused per-element operation.
+// Both operands are BF16 and K-contiguous in global memory ([row][k], leading dimension a
+// multiple of 8 elements, 16-byte aligned base).  One CTA of 128 threads computes a 128 x Nt
+// tile (Nt = 256, 128, ..., 16: the widest that still gives kTcMinCtas CTAs, so that the
+// small GEMMs of the surrogate spread over many SMs).  The K dimension is walked in 64-wide
+// chunks through a 4-stage shared-memory ring:
+//   - thread 0 (the producer) waits until a stage is free and has the tensor memory
+//     accelerator copy the A and B boxes of the next chunk into it (cp.async.bulk.tensor,
+//     128-byte swizzle, rows past M / N and k past K read as zeros), completing on the
+//     stage's "full" mbarrier;
+//   - thread 32 (the MMA issuer) waits for a full stage, issues four K = 16 tcgen05.mma into
+//     the TMEM accumulator and commits them to the stage's "empty" mbarrier, which frees the
+//     stage for the producer once the tensor core has read it; after the last chunk it
+//     commits to the "done" mbarrier;
+//   - every thread waits for "done" and runs the epilogue: tcgen05.ld of its TMEM lane (= tile
+//     row), the fused per-element operation, and 16-byte stores of 16 consecutive columns
+//     (plus, where asked, a transposed BF16 copy whose stores are coalesced across the warp,
+//     and the column sums of the tile's FP32 results: a fixed shuffle tree within each warp,
+//     then the four warps in order).
+// Every wait is bounded: a wait that gives up latches ST_TIMEOUT in *status and the tile is
+// not written.
 //
-// Operands may be stored K-contiguous ([row][k]) or row-contiguous ([k][row]) in global
-// memory, as BF16 or FP32; the loader transposes/converts, so the tensor core always sees
-// K-major shared-memory operands.
+// A K split (ksplit > 1, TC_STORE only) spreads the chunks over grid.z; CTA z writes its
+// partial sum to C + z * split_stride, and the caller sums the slices in a fixed order.
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
@@ -24,9 +34,10 @@ namespace sphgb {
 
 constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;          // rows per CTA tile (UMMA M)
-constexpr int kTcKChunk = 64;      // K per shared-memory stage
+constexpr int kTcKChunk = 64;      // K per pipeline stage (one 128-byte swizzle row)
 constexpr int kTcMaxN = 256;       // columns per CTA tile (UMMA N <= 256)
-constexpr int kTcSmallN = 32;      // columns per CTA tile when M fits one row tile
+constexpr int kTcMinCtas = 64;     // column tiles narrow (to 16) until a GEMM has this many CTAs
+constexpr int kTcStages = 4;       // shared-memory ring depth
 constexpr unsigned kTcSpin = 1u << 22;
 
 enum TcEpilogue : int {
@@ -37,20 +48,24 @@ enum TcEpilogue : int {
 };
 
 struct TcGemm {
-    const void *A;       // M x K
-    const void *B;       // N x K
-    int lda, ldb;        // leading dimensions in elements
-    int a_kcontig, b_kcontig;   // 1: [row][k] storage, 0: [k][row] storage
-    int a_f32, b_f32;    // 1: FP32 storage (converted to BF16), 0: BF16 storage
-    int M, N, K;         // K multiple of 16 (zero-padded past K by the loader)
+    const __nv_bfloat16 *A;   // M x K, [row][k], leading dimension lda
+    const __nv_bfloat16 *B;   // N x K, [row][k], leading dimension ldb
+    int lda, ldb;        // in elements, multiples of 8
+    int M, N, K;
     float *C;            // M x N FP32 (ldc), may be null for TC_GELU_GRAD
     int ldc;
     const float *bias;   // N (TC_BIAS_GELU, TC_BIAS)
     const float *aux_in; // M x N FP32 pre-activation Z (TC_GELU_GRAD), ld = ldaux
     __nv_bfloat16 *aux_out;  // M x N BF16 (TC_BIAS_GELU, TC_GELU_GRAD), ld = ldaux
     int ldaux;
+    __nv_bfloat16 *aux_out_t;  // optional N x M BF16 transposed copy of aux_out ([col][row])
+    int ldaux_t;
     int epilogue;
-    unsigned *status;    // ST_TIMEOUT latched when the mbarrier wait gives up
+    float *colsum;       // optional: per row tile, the column sums of the FP32 epilogue values
+    int ld_colsum;       // (the values C receives) over the tile's rows: colsum[tile * ld + col]
+    int ksplit;          // >= 1; > 1 only with TC_STORE
+    size_t split_stride; // elements between the partial slices of C
+    unsigned *status;    // ST_TIMEOUT latched when an mbarrier wait gives up
 };
 
 // GELU, tanh form: 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
@@ -67,6 +82,10 @@ __device__ __forceinline__ float gelu_grad_f(float z)
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * c * (1.0f + 3.0f * a * z * z);
 }
 
+// Number of K slices tc_gemm writes for g (1 without a split): the caller sums this many.
+int tc_gemm_splits(const TcGemm &g);
+// cudaErrorInvalidValue when the operands break the layout rules above or the tensor maps
+// cannot be built.
 cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s);
 
 }  // namespace sphgb

@@ -579,11 +579,13 @@ def surrogate_form(args):
     n_cycles = (n - n_train) // cycle
     ev = surrogate.haptic_loop(sim, model, sc.trajectory, n_cycles, cycle, tick, dt)
     lat = surrogate.inference_latency_us(sim, model, sc.trajectory)
+    t_step = surrogate.train_step_ms(model, x, y, batch=1024)     # after the evaluation
     out["stirring_logged"] = {"train_pairs": n_train, "eval_ticks": ev["ticks"], "errors": ev,
                               "evaluated": "live: sph_surrogate_anchor per update cycle, "
                                            "sph_surrogate_tick per 1 kHz tick (held-out substeps "
                                            "after the training ones)",
                               "train_steps": steps, "train_s": t_fit, "log_s": t_log,
+                              "train_step_ms_batch1024": t_step,
                               "first_last_loss": [losses[0][1], losses[-1][1]],
                               "jitter_floor": surrogate.jitter_floor(wr)}
     out["tick_latency_us"] = lat

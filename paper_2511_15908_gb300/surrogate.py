@@ -115,6 +115,29 @@ def fit(model: "sph.Surrogate", x, y, steps: int = 3000, batch: int = 1024, lr: 
     return losses
 
 
+def train_step_ms(model: "sph.Surrogate", x, y, batch: int = 1024, steps: int = 200, seed: int = 0) -> float:
+    """Device time of one training step (forward, backward, Adam) on minibatches of the pairs
+    x, y: CUDA events on the model's stream around `steps` steps after 20 untimed ones.  The
+    steps update the model (callers time a model they are done with, or one they refit)."""
+    import torch
+    g = torch.Generator(device=model.device)
+    g.manual_seed(seed)
+    n = x.shape[0]
+    idx = [torch.randint(0, n, (min(batch, n),), device=model.device, generator=g) for _ in range(8)]
+    xs = [x[i].contiguous() for i in idx]
+    ys = [y[i].contiguous() for i in idx]
+    for k in range(20):
+        model.train_step(xs[k % 8], ys[k % 8], 1e-5)
+    model.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(model.stream)
+    for k in range(steps):
+        model.train_step(xs[k % 8], ys[k % 8], 1e-5)
+    e1.record(model.stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def _rel(p, exact, part):
     sl = slice(0, 3) if part == "force" else slice(3, 6)
     return float(np.sqrt(np.mean(np.sum((p[:, sl] - exact[:, sl]) ** 2, 1)))

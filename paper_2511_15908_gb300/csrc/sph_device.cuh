@@ -837,6 +837,220 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     else density_item_v<false, THREADS>(c, blk, s_pend);
 }
 
+#if SPH_DENSITY_BRICK
+// Alternative density pass, built only with -DSPH_DENSITY_BRICK=1 (and SPH_BRICK_X/Y/Z/CAP):
+// one CTA per brick of kBX x kBY x kBZ cells.  The positions of the brick's cells and of a
+// halo of kBH cells around them are staged in shared memory once (row by row: the slots of
+// a row of cells are contiguous), and every particle of the brick walks its rows against
+// the staged copy; rows outside it, which the FP32 margin of the search can add, are read
+// from global memory.  Same neighbours in the same order as density_item_v, hence the same
+// results bit for bit.  Mass boundaries only (volume boundaries keep density_item_v).
+// Measured against the row walk on the stirred coupled scene and rejected (1.76x slower at
+// best): it executes as many instructions plus the staging, and the bricks' uneven particle
+// counts (h/2 walls, air above the free surface) leave thread slots idle.
+constexpr int kBX = SPH_BRICK_X, kBY = SPH_BRICK_Y, kBZ = SPH_BRICK_Z, kBH = 2;
+constexpr int kSY = kBY + 2 * kBH, kSZ = kBZ + 2 * kBH, kSRows = kSY * kSZ;
+constexpr int kStageCap = SPH_BRICK_CAP;
+constexpr int kBrickThreads = 512;
+
+struct BrickShared {
+    float4 x[kStageCap];
+    int2 pend[kPending * kBrickThreads];
+    int pdel[kPending * kBrickThreads];
+    int row_g[kSRows], row_s[kSRows], row_n[kSRows], row_xs[kSRows], row_xe[kSRows];
+    int inner_pre[kBY * kBZ + 1];
+    int ok;
+};
+
+__device__ __forceinline__ void density_brick(const SimConst &c, BrickShared &sh)
+{
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY, z0 = blockIdx.z * kBZ;
+    const int tid = threadIdx.x;
+    // rows of the staged block: counts, then offsets
+    if (tid < kSRows) {
+        const int zz = z0 - kBH + tid / kSY, yy = y0 - kBH + tid % kSY;
+        int g = 0, n = 0, xs = 0, xe = 0;
+        if (zz >= 0 && zz < c.nz && yy >= 0 && yy < c.ny) {
+            xs = max(x0 - kBH, 0);
+            xe = min(x0 + kBX + kBH, c.nx);
+            const int base = (zz * c.ny + yy) * c.nx;
+            g = (int)__ldg(c.cell_start + base + xs);
+            n = (int)__ldg(c.cell_start + base + xe) - g;
+        }
+        sh.row_g[tid] = g;
+        sh.row_n[tid] = n;
+        sh.row_xs[tid] = xs;
+        sh.row_xe[tid] = xe;
+    }
+    if (tid == 0) {
+        int pre = 0;
+        for (int k = 0; k <= kBY * kBZ; ++k) {
+            sh.inner_pre[k] = pre;
+            if (k == kBY * kBZ) break;
+            const int zz = z0 + k / kBY, yy = y0 + k % kBY;
+            if (zz < c.nz && yy < c.ny && x0 < c.nx) {
+                const int base = (zz * c.ny + yy) * c.nx;
+                pre += (int)__ldg(c.cell_start + base + min(x0 + kBX, c.nx)) - (int)__ldg(c.cell_start + base + x0);
+            }
+        }
+    }
+    __syncthreads();
+    const int n_inner = sh.inner_pre[kBY * kBZ];
+    if (n_inner == 0) return;
+    if (tid == 0) {
+        int off = 0;
+        for (int r = 0; r < kSRows; ++r) {
+            sh.row_s[r] = off;
+            off += sh.row_n[r];
+        }
+        sh.ok = off <= kStageCap;
+    }
+    __syncthreads();
+    const bool ok = sh.ok;
+    if (ok) {
+        // each warp copies whole rows
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int r = warp; r < kSRows; r += kBrickThreads / 32) {
+            const int g = sh.row_g[r], s0 = sh.row_s[r], n = sh.row_n[r];
+            for (int k = lane; k < n; k += 32) sh.x[s0 + k] = __ldg(c.xA + g + k);
+        }
+    }
+    __syncthreads();
+
+    for (int item = tid; item < n_inner; item += kBrickThreads) {
+        // the particle's inner row and slot
+        int ir = 0;
+        while (sh.inner_pre[ir + 1] <= item) ++ir;
+        const int zz = z0 + ir / kBY, yy = y0 + ir % kBY;
+        const int p = (int)__ldg(c.cell_start + (zz * c.ny + yy) * c.nx + x0) + (item - sh.inner_pre[ir]);
+        const float4 xi = c.xA[p];
+        uint32_t bad = 0;
+        int kind = 0, excl_lo = 0, excl_n = 0;
+        if (xi.w < 0.0f) pair_scope(c, __float_as_int(c.vA[p].w), kind, excl_lo, excl_n);
+        const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
+        const float *vw = reinterpret_cast<const float *>(c.vA) + 3;
+        const bool near0 = near_origin_planes(c, xi);
+        PairDensitySum acc;
+        acc.self(fabsf(xi.w));
+        ListWriter list;
+        list.dst = c.nlist4 + p;
+        list.n = (size_t)c.n;
+        list.cap = c.nl_cap;
+        int2 *pend = sh.pend + tid;
+        int *pdel = sh.pdel + tid;
+        int np = 0;
+        constexpr int kGlobal = -2147483647 - 1;
+        auto drain = [&]() {
+            if (np == 0) return;
+            int k = 0;
+            int2 e = pend[0];
+            int d = pdel[0];
+            uint32_t mm = (uint32_t)e.y;
+            for (;;) {
+                if (mm == 0u) {
+                    if (++k == np) break;
+                    e = pend[k * kBrickThreads];
+                    d = pdel[k * kBrickThreads];
+                    mm = (uint32_t)e.y;
+                }
+                const int qs = e.x + __ffs(mm) - 1;
+                mm &= mm - 1u;
+                float4 xj;
+                int q;
+                if (d != kGlobal) { xj = sh.x[qs]; q = qs + d; }
+                else { q = qs; xj = __ldg(c.xA + q); }
+                float dx, dy, dz, r2x;
+                pair_offset(xi, xj, near0, dx, dy, dz, r2x);
+                acc.add(c, fabsf(xj.w), 0.0f, dx, dy, dz, r2x);
+                if (!keep_list) continue;
+                if (excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) < (unsigned)excl_n)
+                    continue;
+                list.push((uint32_t)q);
+            }
+            np = 0;
+        };
+        const float ux = __fmul_rn(__fsub_rn(xi.x, c.o[0]), c.inv_cell);
+        const float uy = __fmul_rn(__fsub_rn(xi.y, c.o[1]), c.inv_cell);
+        const float uz = __fmul_rn(__fsub_rn(xi.z, c.o[2]), c.inv_cell);
+        const float Rc = c.Rc, Rc2 = Rc * Rc, mc = c.mc;
+        const int cy = cell_floor(uy, c.ny), cz = cell_floor(uz, c.nz);
+        const int zl = cell_floor(uz - Rc, c.nz), zh = cell_floor(uz + Rc, c.nz);
+        const int yl = cell_floor(uy - Rc, c.ny), yh = cell_floor(uy + Rc, c.ny);
+#pragma unroll 1
+        for (int z = zl; z <= zh; ++z) {
+            const float gz = cell_gap(uz, z, cz, mc);
+            const float rz2 = Rc2 - gz * gz;
+#pragma unroll 1
+            for (int y = yl; y <= yh; ++y) {
+                const float gy = cell_gap(uy, y, cy, mc);
+                const float w2 = rz2 - gy * gy;
+                if (!(w2 >= 0.0f)) continue;
+                const float w = w2 * rsqrtf(fmaxf(w2, 1e-30f)) + mc;
+                const int xa = cell_floor(ux - w, c.nx), xb = cell_floor(ux + w, c.nx);
+                const int base = (z * c.ny + y) * c.nx;
+                const int s0 = in_range(c, __ldg(c.cell_start + in_range(c, base + xa, c.ncell)), c.n + 1);
+                int e0 = in_range(c, __ldg(c.cell_start + in_range(c, base + xb + 1, c.ncell + 1)), c.n + 1);
+                if (e0 - s0 > kMaxCellRun) { e0 = s0 + kMaxCellRun; bad |= ST_CAPACITY; }
+                // staged row?
+                const int rz = z - (z0 - kBH), ry = y - (y0 - kBH);
+                int d = kGlobal;
+                if (ok && (unsigned)rz < (unsigned)kSZ && (unsigned)ry < (unsigned)kSY) {
+                    const int r = rz * kSY + ry;
+                    if (xa >= sh.row_xs[r] && xb < sh.row_xe[r]) d = sh.row_g[r] - sh.row_s[r];
+                }
+                const int sb = d == kGlobal ? s0 : s0 - d, se = d == kGlobal ? e0 : e0 - d;
+                const int pself = d == kGlobal ? p : p - d;
+#pragma unroll 1
+                for (int b = sb; b < se; b += 32) {
+                    const int end = min(se, b + 32);
+                    uint32_t mm = 0u, bit = 1u;
+                    if (d != kGlobal) {
+#pragma unroll kMaskUnroll
+                        for (int q = b; q < end; ++q) {
+                            const float4 xj = sh.x[q];
+                            float dx, dy, dz;
+                            if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
+                            bit <<= 1;
+                        }
+                    } else {
+#pragma unroll kMaskUnroll
+                        for (int q = b; q < end; ++q) {
+                            const float4 xj = __ldg(c.xA + q);
+                            float dx, dy, dz;
+                            if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
+                            bit <<= 1;
+                        }
+                    }
+                    if ((unsigned)(pself - b) < 32u) mm &= ~(1u << (pself - b));
+                    if (!mm) continue;
+                    if (np == kPending) drain();
+                    pend[np * kBrickThreads] = make_int2(b, (int)mm);
+                    pdel[np * kBrickThreads] = d;
+                    ++np;
+                }
+            }
+            if (np > kDrainAt) drain();
+        }
+        drain();
+        list.flush();
+        c.nlist_n[p] = list.nl;
+        const float drho = acc.excess(c, c.rho0);
+        const float rho = __fadd_rn(c.rho0, drho);
+        float pr;
+        if (c.flags & FLAG_TAIT) {
+            const float x = drho / c.rho0;
+            pr = c.tait_B * (x * (7.0f + x * (21.0f + x * (35.0f + x * (35.0f + x * (21.0f + x * (7.0f + x)))))));
+        } else {
+            pr = c.k * drho;
+        }
+        if ((c.flags & FLAG_CLAMP) && pr < 0.0f) pr = 0.0f;
+        c.prho[p] = make_float2(rho, pr / (rho * rho));
+        if (c.flags & FLAG_RECORD) c.nnbr[p] = acc.cnt - 1;
+        report(c, bad);
+    }
+}
+#endif
+
 // Volume-based boundaries (Akinci et al.): each static or rigid particle's weight
 // psi_b = rho0 / sum_{k boundary} W_bk (self included), stored in its (rho, P) slot as
 // (psi_b, its low part) before the density pass reads it.

@@ -32,6 +32,13 @@ __global__ void __launch_bounds__(SPH_DENSITY_THREADS, SPH_DENSITY_MINB) k_densi
     density_item<SPH_DENSITY_THREADS>(c, blockIdx.x);
 }
 __global__ void __launch_bounds__(kTile, 4) k_density_narrow(SimConst c) { density_item<kTile>(c, blockIdx.x); }
+#if SPH_DENSITY_BRICK
+__global__ void __launch_bounds__(kBrickThreads, 2) k_density_brick(SimConst c)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    density_brick(c, *reinterpret_cast<BrickShared *>(dsm));
+}
+#endif
 __global__ void __launch_bounds__(kTile) k_boundary_volume(SimConst c) { boundary_volume_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force(SimConst c) { force_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_wrench(SimConst c) { wrench_item(c, blockIdx.x); }
@@ -98,6 +105,17 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     mark();
     // volume-based boundaries: their weights first (timed with the density pass)
     if (c.flags & FLAG_VOLUME) k_boundary_volume<<<nb, kTile, 0, s>>>(c);
+#if SPH_DENSITY_BRICK
+    static bool brick_attr = false;
+    if (!brick_attr) {
+        cudaFuncSetAttribute(k_density_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BrickShared));
+        brick_attr = true;
+    }
+    if (c.n >= kDensityWideMin && !(c.flags & FLAG_VOLUME))
+        k_density_brick<<<dim3((c.nx + kBX - 1) / kBX, (c.ny + kBY - 1) / kBY, (c.nz + kBZ - 1) / kBZ), kBrickThreads,
+                          sizeof(BrickShared), s>>>(c);
+    else
+#endif
     if (c.n >= kDensityWideMin)
         k_density<<<blocks_for(c.n, SPH_DENSITY_THREADS), SPH_DENSITY_THREADS, 0, s>>>(c);
     else

@@ -374,8 +374,9 @@ def batched_set(name, make, args, cells=(1.001, 2.002)):
 
 def batched_form(args, flush_l2_factory):
     """Batched scenes: (a) the configuration named for the form -- 64 stirring scenes of
-    log-uniform fluid counts 8k-256k (8 M particles, compute-bound); (b) a launch-bound set --
-    256 compact stirring scenes of 2k-8k fluid (2.7 M particles, 6.5k-17k per scene)."""
+    log-uniform fluid counts 8k-256k (8 M particles, compute-bound); (b) 256 compact stirring
+    scenes of 2k-8k fluid (2.7 M particles, 6.5k-17k per scene); (c) a launch-bound set --
+    512 compact scenes of 500-2k fluid (2.8 M particles, mostly tank walls)."""
     from paper_2511_15908_gb300 import scenes
     n_sub = args.steps + args.warmup + 200
     return {"stirring_64_8k_256k": batched_set(
@@ -384,6 +385,10 @@ def batched_form(args, flush_l2_factory):
             "stirring_256_compact_2k_8k": batched_set(
                 "256 compact scenes, fluid log-uniform 2k-8k (seed 1)",
                 lambda cell: scenes.batched(seed=1, n_scenes=256, lo=2000, hi=8000, compact=True,
+                                            n_substeps=n_sub, cell_over_h=cell), args),
+            "stirring_512_compact_500_2k": batched_set(
+                "512 compact scenes, fluid log-uniform 500-2k (seed 2)",
+                lambda cell: scenes.batched(seed=2, n_scenes=512, lo=500, hi=2000, compact=True,
                                             n_substeps=n_sub, cell_over_h=cell), args)}
 
 

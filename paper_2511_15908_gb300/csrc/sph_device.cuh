@@ -837,6 +837,169 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     else density_item_v<false, THREADS>(c, blk, s_pend);
 }
 
+#if SPH_DENSITY_COOP
+// Alternative density pass, built only with -DSPH_DENSITY_COOP=G (G = 4, 8, 16 or 32) and
+// SPH_DENSITY_COOP_MINB: G cooperating lanes per particle (mass boundaries).  The lanes of
+// a group set up the particle's clipped rows of cells together, test the flattened
+// candidates G at a time (ascending slots, the order of the row walk), queue the
+// neighbours in shared memory and evaluate them G at a time, one neighbour per lane, each
+// lane summing its float-pair share; a shuffle tree of TwoSums adds the lanes' shares.
+// Same neighbours, same neighbour list (in the same order) as density_item_v; the density
+// sum, exact to ~1e-13 in any order, may round differently in its last bit.  Measured
+// against the one-thread-per-particle walk on the stirred coupled scene and rejected
+// (2.1x slower at best, G = 8): the group's set-up, compaction and queue round trips cost
+// more than the lanes it keeps busy.
+template <int G>
+__device__ __forceinline__ void density_coop_item(const SimConst &c, int blk)
+{
+    constexpr int kGroups = kTile / G;
+    constexpr int kRowsMax = 36;                     // (z1 - z0 + 1) (y1 - y0 + 1) <= 6 x 6
+    __shared__ int s_rs[kGroups][kRowsMax];          // first slot of each row's range
+    __shared__ int s_pre[kGroups][kRowsMax + 1];     // exclusive prefix of the ranges' lengths
+    __shared__ int s_nb[kGroups][2 * G];             // queued neighbours
+    const int g = threadIdx.x / G, l = threadIdx.x % G;
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << gbase;
+    const int p = blk * kGroups + g;
+    if (p >= c.n) return;                            // the whole group
+    const float4 xi = c.xA[p];
+    uint32_t bad = 0;
+    int kind = 0, excl_lo = 0, excl_n = 0;
+    if (xi.w < 0.0f) pair_scope(c, __float_as_int(c.vA[p].w), kind, excl_lo, excl_n);
+    const bool keep_list = kind != KIND_STATIC || (c.flags & FLAG_RECORD);
+    const float *vw = reinterpret_cast<const float *>(c.vA) + 3;   // id bits, stride 4
+    const bool near0 = near_origin_planes(c, xi);
+
+    // rows of cells (bounds as for_each_row), G rows at a time
+    const float ux = __fmul_rn(__fsub_rn(xi.x, c.o[0]), c.inv_cell);
+    const float uy = __fmul_rn(__fsub_rn(xi.y, c.o[1]), c.inv_cell);
+    const float uz = __fmul_rn(__fsub_rn(xi.z, c.o[2]), c.inv_cell);
+    const float Rc = c.Rc, Rc2 = Rc * Rc, mc = c.mc;
+    const int cy = cell_floor(uy, c.ny), cz = cell_floor(uz, c.nz);
+    const int z0 = cell_floor(uz - Rc, c.nz), z1 = cell_floor(uz + Rc, c.nz);
+    const int y0 = cell_floor(uy - Rc, c.ny), y1 = cell_floor(uy + Rc, c.ny);
+    const int nyw = y1 - y0 + 1;
+    if ((z1 - z0 + 1) * nyw > kRowsMax) bad |= ST_CAPACITY;   // the launcher keeps Rc < 2.5
+    const int nrows = min((z1 - z0 + 1) * nyw, kRowsMax);
+    for (int r = l; r < nrows; r += G) {
+        const int z = z0 + r / nyw, y = y0 + r % nyw;
+        const float gz = cell_gap(uz, z, cz, mc), gy = cell_gap(uy, y, cy, mc);
+        const float w2 = (Rc2 - gz * gz) - gy * gy;
+        int s0 = 0, len = 0;
+        if (w2 >= 0.0f) {
+            const float w = w2 * rsqrtf(fmaxf(w2, 1e-30f)) + mc;
+            const int xa = cell_floor(ux - w, c.nx), xb = cell_floor(ux + w, c.nx);
+            const int base = (z * c.ny + y) * c.nx;
+            s0 = in_range(c, __ldg(c.cell_start + in_range(c, base + xa, c.ncell)), c.n + 1);
+            const int e0 = in_range(c, __ldg(c.cell_start + in_range(c, base + xb + 1, c.ncell + 1)), c.n + 1);
+            len = max(e0 - s0, 0);
+            if (len > kMaxCellRun) { len = kMaxCellRun; bad |= ST_CAPACITY; }
+        }
+        s_rs[g][r] = s0;
+        s_pre[g][r + 1] = len;
+    }
+    __syncwarp(gmask);
+    if (l == 0) {
+        int a = 0;
+        s_pre[g][0] = 0;
+        for (int r = 1; r <= nrows; ++r) { a += s_pre[g][r]; s_pre[g][r] = a; }
+    }
+    __syncwarp(gmask);
+    const int T = s_pre[g][nrows];
+
+    PairDensitySum acc;
+    if (l == 0) acc.self(fabsf(xi.w));
+    else acc.cnt = 0;
+    int nq = 0;                                      // queued neighbours (group-uniform)
+    int nl = 0;                                      // partners listed (group-uniform)
+    int row = 0;                                     // row of the round's first candidate
+    uint32_t *list = reinterpret_cast<uint32_t *>(c.nlist4 + p);
+    const size_t lstride = 4 * (size_t)c.n;          // words between quads of one particle
+    const unsigned lt = (1u << l) - 1u;
+    // one neighbour per lane (lanes l < m): density term, and the partner list in queue order
+    auto eval = [&](int m) {
+        bool partner = false;
+        int q = 0;
+        if (l < m) {
+            q = s_nb[g][l];
+            const float4 xj = __ldg(c.xA + q);
+            float dx, dy, dz, r2x;
+            pair_offset(xi, xj, near0, dx, dy, dz, r2x);
+            acc.add(c, fabsf(xj.w), 0.0f, dx, dy, dz, r2x);
+            partner = keep_list &&
+                      !(excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) < (unsigned)excl_n);
+        }
+        const unsigned pb = (__ballot_sync(gmask, partner) >> gbase) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u));
+        if (partner) {
+            const int k = nl + __popc(pb & lt);
+            if (k < c.nl_cap) list[(size_t)(k >> 2) * lstride + (k & 3)] = (uint32_t)q;
+        }
+        nl += __popc(pb);
+    };
+    for (int k0 = 0; k0 < T; k0 += G) {
+        const int k = k0 + l;
+        bool nbr = false;
+        int q = 0;
+        if (k < T) {
+            int r = row;
+            while (s_pre[g][r + 1] <= k) ++r;
+            q = s_rs[g][r] + (k - s_pre[g][r]);
+            const float4 xj = __ldg(c.xA + q);
+            float dx, dy, dz;
+            nbr = dist2(xi, xj, dx, dy, dz) < c.R2 && q != p;
+        }
+        {
+            int r = row;
+            const int kn = k0 + G;
+            while (r < nrows && s_pre[g][r + 1] <= kn) ++r;
+            row = r;
+        }
+        const unsigned bm = (__ballot_sync(gmask, nbr) >> gbase) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u));
+        if (nbr) s_nb[g][nq + __popc(bm & lt)] = q;
+        nq += __popc(bm);
+        __syncwarp(gmask);
+        if (nq >= G) {
+            eval(G);
+            __syncwarp(gmask);
+            if (l < nq - G) s_nb[g][l] = s_nb[g][G + l];
+            __syncwarp(gmask);
+            nq -= G;
+        }
+    }
+    if (nq > 0) eval(nq);
+
+    // the lanes' shares, added by a fixed shuffle tree
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const float S2 = __shfl_down_sync(gmask, acc.S, off, G);
+        const float L2 = __shfl_down_sync(gmask, acc.L, off, G);
+        const int n2 = __shfl_down_sync(gmask, acc.cnt, off, G);
+        const unsigned b2 = __shfl_down_sync(gmask, bad, off, G);
+        float e;
+        acc.S = two_sum(acc.S, S2, e);
+        acc.L = __fadd_rn(acc.L, __fadd_rn(L2, e));
+        acc.cnt += n2;
+        bad |= b2;
+    }
+    if (l == 0) {
+        c.nlist_n[p] = nl;
+        const float drho = acc.excess(c, c.rho0);
+        const float rho = __fadd_rn(c.rho0, drho);
+        float pr;
+        if (c.flags & FLAG_TAIT) {
+            const float x = drho / c.rho0;
+            pr = c.tait_B * (x * (7.0f + x * (21.0f + x * (35.0f + x * (35.0f + x * (21.0f + x * (7.0f + x)))))));
+        } else {
+            pr = c.k * drho;
+        }
+        if ((c.flags & FLAG_CLAMP) && pr < 0.0f) pr = 0.0f;
+        c.prho[p] = make_float2(rho, pr / (rho * rho));
+        if (c.flags & FLAG_RECORD) c.nnbr[p] = acc.cnt - 1;
+        report(c, bad);
+    }
+}
+#endif
+
 #if SPH_DENSITY_BRICK
 // Alternative density pass, built only with -DSPH_DENSITY_BRICK=1 (and SPH_BRICK_X/Y/Z/CAP):
 // one CTA per brick of kBX x kBY x kBZ cells.  The positions of the brick's cells and of a

@@ -32,6 +32,12 @@ __global__ void __launch_bounds__(SPH_DENSITY_THREADS, SPH_DENSITY_MINB) k_densi
     density_item<SPH_DENSITY_THREADS>(c, blockIdx.x);
 }
 __global__ void __launch_bounds__(kTile, 4) k_density_narrow(SimConst c) { density_item<kTile>(c, blockIdx.x); }
+#if SPH_DENSITY_COOP
+__global__ void __launch_bounds__(kTile, SPH_DENSITY_COOP_MINB) k_density_coop(SimConst c)
+{
+    density_coop_item<SPH_DENSITY_COOP>(c, blockIdx.x);
+}
+#endif
 #if SPH_DENSITY_BRICK
 __global__ void __launch_bounds__(kBrickThreads, 2) k_density_brick(SimConst c)
 {
@@ -114,6 +120,11 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     if (c.n >= kDensityWideMin && !(c.flags & FLAG_VOLUME))
         k_density_brick<<<dim3((c.nx + kBX - 1) / kBX, (c.ny + kBY - 1) / kBY, (c.nz + kBZ - 1) / kBZ), kBrickThreads,
                           sizeof(BrickShared), s>>>(c);
+    else
+#endif
+#if SPH_DENSITY_COOP
+    if (c.n >= kDensityWideMin && !(c.flags & FLAG_VOLUME) && c.Rc < 2.5f)
+        k_density_coop<<<(unsigned)(((long long)c.n * SPH_DENSITY_COOP + kTile - 1) / kTile), kTile, 0, s>>>(c);
     else
 #endif
     if (c.n >= kDensityWideMin)

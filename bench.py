@@ -577,8 +577,8 @@ def surrogate_form(args):
     model.set_scene(sc.params)
     x, y = surrogate.pairs(model, desc, wr, cycle, dt)
     t0 = time.perf_counter()
-    steps = 3000
-    losses = surrogate.fit(model, x, y, steps=steps, batch=1024, lr=1e-3)
+    steps = 20000
+    losses, vals = surrogate.fit(model, x, y, steps=steps, batch=1024, lr=1e-3, val_frac=0.1)
     torch.cuda.synchronize()
     t_fit = time.perf_counter() - t0
     n_cycles = (n - n_train) // cycle
@@ -592,6 +592,8 @@ def surrogate_form(args):
                               "train_steps": steps, "train_s": t_fit, "log_s": t_log,
                               "train_step_ms_batch1024": t_step,
                               "first_last_loss": [losses[0][1], losses[-1][1]],
+                              "early_stopping": {"validation": "last 10 % of the training pairs",
+                                                 "best_step_and_loss": list(min(vals, key=lambda v: v[1]))},
                               "jitter_floor": surrogate.jitter_floor(wr)}
     out["tick_latency_us"] = lat
     per_ep = 100
@@ -608,7 +610,7 @@ def surrogate_form(args):
     model_d = sph.Surrogate(max_batch=2048)
     model_d.set_scene(sd.params)
     xd_, yd_ = surrogate.pairs(model_d, d_d, w_d, cyc_d, dtd, rows=np.arange(nd_train))
-    surrogate.fit(model_d, xd_, yd_, steps=3000, batch=1024, lr=1e-3)
+    surrogate.fit(model_d, xd_, yd_, steps=20000, batch=1024, lr=1e-3, val_frac=0.1)
     ev_in = surrogate.offline_errors(model_d, d_d[nd_train:], w_d[nd_train:], cyc_d, 1, dtd)
     # the stirring tank's held-out substeps in its own scales (first logged after training)
     model_d.set_scene(sc.params)

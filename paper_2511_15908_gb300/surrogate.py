@@ -94,16 +94,33 @@ def standardisation(x: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 
 def fit(model: "sph.Surrogate", x, y, steps: int = 3000, batch: int = 1024, lr: float = 1e-3,
-        seed: int = 0, init_seed: int = 0):
+        seed: int = 0, init_seed: int = 0, val_frac: float = 0.0, eval_every: int = 250):
     """Train from seeded initial weights with Adam on random minibatches (device gathers);
-    x, y: CUDA tensors (n, 269) and (n, 6)."""
+    x, y: CUDA tensors (n, 269) and (n, 6), rows in time order.  With val_frac > 0 the last
+    val_frac of the rows are held out for validation: their MSE (standardised outputs) is
+    taken every eval_every steps and the weights of the best evaluation are kept (early
+    stopping).  Returns [(step, training loss)], and with validation also the
+    [(step, validation loss)] list."""
     import torch
-    model.set_params(scenes.mlp_init_params(init_seed),
-                     standardisation(x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)))
+    n_all = x.shape[0]
+    n = n_all - int(round(val_frac * n_all)) if val_frac > 0 else n_all
+    norm = standardisation(x[:n].cpu().numpy().astype(np.float64), y[:n].cpu().numpy().astype(np.float64))
+    model.set_params(scenes.mlp_init_params(init_seed), norm)
+    ym = torch.tensor(norm[2 * N_IN:2 * N_IN + N_OUT], device=model.device)
+    ys = torch.tensor(norm[2 * N_IN + N_OUT:], device=model.device)
+
+    def val_loss():
+        tot = 0.0
+        for a in range(n, n_all, model.max_batch):
+            yp = model.forward(x[a:min(n_all, a + model.max_batch)])
+            d = (yp - y[a:min(n_all, a + model.max_batch)]) / ys
+            tot += float((d * d).sum())
+        return tot / ((n_all - n) * N_OUT)
+
     g = torch.Generator(device=model.device)
     g.manual_seed(seed)
-    losses = []
-    n = x.shape[0]
+    losses, vals = [], []
+    best = (np.inf, None)
     for s in range(steps):
         idx = torch.randint(0, n, (min(batch, n),), device=model.device, generator=g)
         lr_s = lr * (0.1 ** (s / max(1, steps)))          # exponential decay to lr / 10
@@ -111,7 +128,15 @@ def fit(model: "sph.Surrogate", x, y, steps: int = 3000, batch: int = 1024, lr: 
         loss = model.train_step(x[idx], y[idx], lr_s, want_loss=want)
         if want:
             losses.append((s, loss))
+        if n < n_all and ((s + 1) % eval_every == 0 or s == steps - 1):
+            v = val_loss()
+            vals.append((s + 1, v))
+            if v < best[0]:
+                best = (v, model.get_params())
     model.sync()
+    if best[1] is not None:
+        model.set_params(best[1])                          # keeps the standardisation
+        return losses, vals
     return losses
 
 

@@ -47,10 +47,15 @@ def test_forward_matches_oracle(sph):
     m.close()
 
 
-def test_gradients_match_oracle(sph):
+@pytest.mark.parametrize("B", [272, 130, 1100])
+def test_gradients_match_oracle(sph, B):
+    """272: three row tiles, five K chunks of the batch contraction in five K slices; 130: a
+    ragged row tile and a two-row K chunk (the batch capacity is not a multiple of 8 either,
+    so the column-major copies have padded rows); 1100: 18 K chunks over 8 K slices of 3
+    chunks, the last two slices empty (written as zeros)."""
     import torch
-    params, norm, X, T = _data(272, seed=1)
-    m = sph.Surrogate(max_batch=512)
+    params, norm, X, T = _data(B, seed=1)
+    m = sph.Surrogate(max_batch=B + 3)
     m.set_params(params, norm)
     g, loss = m.gradients(torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda"))
     lref, gref = omlp.grad(params, norm, X, T, bf=True)

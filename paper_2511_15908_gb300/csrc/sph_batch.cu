@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
 // 64 registers (4 blocks); 5 blocks give 51 without spilling (6 spill: the scene's
 // parameters live in shared memory here), per-phase batch 4.29 -> 3.90 ms on 64 scenes.
 template <int PH>
-constexpr int batch_phase_minb() { return PH == P_DENSITY ? 4 : PH == P_FORCE ? 3 : 1; }
+constexpr int batch_phase_minb() { return PH == P_DENSITY ? 3 : PH == P_FORCE ? 3 : 1; }
 
 template <int PH>
 __global__ void __launch_bounds__(kTile, batch_phase_minb<PH>()) k_batch_phase(BatchConst b)

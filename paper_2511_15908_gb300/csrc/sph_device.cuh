@@ -439,6 +439,108 @@ __device__ __forceinline__ float diff_lo(float a, float b, float d)
     return __fadd_rn(__fsub_rn(a, __fsub_rn(d, bb)), __fsub_rn(-b, bb));
 }
 
+// ---------------------------------------------- two neighbours at once (packed FP32)
+// sm_100 and later issue a pair of FP32 additions, multiplications or FMAs as one
+// instruction (__fadd2_rn, __fmul2_rn, __ffma2_rn), each component rounded exactly as the
+// scalar operation.  The float-pair arithmetic below evaluates two neighbours' terms that
+// way: component for component the same operations as the scalar functions above, so the
+// same values; the passes are bound by instruction issue, which the pairing halves for
+// this part.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ float2 two_sum2(float2 a, float2 b, float2 &err)
+{
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    err = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+    return s;
+}
+
+__device__ __forceinline__ float2 cube_pair2(float2 th, float2 tl, float2 &lo)
+{
+    const float2 t2 = mul2(th, th), e2 = fma2(th, th, neg2(t2));
+    const float2 t3 = mul2(t2, th), e3 = fma2(t2, th, neg2(t3));
+    lo = fma2(mul2(f2s(3.0f), t2), tl, fma2(e2, th, e3));
+    return t3;
+}
+
+__device__ __forceinline__ float2 diff_lo2(float2 a, float2 b, float2 d)
+{
+    const float2 bb = sub2(d, a);
+    return add2(sub2(a, sub2(d, bb)), sub2(neg2(b), bb));
+}
+
+// pair_offset for two neighbours (x, y, z components of xa and xb packed)
+__device__ __forceinline__ void pair_offset2(float4 xi, float4 xa, float4 xb, bool near0, float2 &dx, float2 &dy,
+                                             float2 &dz, float2 &r2x, float2 &lx, float2 &ly, float2 &lz)
+{
+    const float2 ax = f2(xa.x, xb.x), ay = f2(xa.y, xb.y), az = f2(xa.z, xb.z);
+    const float2 ix = f2s(xi.x), iy = f2s(xi.y), iz = f2s(xi.z);
+    dx = sub2(ax, ix);
+    dy = sub2(ay, iy);
+    dz = sub2(az, iz);
+    r2x = f2s(0.0f);
+    lx = ly = lz = f2s(0.0f);
+    if (near0) {
+        lx = diff_lo2(ax, ix, dx);
+        ly = diff_lo2(ay, iy, dy);
+        lz = diff_lo2(az, iz, dz);
+        r2x = mul2(f2s(2.0f), fma2(dx, lx, fma2(dy, ly, mul2(dz, lz))));
+    }
+}
+
+struct PairQ2 {
+    float2 qh, ql;
+};
+__device__ __forceinline__ PairQ2 pair_q2(const SimConst &c, float2 dx, float2 dy, float2 dz, float2 r2x)
+{
+    const float2 px = mul2(dx, dx), py = mul2(dy, dy), pz = mul2(dz, dz);
+    const float2 ex = fma2(dx, dx, neg2(px)), ey = fma2(dy, dy, neg2(py));
+    const float2 ez = fma2(dz, dz, neg2(pz));
+    float2 e1, e2;
+    const float2 s1 = two_sum2(px, py, e1);
+    const float2 r2h = two_sum2(s1, pz, e2);
+    const float2 r2l = add2(add2(add2(ex, ey), ez), add2(add2(e1, e2), r2x));
+    const float2 rs = f2(rsqrtf(fmaxf(r2h.x, 1e-30f)), rsqrtf(fmaxf(r2h.y, 1e-30f)));
+    const float2 hrs = mul2(f2s(0.5f), rs);
+    float2 r = mul2(r2h, rs);
+    r = fma2(hrs, fma2(neg2(r), r, r2h), r);
+    const float2 rl = mul2(add2(fma2(neg2(r), r, r2h), r2l), hrs);
+    PairQ2 o;
+    o.qh = mul2(r, f2s(c.invh_hi));
+    o.ql = add2(fma2(r, f2s(c.invh_hi), neg2(o.qh)), fma2(r, f2s(c.invh_lo), mul2(rl, f2s(c.invh_hi))));
+    return o;
+}
+
+// the density terms (mh + ml)(6 w(q)) of two neighbours as float pairs (hi, lo): the
+// arithmetic of PairDensitySum::add_q before its accumulation
+__device__ __forceinline__ void density_term2(const PairQ2 &pq, float2 mh, float2 ml, float2 &hi, float2 &lo)
+{
+    const float2 qh = pq.qh, ql = pq.ql;
+    const float2 th = sub2(f2s(2.0f), qh);
+    const float2 tl = sub2(sub2(sub2(f2s(2.0f), th), qh), ql);
+    float2 uh = sub2(f2s(1.0f), qh);
+    float2 ul = sub2(sub2(sub2(f2s(1.0f), uh), qh), ql);
+    if (!(uh.x > 0.0f)) { uh.x = 0.0f; ul.x = 0.0f; }
+    if (!(uh.y > 0.0f)) { uh.y = 0.0f; ul.y = 0.0f; }
+    float2 t3l;
+    const float2 t3 = cube_pair2(th, tl, t3l);
+    const float2 u2 = mul2(uh, uh);
+    const float2 u3 = mul2(u2, uh);
+    const float2 u3l = mul2(mul2(f2s(3.0f), u2), ul);
+    const float2 m4u3 = mul2(f2s(-4.0f), u3);
+    const float2 w6h = add2(t3, m4u3);
+    const float2 w6l = add2(sub2(m4u3, sub2(w6h, t3)), fma2(f2s(-4.0f), u3l, t3l));
+    hi = mul2(mh, w6h);
+    lo = fma2(ml, w6h, fma2(mh, w6l, fma2(mh, w6h, neg2(hi))));
+}
+
 // Sum of m_j * 6 w(q_ij) over a particle's neighbours with an error of a few units of the
 // second order in FP32 rounding (~1e-13 relative), i.e. as good as the FP64 definition for
 // the pressure the force pass needs: p = k (rho - rho0) turns one FP32 ulp of rho ~ 1000
@@ -517,6 +619,11 @@ struct PairDensitySum {
         // term (mh + ml)(w6h + w6l)
         const float th_ = __fmul_rn(mh, w6h);
         const float lo = __fmaf_rn(ml, w6h, __fmaf_rn(mh, w6l, __fmaf_rn(mh, w6h, -th_)));
+        add_term(th_, lo);
+    }
+    // a term (hi, lo) computed elsewhere (density_term2)
+    __device__ __forceinline__ void add_term(float th_, float lo)
+    {
         float es;
         S = two_sum(S, th_, es);
         L = __fadd_rn(L, __fadd_rn(lo, es));
@@ -600,6 +707,10 @@ struct PairGradSum {
     {
         const float th = __fmul_rn(mh, d);
         const float tl = __fmaf_rn(mh, dl, __fmaf_rn(ml, d, __fmaf_rn(mh, d, -th)));
+        acc1(S, L, th, tl);
+    }
+    static __device__ __forceinline__ void acc1(float &S, float &L, float th, float tl)
+    {
         float e;
         S = two_sum(S, th, e);
         L = __fadd_rn(L, __fadd_rn(tl, e));
@@ -694,6 +805,9 @@ struct ListWriter {
 #ifndef SPH_DENSITY_PENDING
 #define SPH_DENSITY_PENDING 8
 #endif
+#ifndef SPH_DENSITY_PAIRED
+#define SPH_DENSITY_PAIRED 1
+#endif
 #ifndef SPH_DENSITY_DRAIN_AT
 #define SPH_DENSITY_DRAIN_AT 0
 #endif
@@ -725,6 +839,80 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
     int2 *pend = s_pend + threadIdx.x;            // entry k at pend[k * THREADS]
     int np = 0;
 
+#if SPH_DENSITY_PAIRED
+    // The neighbours are evaluated two at a time with packed FP32 instructions (the
+    // terms, component for component the scalar arithmetic) and accumulated in the order
+    // they are found, so the sum is the one-at-a-time sum bit for bit.  An odd neighbour
+    // waits (held) for the next drain's first, or for the end of the walk.
+    bool held = false;
+    float4 hx = xi;
+    float hmh = 0.0f, hml = 0.0f;
+    auto eval2 = [&](float4 xa, float mah, float mal, float4 xb, float mbh, float mbl, bool has_b) {
+        float2 dx, dy, dz, r2x, lx, ly, lz;
+        pair_offset2(xi, xa, xb, near0, dx, dy, dz, r2x, lx, ly, lz);
+        const PairQ2 pq = pair_q2(c, dx, dy, dz, r2x);
+        float2 hi, lo;
+        density_term2(pq, f2(mah, mbh), f2(mal, mbl), hi, lo);
+        acc.add_term(hi.x, lo.x);
+        if (has_b) acc.add_term(hi.y, lo.y);
+    };
+    auto drain = [&]() {
+        if (np == 0) return;
+        int k = 0;
+        int2 e = pend[0];
+        uint32_t mm = (uint32_t)e.y;
+        auto next = [&](int &q) {
+            while (mm == 0u) {
+                if (++k >= np) return false;
+                e = pend[k * THREADS];
+                mm = (uint32_t)e.y;
+            }
+            q = e.x + __ffs(mm) - 1;
+            mm &= mm - 1u;
+            return true;
+        };
+        // the neighbour's position and weight (a boundary neighbour of the volume variant
+        // weighs psi, kept in its (rho, P) slot as a float pair), and its partner entry: a
+        // volume-boundary particle interacts with fluid and soft ones only, a static or
+        // rigid one not with its own body
+        auto take = [&](int q, float4 &xj, float &mh, float &ml) {
+            xj = __ldg(c.xA + q);
+            mh = fabsf(xj.w);
+            ml = 0.0f;
+            if (vol && !vol_boundary && xj.w < 0.0f) {
+                const float2 psi = __ldg(&c.prho[q]);
+                mh = psi.x;
+                ml = psi.y;
+            }
+            if (keep_list && !(vol_boundary && xj.w < 0.0f) &&
+                !(excl_n && (unsigned)(__float_as_int(__ldg(vw + 4 * (size_t)q)) - excl_lo) < (unsigned)excl_n))
+                list.push((uint32_t)q);
+        };
+        int q;
+        float4 xb;
+        float mbh, mbl;
+        if (vol_boundary) {                        // counted; the slot keeps psi
+            while (next(q)) {
+                take(q, xb, mbh, mbl);
+                ++acc.cnt;
+            }
+            np = 0;
+            return;
+        }
+        for (;;) {
+            if (!held) {
+                if (!next(q)) break;
+                take(q, hx, hmh, hml);
+                held = true;
+            }
+            if (!next(q)) break;
+            take(q, xb, mbh, mbl);
+            eval2(hx, hmh, hml, xb, mbh, mbl, true);
+            held = false;
+        }
+        np = 0;
+    };
+#else
     // evaluate the pending neighbours in one flat loop (every stored mask is non-empty)
     auto drain = [&]() {
         if (np == 0) return;
@@ -763,6 +951,8 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
         np = 0;
     };
 
+#endif
+
     // rows of cells around the particle (bounds as for_each_row)
     const float ux = __fmul_rn(__fsub_rn(xi.x, c.o[0]), c.inv_cell);
     const float uy = __fmul_rn(__fsub_rn(xi.y, c.o[1]), c.inv_cell);
@@ -791,6 +981,26 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
             for (int b = s0; b < e0; b += 32) {
                 const int end = min(e0, b + 32);
                 uint32_t mm = 0u, bit = 1u;
+#if SPH_DENSITY_PAIRED
+                // two candidates per step: the predicate of dist2, component for component
+                const float2 ix = f2s(xi.x), iy = f2s(xi.y), iz = f2s(xi.z);
+                int q = b;
+#pragma unroll 2
+                for (; q + 1 < end; q += 2) {
+                    const float4 xa = __ldg(c.xA + q), xb = __ldg(c.xA + q + 1);
+                    const float2 dx = sub2(f2(xa.x, xb.x), ix), dy = sub2(f2(xa.y, xb.y), iy);
+                    const float2 dz = sub2(f2(xa.z, xb.z), iz);
+                    const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                    if (r2.x < c.R2) mm |= bit;
+                    if (r2.y < c.R2) mm |= bit << 1;
+                    bit <<= 2;
+                }
+                if (q < end) {
+                    const float4 xj = __ldg(c.xA + q);
+                    float dx, dy, dz;
+                    if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
+                }
+#else
 #pragma unroll kMaskUnroll
                 for (int q = b; q < end; ++q) {
                     const float4 xj = __ldg(c.xA + q);
@@ -798,6 +1008,7 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
                     if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
                     bit <<= 1;
                 }
+#endif
                 if ((unsigned)(p - b) < 32u) mm &= ~(1u << (p - b));   // self: summed above
                 if (!mm) continue;
                 if (np == kPending) drain();
@@ -808,6 +1019,9 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
         if (np > kDrainAt) drain();                // the plane's neighbours
     }
     drain();
+#if SPH_DENSITY_PAIRED
+    if (held) eval2(hx, hmh, hml, xi, 0.0f, 0.0f, false);
+#endif
     list.flush();
     c.nlist_n[p] = list.nl;
     const float drho = acc.excess(c, c.rho0);

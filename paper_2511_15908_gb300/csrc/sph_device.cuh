@@ -808,6 +808,10 @@ struct ListWriter {
 #ifndef SPH_DENSITY_PAIRED
 #define SPH_DENSITY_PAIRED 1
 #endif
+#ifndef SPH_PAIR_UNROLL
+#define SPH_PAIR_UNROLL 1
+#endif
+constexpr int kPairUnroll = SPH_PAIR_UNROLL;
 #ifndef SPH_DENSITY_DRAIN_AT
 #define SPH_DENSITY_DRAIN_AT 0
 #endif
@@ -985,7 +989,7 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
                 // two candidates per step: the predicate of dist2, component for component
                 const float2 ix = f2s(xi.x), iy = f2s(xi.y), iz = f2s(xi.z);
                 int q = b;
-#pragma unroll 2
+#pragma unroll kPairUnroll
                 for (; q + 1 < end; q += 2) {
                     const float4 xa = __ldg(c.xA + q), xb = __ldg(c.xA + q + 1);
                     const float2 dx = sub2(f2(xa.x, xb.x), ix), dy = sub2(f2(xa.y, xb.y), iy);

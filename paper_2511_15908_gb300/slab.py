@@ -15,7 +15,9 @@ now in its slab and hands the others to their new owner (the same neighbour exch
 
 This module holds the decomposition and the data movement only; the exchanges go through
 torch.distributed (gloo on CPU, NCCL between GPUs; no multicast, no library kernel on peer
-memory).  The per-rank substep is the caller's.
+memory).  The per-rank substep is the caller's.  Free rigid bodies would need each rank to
+integrate the body from the allreduced wrench before the next substep; soft bodies whose
+springs cross a slab edge are not handled.
 """
 from __future__ import annotations
 
@@ -115,15 +117,32 @@ def allreduce_wrench(w: np.ndarray) -> np.ndarray:
     return t.numpy()
 
 
-def particle_positions(scene) -> np.ndarray:
+def migrate(ids: np.ndarray, x: np.ndarray, v: np.ndarray, slabs: "Slabs", rank: int, world: int):
+    """Owner hand-over after a substep: of this rank's particles (global ids, FP32 positions
+    and velocities after the substep), those whose position now lies in a neighbour's slab
+    go to that neighbour (one exchange); returns this rank's particles: the ones that stayed,
+    then the arrivals, and the number of arrivals."""
+    own = slabs.owner(x)
+    if np.any(np.abs(own - rank) > 1):
+        raise ValueError("a particle crossed more than one slab in one substep")
+    stay = own == rank
+    gx, gv, gid = unpack(neighbour_exchange(pack(x, v, ids), own == rank - 1, own == rank + 1, rank, world))
+    return (np.concatenate([np.asarray(ids)[stay], gid]), np.concatenate([np.asarray(x, np.float32)[stay], gx]),
+            np.concatenate([np.asarray(v, np.float32)[stay], gv]), int(gid.size))
+
+
+def particle_positions(scene, step: int = 0) -> np.ndarray:
     """Positions (id order) used to assign owners: fluid and static / soft particles as
-    given, rigid particles placed from the body's pose at the first substep (FP64, then
-    FP32; the substep itself places them again)."""
+    given, rigid particles placed from the body's pose at substep `step` (the grab path's
+    row for a grabbed body, clamped to its last; FP64, then FP32; the substep itself
+    places them again)."""
     xs = [np.asarray(scene.fluid_x, np.float32)]
     for bi, b in enumerate(scene.bodies):
         if b.kind == 2:                               # rigid
-            pose = (scene.trajectory[0, :7] if bi == scene.grab_body and scene.trajectory is not None
-                    else b.pose).astype(np.float64)
+            row = None
+            if bi == scene.grab_body and scene.trajectory is not None:
+                row = scene.trajectory[min(step, scene.trajectory.shape[0] - 1), :7]
+            pose = (row if row is not None else b.pose).astype(np.float64)
             w, x, y, z = pose[3:7] / np.linalg.norm(pose[3:7])
             R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
                           [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],

@@ -111,3 +111,110 @@ def test_two_ranks_equal_one_undivided_gpu_substep():
         F, T = d["wrench"][:3], d["wrench"][3:]
         assert np.linalg.norm(F - wref[:3]) <= 1e-4 * np.linalg.norm(wref[:3])
         assert np.linalg.norm(T - wref[3:]) <= 1e-4 * np.linalg.norm(wref[3:])
+
+
+def _rank_multi(rank, world, port, n_sub, out):
+    """n_sub substeps, each one library run of this rank's owned + ghost particles; the
+    owned fluid particles that left the slab are handed over after each substep."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_2511_15908_gb300 import sph
+    sph.load()
+    sc = _scene()
+    s = sc.fluid_spacing
+    R = 2.0 * float(np.float32(sc.params["h"]))
+    sl = slab.Slabs(0.0, 19 * s, world, halo=2.0 * R)     # the middle edge on a column (9.5 s)
+    nf = sc.n_fluid
+    x0 = slab.particle_positions(sc)
+    own = sl.owner(x0[:nf]) == rank
+    ids_f = np.nonzero(own)[0]
+    x_f, v_f = x0[:nf][own], slab.particle_velocities(sc)[:nf][own]
+    first = nf + sum(b.n for b in sc.bodies[:sc.grab_body])
+    nbody = sc.bodies[sc.grab_body].n
+    mass = _mass_by_id(sc)
+    wrenches, arrivals = [], 0
+    for k in range(n_sub):
+        xb = slab.particle_positions(sc, step=k)[nf:]
+        ob = sl.owner(xb) == rank
+        ids = np.concatenate([ids_f, nf + np.nonzero(ob)[0]])
+        x = np.concatenate([x_f, xb[ob]])
+        v = np.concatenate([v_f, np.zeros((int(ob.sum()), 3), np.float32)])
+        left, right = sl.ghost_masks(x, rank)
+        gx, gv, gid = slab.unpack(slab.neighbour_exchange(slab.pack(x, v, ids), left, right, rank, world))
+        sub, sub_ids = slab.sub_scene(sc, np.concatenate([ids, gid]), np.concatenate([x, gx]),
+                                      np.concatenate([v, gv]))
+        sim = sph.Simulation(sub, flags=sub.params["flags"] | sph.FLAG_RECORD)
+        sim.step(1)
+        st = sim.state(record=True)
+        sim.close()
+        mine_f = np.isin(sub_ids, ids_f)
+        sel = np.isin(sub_ids, ids) & (sub_ids >= first) & (sub_ids < first + nbody)
+        f = mass[sub_ids[sel]][:, None] * st["acc"][sel].astype(np.float64)
+        xg = sc.trajectory[min(k, sc.trajectory.shape[0] - 1), :3].astype(np.float64)
+        w = np.zeros((1, 6))
+        w[0, :3], w[0, 3:] = f.sum(0), np.cross(xb[sub_ids[sel] - nf].astype(np.float64) - xg, f).sum(0)
+        wrenches.append(slab.allreduce_wrench(w)[0])
+        ids_f, x_f, v_f, n_in = slab.migrate(sub_ids[mine_f], st["x"][mine_f], st["v"][mine_f], sl, rank, world)
+        arrivals += n_in
+    out[rank] = dict(ids=ids_f, x=x_f, v=v_f, wrench=np.array(wrenches), arrivals=arrivals)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_follow_one_undivided_gpu_run_with_handover():
+    """Five substeps on two slabs with the library as the per-rank substep, particles
+    handed over between them, against five undivided substeps on the same GPU: every fluid
+    particle owned once at the end, positions and velocities within what the parity bar
+    allows over five substeps (the two runs differ in FP32 summation order), the allreduced
+    wrench of every substep within 1e-4."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_15908_gb300 import build
+    build.build()
+    n_sub = 5
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        port = 35000 + os.getpid() % 2000
+        ps = [ctx.Process(target=_rank_multi, args=(r, 2, port, n_sub, out)) for r in range(2)]
+        for p in ps:
+            p.start()
+        for p in ps:
+            p.join(600)
+            assert p.exitcode == 0
+        res = dict(out)
+    from paper_2511_15908_gb300 import sph
+    sph.load()
+    sc = _scene()
+    sim = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_RECORD)
+    nf = sc.n_fluid
+    first = nf + sum(b.n for b in sc.bodies[:sc.grab_body])
+    nbody = sc.bodies[sc.grab_body].n
+    mass = _mass_by_id(sc)
+    wref = []
+    for k in range(n_sub):
+        sim.step(1)
+        st = sim.state(record=True)
+        sel = np.arange(first, first + nbody)
+        f = mass[sel][:, None] * st["acc"][sel].astype(np.float64)
+        xg = sc.trajectory[min(k, sc.trajectory.shape[0] - 1), :3].astype(np.float64)
+        xb = slab.particle_positions(sc, step=k)[sel].astype(np.float64)
+        wref.append(np.concatenate([f.sum(0), np.cross(xb - xg, f).sum(0)]))
+    x_ref, v_ref = st["x"].astype(np.float64), st["v"].astype(np.float64)
+    sim.close()
+    ids = np.concatenate([res[r]["ids"] for r in range(2)])
+    assert np.array_equal(np.sort(ids), np.arange(nf))
+    assert res[0]["arrivals"] + res[1]["arrivals"] > 0, "no particle changed slab"
+    dt = float(np.float32(sc.params["dt"]))
+    for r in range(2):
+        d = res[r]
+        i = d["ids"]
+        # per substep the bar allows |da| <= 1e-4 max(|a|, 0.1 g); |a| stays below ~50 g here
+        dv_bar = n_sub * 1e-4 * 50 * G * dt
+        assert np.max(np.abs(d["v"] - v_ref[i])) <= dv_bar
+        assert np.max(np.abs(d["x"] - x_ref[i])) <= n_sub * dt * dv_bar + 1e-7
+        for k in range(n_sub):
+            F, T = d["wrench"][k, :3], d["wrench"][k, 3:]
+            assert np.linalg.norm(F - wref[k][:3]) <= 1e-4 * np.linalg.norm(wref[k][:3])
+            assert np.linalg.norm(T - wref[k][3:]) <= 1e-4 * np.linalg.norm(wref[k][3:])

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
                     case P_SCATTER: scatter_item(c, blk); break;
                     case P_GATHER: rank_gather_item(c, blk); break;
                     case P_VOLUME: boundary_volume_item(c, blk); break;
-                    case P_DENSITY: density_item<kTile>(c, blk); break;
+                    case P_DENSITY: density_item<kTile, false>(c, blk); break;
                     case P_FORCE: force_item(c, blk); break;
                     default: wrench_item(c, blk); break;
                     }
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kTile, SPH_BATCH_MINB) k_batch(BatchConst b, i
 // 64 registers (4 blocks); 5 blocks give 51 without spilling (6 spill: the scene's
 // parameters live in shared memory here), per-phase batch 4.29 -> 3.90 ms on 64 scenes.
 template <int PH>
-constexpr int batch_phase_minb() { return PH == P_DENSITY ? 3 : PH == P_FORCE ? 3 : 1; }
+constexpr int batch_phase_minb() { return PH == P_DENSITY ? 4 : PH == P_FORCE ? 3 : 1; }
 
 template <int PH>
 __global__ void __launch_bounds__(kTile, batch_phase_minb<PH>()) k_batch_phase(BatchConst b)
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kTile, batch_phase_minb<PH>()) k_batch_phase(B
     case P_SCATTER: scatter_item(c, blk); break;
     case P_GATHER: rank_gather_item(c, blk); break;
     case P_VOLUME: boundary_volume_item(c, blk); break;
-    case P_DENSITY: density_item<kTile>(c, blk); break;
+    case P_DENSITY: density_item<kTile, false>(c, blk); break;
     case P_FORCE: force_item(c, blk); break;
     default: wrench_item(c, blk); break;
     }

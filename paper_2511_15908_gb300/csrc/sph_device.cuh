@@ -818,7 +818,7 @@ constexpr int kPairUnroll = SPH_PAIR_UNROLL;
 constexpr int kPending = SPH_DENSITY_PENDING;   // (chunk start, mask) pairs kept per thread
 constexpr int kDrainAt = SPH_DENSITY_DRAIN_AT;  // a plane's end drains when more are pending
 
-template <bool VOL, int THREADS>
+template <bool VOL, int THREADS, bool PAIRED>
 __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 *s_pend)
 {
     const int p = blk * THREADS + (int)threadIdx.x;
@@ -843,7 +843,6 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
     int2 *pend = s_pend + threadIdx.x;            // entry k at pend[k * THREADS]
     int np = 0;
 
-#if SPH_DENSITY_PAIRED
     // The neighbours are evaluated two at a time with packed FP32 instructions (the
     // terms, component for component the scalar arithmetic) and accumulated in the order
     // they are found, so the sum is the one-at-a-time sum bit for bit.  An odd neighbour
@@ -860,7 +859,7 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
         acc.add_term(hi.x, lo.x);
         if (has_b) acc.add_term(hi.y, lo.y);
     };
-    auto drain = [&]() {
+    auto drain_paired = [&]() {
         if (np == 0) return;
         int k = 0;
         int2 e = pend[0];
@@ -916,9 +915,8 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
         }
         np = 0;
     };
-#else
     // evaluate the pending neighbours in one flat loop (every stored mask is non-empty)
-    auto drain = [&]() {
+    auto drain_scalar = [&]() {
         if (np == 0) return;
         int k = 0;
         int2 e = pend[0];
@@ -955,7 +953,11 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
         np = 0;
     };
 
-#endif
+    // PAIRED: the packed evaluation above; otherwise one neighbour at a time (same sums)
+    auto drain = [&]() {
+        if constexpr (PAIRED) drain_paired();
+        else drain_scalar();
+    };
 
     // rows of cells around the particle (bounds as for_each_row)
     const float ux = __fmul_rn(__fsub_rn(xi.x, c.o[0]), c.inv_cell);
@@ -985,7 +987,7 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
             for (int b = s0; b < e0; b += 32) {
                 const int end = min(e0, b + 32);
                 uint32_t mm = 0u, bit = 1u;
-#if SPH_DENSITY_PAIRED
+                if constexpr (PAIRED) {
                 // two candidates per step: the predicate of dist2, component for component
                 const float2 ix = f2s(xi.x), iy = f2s(xi.y), iz = f2s(xi.z);
                 int q = b;
@@ -1004,7 +1006,7 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
                     float dx, dy, dz;
                     if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
                 }
-#else
+                } else {
 #pragma unroll kMaskUnroll
                 for (int q = b; q < end; ++q) {
                     const float4 xj = __ldg(c.xA + q);
@@ -1012,7 +1014,7 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
                     if (dist2(xi, xj, dx, dy, dz) < c.R2) mm |= bit;
                     bit <<= 1;
                 }
-#endif
+                }
                 if ((unsigned)(p - b) < 32u) mm &= ~(1u << (p - b));   // self: summed above
                 if (!mm) continue;
                 if (np == kPending) drain();
@@ -1023,9 +1025,9 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
         if (np > kDrainAt) drain();                // the plane's neighbours
     }
     drain();
-#if SPH_DENSITY_PAIRED
-    if (held) eval2(hx, hmh, hml, xi, 0.0f, 0.0f, false);
-#endif
+    if constexpr (PAIRED) {
+        if (held) eval2(hx, hmh, hml, xi, 0.0f, 0.0f, false);
+    }
     list.flush();
     c.nlist_n[p] = list.nl;
     const float drho = acc.excess(c, c.rho0);
@@ -1047,12 +1049,14 @@ __device__ __forceinline__ void density_item_v(const SimConst &c, int blk, int2 
 
 // The volume-boundary variant is a separate instance, so the default path carries none of
 // its per-neighbour tests.
-template <int THREADS>
+// PAIRED = false keeps the register footprint of the one-at-a-time evaluation (kernels that
+// carry more state, such as the batched phases), with the same results.
+template <int THREADS, bool PAIRED = (SPH_DENSITY_PAIRED != 0)>
 __device__ __forceinline__ void density_item(const SimConst &c, int blk)
 {
     __shared__ int2 s_pend[kPending * THREADS];      // the block's pending neighbour masks
-    if (c.flags & FLAG_VOLUME) density_item_v<true, THREADS>(c, blk, s_pend);
-    else density_item_v<false, THREADS>(c, blk, s_pend);
+    if (c.flags & FLAG_VOLUME) density_item_v<true, THREADS, PAIRED>(c, blk, s_pend);
+    else density_item_v<false, THREADS, PAIRED>(c, blk, s_pend);
 }
 
 #if SPH_DENSITY_COOP

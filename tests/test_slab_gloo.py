@@ -194,3 +194,26 @@ def test_slab_owner_and_ghost_masks():
     assert not left0.any()
     _, right3 = sl.ghost_masks(x, 3)
     assert not right3.any()
+
+
+def test_migrate_refuses_a_particle_that_crossed_two_slabs():
+    # the check runs before any message is exchanged
+    sl = slab.Slabs(0.0, 3.0, 3, halo=0.1)
+    ids = np.array([5, 6])
+    x = np.array([[0.5, 0, 0], [2.5, 0, 0]], np.float32)      # the second is in rank 2's slab
+    with pytest.raises(ValueError):
+        slab.migrate(ids, x, np.zeros_like(x), sl, 0, 3)
+
+
+def test_particle_positions_follow_the_grab_path():
+    sc = _scene()
+    first = sc.n_fluid + sum(b.n for b in sc.bodies[:sc.grab_body])
+    n = sc.bodies[sc.grab_body].n
+    traj = np.repeat(sc.trajectory[:1], 3, axis=0).copy()
+    traj[2, 0] += 0.05                                       # the body moves 5 cm along x
+    sc.trajectory = traj
+    p0 = slab.particle_positions(sc, step=0)[first:first + n]
+    p2 = slab.particle_positions(sc, step=2)[first:first + n]
+    p9 = slab.particle_positions(sc, step=9)[first:first + n]  # past the path's end: its last row
+    np.testing.assert_allclose(p2 - p0, np.tile([0.05, 0, 0], (n, 1)), atol=1e-6)
+    np.testing.assert_array_equal(p9, p2)

@@ -22,6 +22,7 @@
 #include "sph.h"
 #include "sph_device.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace sphgb {
 
@@ -409,10 +410,9 @@ __global__ void k_sur_tick_features(float t0, float t1, float t2, float t3, floa
 
 // The tick's wrench: the anchor's exact FP64 wrench plus the network's correction, taken out
 // of the standardised, scale-free, body-frame output.
-__global__ void k_sur_tick_output(const float *y, const float *ymean, const float *ystd, const float *anchor,
-                                  const double *wa, SurScale s, double *out)
+__device__ __forceinline__ void tick_output(const float *y, const float *ymean, const float *ystd,
+                                            const float *anchor, const double *wa, const SurScale &s, double *out)
 {
-    if (threadIdx.x != 0) return;
     const float qa[4] = {anchor[3], anchor[4], anchor[5], anchor[6]};
     const float w = qa[0], x = qa[1], yq = qa[2], z = qa[3];
     const float R[9] = {1 - 2 * (yq * yq + z * z), 2 * (x * yq - w * z), 2 * (x * z + w * yq),
@@ -427,6 +427,180 @@ __global__ void k_sur_tick_output(const float *y, const float *ymean, const floa
             const float wv = R[3 * i] * b[0] + R[3 * i + 1] * b[1] + R[3 * i + 2] * b[2];
             out[3 * part + i] = wa[3 * part + i] + (double)wv * sc;
         }
+    }
+}
+
+__global__ void k_sur_tick_output(const float *y, const float *ymean, const float *ystd, const float *anchor,
+                                  const double *wa, SurScale s, double *out)
+{
+    if (threadIdx.x == 0) tick_output(y, ymean, ystd, anchor, wa, s, out);
+}
+
+// The whole haptic tick in one CTA of 128 threads: the tick's 269 inputs, the four layers as
+// tcgen05 MMAs with the activations kept on chip, and the wrench.  The input row sits in
+// row 0 of a 128-row BF16 A tile in shared memory (the other rows are zero), written in the
+// K-major 128-byte-swizzled layout the MMA descriptors expect (row 0 is not permuted by the
+// swizzle); each layer's weights arrive by TMA (the GEMM's tensor maps: 64-wide K chunks,
+// zero past K), the MMAs accumulate into TMEM, and the accumulator's row 0 (TMEM lane 0)
+// goes through the layer's bias and GELU, rounded to BF16, into the A tile for the next
+// layer.  The rounding points and operations are those of sph_mlp_forward; the result is
+// the anchor's wrench plus the de-standardised, rotated correction.
+struct TickArgs {
+    float t13[13];
+    float tau;
+    const float *anchor;
+    SurScale s;
+    const float *xmean, *xinv, *ymean, *ystd;
+    const float *b1, *b2, *b3, *b4;
+    const double *wa;
+    double *out;
+    unsigned *status;
+};
+constexpr int kTickChunk = kTcM * kTcKChunk * 2;              // one K chunk of a 128-row tile
+// A tile (5 chunks), W1 (5 chunks; W3 reuses it once layer 1 is done), W2 (2), W4 (2 chunks
+// of 16 rows), alignment, barriers
+constexpr int kTickW4 = kOutPad * kTcKChunk * 2;
+constexpr int kTickSmem = (5 + 5 + 2) * kTickChunk + 2 * kTickW4 + 1024 + 64;
+
+__global__ void __launch_bounds__(128, 1)
+    k_sur_tick_fused(const __grid_constant__ CUtensorMap m1, const __grid_constant__ CUtensorMap m2,
+                     const __grid_constant__ CUtensorMap m3, const __grid_constant__ CUtensorMap m4, TickArgs a)
+{
+    using namespace tcx;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ float s_v[kInPad];                 // the features, then each layer's row
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t A = (raw + 1023u) & ~1023u, W1 = A + 5u * kTickChunk, W2 = W1 + 5u * kTickChunk;
+    const uint32_t W4 = W2 + 2u * kTickChunk, bar = W4 + 2u * kTickW4;
+    // full[l]: layer l's weights have landed (one phase each); done: a layer's MMAs completed
+    const uint32_t done = bar + 32u;
+    auto full = [&](int l) { return bar + 8u * (uint32_t)l; };
+    unsigned char *Ap = smem_raw + (A - raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // element k of row 0 of the A tile: chunk k / 64, byte 2 (k % 64) of the row
+    auto put = [&](int k, float v) {
+        *reinterpret_cast<__nv_bfloat16 *>(Ap + (size_t)(k >> 6) * kTickChunk + 2 * (k & 63)) = __float2bfloat16_rn(v);
+    };
+    // rows 1-127 of the A tile are never written: they only feed rows 1-127 of the
+    // accumulator, which nothing reads
+    const CUtensorMap *maps[4] = {&m1, &m2, &m3, &m4};
+    const int nk[4] = {(kInPad + kTcKChunk - 1) / kTcKChunk, kHid / kTcKChunk, kHid / kTcKChunk, kHid / kTcKChunk};
+    const int nn[4] = {kHid, kHid, kHid, kOutPad};
+    const uint32_t wbase[4] = {W1, W2, W1, W4};
+    const uint32_t wstride[4] = {(uint32_t)kTickChunk, (uint32_t)kTickChunk, (uint32_t)kTickChunk, (uint32_t)kTickW4};
+    auto load_w = [&](int l) {
+        mbar_expect_tx(full(l), (uint32_t)(nk[l] * nn[l] * kTcKChunk * 2));
+        for (int c = 0; c < nk[l]; ++c) tma_load_2d(wbase[l] + (uint32_t)c * wstride[l], maps[l], c * kTcKChunk, 0, full(l));
+    };
+    if (tid == 0) {
+        s_fail = 0;
+        for (int l = 0; l < 4; ++l) mbar_init(full(l));
+        mbar_init(done);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        load_w(0);                                 // W1, W2 and W4 now; W3 into W1's place later
+        load_w(1);
+        load_w(3);
+    }
+    // the inputs, sur_features' arithmetic spread over the threads: thread k < 64 the
+    // descriptor cell k, thread 64 the pose and velocity part
+    {
+        const float *an = a.anchor;
+        const float qa[4] = {an[3], an[4], an[5], an[6]};
+        const float ih = 1.0f / a.s.h, ic = 1.0f / a.s.c, irho = 1.0f / a.s.rho0;
+        float d[3], o[3];
+        if (tid < 64) {
+            const float *cell = an + 13 + 4 * tid;
+            s_v[13 + 4 * tid] = cell[0] * irho - 1.0f;
+            for (int i = 0; i < 3; ++i) d[i] = cell[1 + i] * ic;
+            rot_t_apply(qa, d, o);
+            for (int i = 0; i < 3; ++i) s_v[14 + 4 * tid + i] = o[i];
+        } else if (tid == 64) {
+            for (int i = 0; i < 3; ++i) d[i] = (a.t13[i] - an[i]) * ih;
+            rot_t_apply(qa, d, o);
+            for (int i = 0; i < 3; ++i) s_v[i] = o[i];
+            s_v[3] = a.tau * a.s.c * ih;
+            for (int i = 0; i < 3; ++i) d[i] = (a.t13[7 + i] - an[7 + i]) * ic;
+            rot_t_apply(qa, d, o);
+            for (int i = 0; i < 3; ++i) s_v[4 + i] = o[i];
+            for (int i = 0; i < 3; ++i) d[i] = a.t13[7 + i] * ic;
+            rot_t_apply(qa, d, o);
+            for (int i = 0; i < 3; ++i) s_v[7 + i] = o[i];
+            for (int i = 0; i < 3; ++i) d[i] = a.t13[10 + i] * a.s.h * ic;
+            rot_t_apply(qa, d, o);
+            for (int i = 0; i < 3; ++i) s_v[10 + i] = o[i];
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(128));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = s_tmem;
+    // row 0 over all five K chunks (320 columns): the weights' zero fill past K = 272 meets
+    // zeros here, never stale shared memory
+    for (int k = tid; k < 5 * kTcKChunk; k += 128) put(k, k < kIn ? (s_v[k] - a.xmean[k]) * a.xinv[k] : 0.0f);
+
+    const float *bias[3] = {a.b1, a.b2, a.b3};
+    for (int l = 0; l < 4; ++l) {
+        // the A row written by the threads becomes visible to the tensor core
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0 && l == 1) load_w(2);          // layer 1's MMAs are done with W1
+        if (tid == 32) {
+            if (mbar_wait(full(l), 0u)) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t idesc = instr_desc(nn[l]);
+                for (int c = 0; c < nk[l]; ++c)
+#pragma unroll
+                    for (int j = 0; j < kTcKChunk / 16; ++j)
+                        mma_bf16(tmem, smem_desc_sw128(A + (uint32_t)c * kTickChunk + 32u * j),
+                                 smem_desc_sw128(wbase[l] + (uint32_t)c * wstride[l] + 32u * j), idesc,
+                                 (c > 0 || j > 0) ? 1u : 0u);
+            } else {
+                s_fail = 1;
+            }
+            mma_commit(done);                      // fires once the issued MMAs completed
+        }
+        __syncwarp();
+        if (!mbar_wait(done, (uint32_t)(l & 1))) s_fail = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (warp == 0) {
+            // row 0 of the accumulator is TMEM lane 0: lane 0 of warp 0
+            for (int c0 = 0; c0 < nn[l]; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + (uint32_t)c0, r);
+                if (lane == 0)
+                    for (int j = 0; j < 16; ++j) s_v[c0 + j] = __uint_as_float(r[j]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (l < 3) {
+            put(tid, gelu_f(s_v[tid] + bias[l][tid]));     // kHid = 128 = the threads
+        } else if (tid == 0) {
+            float y[kOut];
+            for (int j = 0; j < kOut; ++j) y[j] = s_v[j] + a.b4[j];
+            if (s_fail) {
+                if (a.status) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+            } else {
+                tick_output(y, a.ymean, a.ystd, a.anchor, a.wa, a.s, a.out);
+            }
+            // the model's status word rides along with the wrench (one copy to the host)
+            a.out[kOut] = a.status ? (double)*reinterpret_cast<volatile unsigned *>(a.status) : 0.0;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
     }
 }
 
@@ -461,6 +635,9 @@ struct sph_mlp {
     double *pin = nullptr;
     cudaEvent_t anchored = nullptr;
     bool has_anchor = false;
+    // the fused tick's TMA maps of the BF16 weights (built once; false: the unfused path)
+    CUtensorMap wmap[4];
+    bool tick_fused = false;
     std::string err;
 };
 
@@ -510,7 +687,7 @@ size_t mlp_sizes(int B, size_t *sz)
     sz[i++] = 4 * (size_t)kIn;                // anchor
     sz[i++] = 4 * (size_t)kIn;                // tick_x
     sz[i++] = 8 * (size_t)kOut;               // anchor_w
-    sz[i++] = 8 * (size_t)kOut;               // tick_w
+    sz[i++] = 8 * (size_t)(kOut + 2);         // tick_w (+ the status word)
     sz[i++] = 2 * (size_t)kHid * kHid;        // w2t
     sz[i++] = 2 * (size_t)kHid * kHid;        // w3t
     sz[i++] = 2 * (size_t)kHid * kOutPad;     // w4t
@@ -693,9 +870,13 @@ sph_status sph_mlp_create(void *d_workspace, size_t bytes, void *cuda_stream, in
     m->xbT = h(); m->h1T = h(); m->h2T = h(); m->h3T = h(); m->dybT = h();
     m->dz3T = h(); m->dz2T = h(); m->dz1T = h();
     m->ldt = ldt_of(max_batch);
+    m->tick_fused = tc_operand_map(&m->wmap[0], m->w1b, kHid, kInPad, kInPad, kHid) &&
+                    tc_operand_map(&m->wmap[1], m->w2b, kHid, kHid, kHid, kHid) &&
+                    tc_operand_map(&m->wmap[2], m->w3b, kHid, kHid, kHid, kHid) &&
+                    tc_operand_map(&m->wmap[3], m->w4b, kOutPad, kHid, kHid, kOutPad);
     cudaError_t e = cudaMemsetAsync(ws, 0, L.total, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-    if (e == cudaSuccess) e = cudaHostAlloc(&m->pin, 8 * kOut, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&m->pin, 8 * (kOut + 2), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&m->anchored, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (m->pin) cudaFreeHost(m->pin);
@@ -877,16 +1058,55 @@ sph_status sph_surrogate_tick(sph_mlp *m, const float pose_vel[13], float elapse
     if (!m || !pose_vel || !out || !(elapsed >= 0.0f)) return SPH_ERR_ARG;
     if (!m->has_anchor) return mfail(m, SPH_ERR_STATE, "no anchor: call sph_surrogate_anchor first");
     const float *t = pose_vel;
-    k_sur_tick_features<<<1, 32, 0, m->stream>>>(t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9],
-                                                 t[10], t[11], t[12], elapsed, m->anchor, m->scale, m->tick_x);
-    MLP_CUDA(m, cudaGetLastError());
-    sph_status st = mlp_forward(m, m->tick_x, 1, false);
-    if (st != SPH_OK) return st;
     const float *ymean = m->norm + 2 * kIn, *ystd = m->norm + 2 * kIn + kOut;
-    k_sur_tick_output<<<1, 32, 0, m->stream>>>(m->y, ymean, ystd, m->anchor, m->anchor_w, m->scale, m->tick_w);
-    MLP_CUDA(m, cudaGetLastError());
-    MLP_CUDA(m, cudaMemcpyAsync(m->pin, m->tick_w, 8 * kOut, cudaMemcpyDeviceToHost, m->stream));
-    st = mlp_status(m);                         // synchronises the model's stream
+    if (m->tick_fused) {
+        // one kernel: inputs, the four layers on the tensor cores, the wrench
+        static bool configured = false;
+        if (!configured) {
+            MLP_CUDA(m, cudaFuncSetAttribute(k_sur_tick_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kTickSmem));
+            configured = true;
+        }
+        TickArgs a;
+        for (int i = 0; i < 13; ++i) a.t13[i] = t[i];
+        a.tau = elapsed;
+        a.anchor = m->anchor;
+        a.s = m->scale;
+        a.xmean = m->norm;
+        a.xinv = m->norm + kIn;
+        a.ymean = ymean;
+        a.ystd = ystd;
+        a.b1 = m->master + kOffB1;
+        a.b2 = m->master + kOffB2;
+        a.b3 = m->master + kOffB3;
+        a.b4 = m->b4pad;
+        a.wa = m->anchor_w;
+        a.out = m->tick_w;
+        a.status = m->status;
+        k_sur_tick_fused<<<1, 128, kTickSmem, m->stream>>>(m->wmap[0], m->wmap[1], m->wmap[2], m->wmap[3], a);
+        MLP_CUDA(m, cudaGetLastError());
+    } else {
+        k_sur_tick_features<<<1, 32, 0, m->stream>>>(t[0], t[1], t[2], t[3], t[4], t[5], t[6], t[7], t[8], t[9],
+                                                     t[10], t[11], t[12], elapsed, m->anchor, m->scale, m->tick_x);
+        MLP_CUDA(m, cudaGetLastError());
+        sph_status st = mlp_forward(m, m->tick_x, 1, false);
+        if (st != SPH_OK) return st;
+        k_sur_tick_output<<<1, 32, 0, m->stream>>>(m->y, ymean, ystd, m->anchor, m->anchor_w, m->scale, m->tick_w);
+        MLP_CUDA(m, cudaGetLastError());
+    }
+    sph_status st;
+    if (m->tick_fused) {
+        // the wrench and the status word in one copy
+        MLP_CUDA(m, cudaMemcpyAsync(m->pin, m->tick_w, 8 * (kOut + 1), cudaMemcpyDeviceToHost, m->stream));
+        MLP_CUDA(m, cudaStreamSynchronize(m->stream));
+        st = SPH_OK;
+        if (m->pin[kOut] != 0.0) {
+            MLP_CUDA(m, cudaMemsetAsync(m->status, 0, 4, m->stream));
+            st = mfail(m, SPH_ERR_TIMEOUT, "a tensor-core completion wait gave up");
+        }
+    } else {
+        MLP_CUDA(m, cudaMemcpyAsync(m->pin, m->tick_w, 8 * kOut, cudaMemcpyDeviceToHost, m->stream));
+        st = mlp_status(m);                     // synchronises the model's stream
+    }
     if (st != SPH_OK) return st;
     std::memcpy(out, m->pin, 8 * kOut);
     return SPH_OK;

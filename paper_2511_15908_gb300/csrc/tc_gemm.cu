@@ -4,92 +4,19 @@
 
 #include "sph_internal.cuh"
 #include "tc_gemm.cuh"
+#include "tc_ptx.cuh"
 
 namespace sphgb {
 
 namespace {
+
+using namespace tcx;
 
 constexpr int kStageA = kTcM * kTcKChunk * 2;          // 16 KB: 128 rows x 128 B
 constexpr int kStageB = kTcMaxN * kTcKChunk * 2;       // 32 KB: up to 256 rows x 128 B
 constexpr int kStageBytes = kStageA + kStageB;
 // the ring, 1 KB of slack to align it to the 1024-byte swizzle period, and the barriers
 constexpr int kSmemBytes = kTcStages * kStageBytes + 1024 + 256;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor of a K-major operand written by TMA with the 128-byte
-// swizzle: rows of 128 bytes (64 BF16 of K), 8-row groups 1024 bytes apart (SBO); the
-// leading-byte offset is unused for a swizzled K-major operand whose K step stays inside
-// one 128-byte row (encoded as 1); descriptor version 1 (bit 46); swizzle mode 2 = 128 B.
-// The K = 16 steps inside a chunk advance the start address by 32 bytes: the hardware
-// applies the swizzle to the absolute address bits, so the offset composes with it.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
-    d |= (uint64_t)1u << 46;
-    d |= (uint64_t)2u << 61;
-    return d;
-}
-
-// Instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major, N, M = 128.
-__device__ __forceinline__ uint32_t instr_desc(int n)
-{
-    uint32_t d = 0;
-    d |= 1u << 4;                          // D format: F32
-    d |= 1u << 7;                          // A format: BF16
-    d |= 1u << 10;                         // B format: BF16
-    d |= (uint32_t)(n >> 3) << 17;         // N / 8
-    d |= (uint32_t)(kTcM >> 4) << 24;      // M / 16
-    return d;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(addr));
-}
-
-// Bounded wait for the completion of the phase with the given parity; false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity)
-{
-    for (unsigned it = 0; it < kTcSpin; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes) : "memory");
-}
-
-// 2-D tiled TMA load of the box at (x = k, y = row) into shared memory, completing on mbar.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-                 : "memory");
-}
 
 // The fused per-element operation of one accumulator value at (row, col); returns the value
 // the transposed copy (if any) receives.
@@ -332,9 +259,11 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
+}  // namespace
+
 // Tensor map of a K-contiguous BF16 operand [rows][K] (leading dimension ld elements): boxes
 // of 64 K x box_rows rows with the 128-byte swizzle; out-of-range elements read as zero.
-bool operand_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K, int ld, int box_rows)
+bool tc_operand_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K, int ld, int box_rows)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
@@ -351,6 +280,8 @@ bool operand_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K, int 
 // kTcMinCtas CTAs (row tiles x column tiles x K slices).  These GEMMs are small: a CTA's
 // epilogue (one thread per row, one warp per SM sub-partition) is latency bound, so more,
 // narrower tiles finish sooner than few wide ones; A is re-read from L2 per column tile.
+namespace {
+
 int ntile_of(const TcGemm &g, int slices)
 {
     const int mt = (g.M + kTcM - 1) / kTcM;
@@ -394,7 +325,7 @@ cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s)
     const int ntile = ntile_of(g, slices);
     const int box_b = ntile;
     CUtensorMap ma, mb;
-    if (!operand_map(&ma, g.A, g.M, g.K, g.lda, kTcM) || !operand_map(&mb, g.B, g.N, g.K, g.ldb, box_b))
+    if (!tc_operand_map(&ma, g.A, g.M, g.K, g.lda, kTcM) || !tc_operand_map(&mb, g.B, g.N, g.K, g.ldb, box_b))
         return cudaErrorInvalidValue;
     dim3 grid((g.M + kTcM - 1) / kTcM, (g.N + ntile - 1) / ntile, slices);
     k_tc_gemm<<<grid, kTcThreads, kSmemBytes, s>>>(ma, mb, g, ntile, box_b, cps);

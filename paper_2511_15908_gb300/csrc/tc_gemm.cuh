@@ -27,6 +27,7 @@
 // partial sum to C + z * split_stride, and the caller sums the slices in a fixed order.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -81,6 +82,11 @@ __device__ __forceinline__ float gelu_grad_f(float z)
     float t = tanhf(c * (z + a * z * z * z));
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * c * (1.0f + 3.0f * a * z * z);
 }
+
+// Tensor map of a K-contiguous BF16 operand [rows][K] (leading dimension ld elements, a
+// multiple of 8; 16-byte aligned base) for TMA boxes of 64 K x box_rows rows with the
+// 128-byte swizzle, elements past rows / K reading as zero; false if the driver refuses it.
+bool tc_operand_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K, int ld, int box_rows);
 
 // Number of K slices tc_gemm writes for g (1 without a split): the caller sums this many.
 int tc_gemm_splits(const TcGemm &g);

@@ -1061,11 +1061,8 @@ sph_status sph_surrogate_tick(sph_mlp *m, const float pose_vel[13], float elapse
     const float *ymean = m->norm + 2 * kIn, *ystd = m->norm + 2 * kIn + kOut;
     if (m->tick_fused) {
         // one kernel: inputs, the four layers on the tensor cores, the wrench
-        static bool configured = false;
-        if (!configured) {
-            MLP_CUDA(m, cudaFuncSetAttribute(k_sur_tick_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, kTickSmem));
-            configured = true;
-        }
+        static std::atomic<unsigned long long> configured{0};
+        MLP_CUDA(m, smem_opt_in(k_sur_tick_fused, kTickSmem, configured));
         TickArgs a;
         for (int i = 0; i < 13; ++i) a.t13[i] = t[i];
         a.tau = elapsed;

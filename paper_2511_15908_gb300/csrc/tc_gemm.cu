@@ -310,11 +310,10 @@ int tc_gemm_splits(const TcGemm &g)
 
 cudaError_t tc_gemm(const TcGemm &g, cudaStream_t s)
 {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    static std::atomic<unsigned long long> configured{0};
+    {
+        cudaError_t e = smem_opt_in(k_tc_gemm, kSmemBytes, configured);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
     if (!g.A || !g.B || (g.lda & 7) || (g.ldb & 7) || g.lda < g.K || g.ldb < g.K ||

@@ -26,6 +26,7 @@
 // A K split (ksplit > 1, TC_STORE only) spreads the chunks over grid.z; CTA z writes its
 // partial sum to C + z * split_stride, and the caller sums the slices in a fixed order.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -87,6 +88,21 @@ __device__ __forceinline__ float gelu_grad_f(float z)
 // multiple of 8; 16-byte aligned base) for TMA boxes of 64 K x box_rows rows with the
 // 128-byte swizzle, elements past rows / K reading as zero; false if the driver refuses it.
 bool tc_operand_map(CUtensorMap *map, const __nv_bfloat16 *p, int rows, int K, int ld, int box_rows);
+
+// Opt a kernel into `bytes` of dynamic shared memory on the current device, once per device
+// (the attribute is per device; `done` remembers the devices, up to 64, already set).
+template <class Kernel>
+inline cudaError_t smem_opt_in(Kernel *kernel, int bytes, std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load() & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit);
+    return e;
+}
 
 // Number of K slices tc_gemm writes for g (1 without a split): the caller sums this many.
 int tc_gemm_splits(const TcGemm &g);

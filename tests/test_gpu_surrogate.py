@@ -41,9 +41,14 @@ def test_forward_matches_oracle(sph):
     y = m.forward(torch.tensor(X, device="cuda"))
     m.sync()
     ref = omlp.forward(params, norm, X, bf=True)
-    got = y.cpu().numpy()
-    scale = np.abs(ref).max()
-    assert np.abs(got - ref).max() <= 2e-3 * scale, np.abs(got - ref).max() / scale
+    got = y.cpu().numpy().astype(np.float64)
+    # element by element, per output: both sides round to BF16 at the same points, so they
+    # differ where an FP32 tensor-core sum and the FP64 sum round an activation to
+    # neighbouring BF16 numbers (one unit: 2^-8 relative)
+    rms = np.sqrt(np.mean(ref * ref, axis=0))
+    ratio = np.abs(got - ref) / (2.0 ** -6 * np.abs(ref) + 2.0 ** -8 * rms)
+    print(f"max |dy| / (2^-6 |y| + 2^-8 rms) = {ratio.max():.3f}")
+    assert ratio.max() <= 1.0, ratio.max()
     m.close()
 
 

@@ -203,6 +203,14 @@ def test_tait_eos_coupled_reduced(sph):
     check_one_substep(sph, sc, mode=1)
 
 
+def test_tait_eos_full_size_record_mode(sph):
+    # the Tait equation of state on the full coupled scene through the packed density pass
+    # and the 512-thread instance: neighbour counts bit-exact, every acceleration in the bar
+    sc = scenes.with_velocity_noise(scenes.coupled(seed=0, n_substeps=10), seed=17, sigma=0.2)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_TAIT)
+    check_one_substep(sph, sc, mode=1, record=True)
+
+
 def test_volume_boundaries_dam_break_grabbed_cube(sph):
     sc = scenes.with_velocity_noise(scenes.dam_break(seed=3, grab=True, cube_pos=(0.4, 0.4, 0.2)),
                                     seed=13, sigma=0.3)

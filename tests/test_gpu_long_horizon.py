@@ -9,7 +9,9 @@
 - fluid and a released buoyant cube in a closed tank, undriven, never gain mechanical energy
   over 3000 substeps;
 - a stirred coupled scene with a soft body stays finite, with at most a few spray particles
-  leaving the domain.
+  leaving the domain;
+- the full coupled scene the benchmark times (about 1.05 M particles) keeps every particle
+  inside the grid domain over 1000 substeps.
 """
 import numpy as np
 import pytest
@@ -138,5 +140,21 @@ def test_stirred_coupled_scene_stays_finite(sph):
     assert np.all(np.isfinite(st["x"])) and np.all(np.isfinite(st["v"]))
     outside = ~(np.all(st["x"] >= lo, axis=1) & np.all(st["x"] <= hi, axis=1))
     assert outside.mean() < 1e-3
+    assert np.all(np.isfinite(sim.grab_wrench(smoothed=True)))
+    sim.close()
+
+
+def test_benchmark_coupled_scene_keeps_every_particle_over_its_horizon(sph):
+    # the full coupled scene bench.py times (settled fill, probe on its random walk) over
+    # 1000 substeps: no particle leaves the grid domain (the status word would report it),
+    # the state stays finite and slow, and the wrench stays finite
+    sc = scenes.coupled(seed=0, n_substeps=1000)
+    sim = sph.Simulation(sc)
+    for _ in range(10):
+        sim.step(100)
+        sim.sync()                                   # raises on any out-of-domain report
+    st = sim.state()
+    assert np.all(np.isfinite(st["x"])) and np.all(np.isfinite(st["v"]))
+    assert np.linalg.norm(st["v"][:sc.n_fluid], axis=1).max() < 1.0
     assert np.all(np.isfinite(sim.grab_wrench(smoothed=True)))
     sim.close()

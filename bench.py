@@ -522,14 +522,20 @@ def size_sweep_form(args, flush_l2_factory, sc_main):
     """Substep time against particle count (the paper relates particle count to frame rate):
     the dam break (4,096 fluid), the stirring tank (250k fluid) and the coupled scene (1M
     fluid), each 10 warm-up and 50 timed substeps with an L2 flush before each, CUDA events
-    on the simulation's stream."""
+    on the simulation's stream; the two small scenes also with the low-latency density pass
+    (SPH_FLAG_LOW_LATENCY), and a compact stirring scene (369 fluid, 4,821 particles)."""
     import torch
     from paper_2511_15908_gb300 import scenes, sph
     out = {}
-    for name, sc in (("dam_break_4k", scenes.dam_break(seed=0)),
-                     ("stirring_250k", scenes.stirring_tank(seed=0, n_substeps=64)),
-                     ("coupled_1M", sc_main)):
-        sim = sph.Simulation(sc)
+    compact = scenes.batched(seed=4, n_scenes=1, lo=100, hi=400, compact=True, n_substeps=64)[0]
+    ll = sph.FLAG_LOW_LATENCY
+    for name, sc, extra in (("dam_break_4k", scenes.dam_break(seed=0), 0),
+                            ("dam_break_4k_low_latency", scenes.dam_break(seed=0), ll),
+                            ("compact_stirring_369", compact, 0),
+                            ("compact_stirring_369_low_latency", compact, ll),
+                            ("stirring_250k", scenes.stirring_tank(seed=0, n_substeps=64), 0),
+                            ("coupled_1M", sc_main, 0)):
+        sim = sph.Simulation(sc, flags=sc.params["flags"] | extra)
         flush = flush_l2_factory(sim.stream)
         domain = [0]
         for _ in range(10):
@@ -651,6 +657,8 @@ def run_ours(args):
     from paper_2511_15908_gb300 import build, sph
     build.build()
     sc = _workload(args.workload, args.fluid)
+    if args.low_latency:
+        sc.params = dict(sc.params, flags=sc.params["flags"] | sph.FLAG_LOW_LATENCY)
     peaks, peak_kind = _peaks()
 
     # first substep with the record flag: accelerations for the parity figure against the
@@ -732,7 +740,7 @@ def run_ours(args):
         achieved = flops / t_dom / 1e12
         roofline = {"bound": "alu", "kernel": dom_name, "achieved": achieved, "peak": alu_peak,
                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                    "traffic": _traffic(dom_name),
+                    "traffic": None if args.low_latency else _traffic(dom_name),
                     "flops_per_pair": (DENSITY_FLOPS_PER_PAIR if dom_name == "density"
                                        else FORCE_FLOPS_PER_PAIR),
                     "pairs_per_launch": pairs if dom_name == "density" else pairs - n_all,
@@ -745,7 +753,7 @@ def run_ours(args):
         achieved = bytes_ / t_dom / 1e9
         roofline = {"bound": "hbm", "kernel": dom_name, "achieved": achieved,
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                    "traffic": _traffic(dom_name)}
+                    "traffic": None if args.low_latency else _traffic(dom_name)}
     force_hbm = FORCE_BYTES_PER_PARTICLE * n_all / (kmean[6] / 1e3) / 1e9
     density_hbm = DENSITY_BYTES_PER_PARTICLE * n_all / (kmean[5] / 1e3) / 1e9
     step_hbm = BYTES_PER_PARTICLE_STEP * n_all / (ms_per_step / 1e3) / 1e9
@@ -841,7 +849,9 @@ def run_ours(args):
                            "regime": f"stirred: timed after {SPIN_UP_SUBSTEPS + 1 + args.warmup} "
                                      "untimed substeps of the probe's random walk from the "
                                      "settled fill",
-                           "out_of_domain_reports": domain[0]},
+                           "out_of_domain_reports": domain[0],
+                           "density_pass": ("low latency: 32 or 16 threads per particle"
+                                            if args.low_latency else "one thread per particle")},
                 "gpu_launches": 8 * args.steps,
                 "kernel_ms": {k: float(v) for k, v in zip(sph.KERNELS, kmean)},
                 "kernel_share": shares,
@@ -876,6 +886,8 @@ def main():
     ap.add_argument("--workload", default="coupled", choices=["coupled", "stirring", "dam_break"])
     ap.add_argument("--fluid", type=int, default=0,
                     help="coupled scene on a shorter tank with this many fluid particles (profiling)")
+    ap.add_argument("--low-latency", action="store_true",
+                    help="run the workload with SPH_FLAG_LOW_LATENCY (small scenes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / surrogate forms")
     ap.add_argument("--sur-substeps", type=int, default=32000)

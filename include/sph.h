@@ -65,7 +65,7 @@ enum {
                                           Sec. 3.1 names as the alternative to Eq. pressure:
                                           p = B ((rho / rho0)^7 - 1), B = k rho0 / 7 (the
                                           same slope as k (rho - rho0) at rest) */
-    SPH_FLAG_VOLUME_BOUNDARY = 1u << 4 /* volume-based boundary particles (Akinci et al., whose
+    SPH_FLAG_VOLUME_BOUNDARY = 1u << 4,/* volume-based boundary particles (Akinci et al., whose
                                           coupling Sec. 2.1 cites): a static or rigid
                                           particle b weighs psi_b = rho0 / sum_{k boundary}
                                           W_bk instead of its mass in the density of fluid
@@ -75,6 +75,21 @@ enum {
                                           force; boundary particles exert no SPH force on
                                           each other; sph_get_state reports psi_b as a
                                           boundary particle's density */
+    SPH_FLAG_LOW_LATENCY = 1u << 5     /* the density pass (Alg. 1's density loop) takes 32
+                                          (scenes up to 20,000 particles) or 16
+                                          cooperating threads per particle instead of one:
+                                          for scenes too small to fill the GPU, whose
+                                          substep waits for the serial neighbour loop of
+                                          their half-spacing body particles (~226
+                                          neighbours each).  Same neighbours, neighbour
+                                          counts and interaction lists; the densities'
+                                          float-pair sums are added in another order, so
+                                          the FP32 excess rho - rho0 may round to the
+                                          neighbouring value.  Slower on a
+                                          scene that fills the GPU.  No effect with
+                                          SPH_FLAG_VOLUME_BOUNDARY or inside a batch
+                                          (sph_batch_*), which runs one thread per
+                                          particle */
 };
 
 /* Body kinds (Sec. 3.2 particle types). */

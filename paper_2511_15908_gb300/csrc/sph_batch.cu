@@ -402,6 +402,10 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
         if (st != SPH_OK) return st;
         // a small reduction grid per scene: many scenes already fill the GPU
         table[s].n_wgrid = std::max(table[s].n_wblocks, 4);
+        // every structure runs one thread per particle in the density pass, so that all of
+        // them give the same results (a batch fills the GPU; the low-latency pass is not
+        // what it needs)
+        table[s].flags &= ~FLAG_LOW_LATENCY;
     }
     sph_batch *b = new sph_batch();
     b->n = n_scenes;

@@ -31,7 +31,8 @@ constexpr int kTile = 256;     // threads per block = particles per tile
 
 
 constexpr int KIND_STATIC = 1, KIND_RIGID = 2, KIND_SOFT = 3;
-constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u, FLAG_TAIT = 8u, FLAG_VOLUME = 16u;
+constexpr uint32_t FLAG_CLAMP = 1u, FLAG_RECORD = 2u, FLAG_TAIT = 8u, FLAG_VOLUME = 16u,
+                   FLAG_LOW_LATENCY = 32u;
 
 // ------------------------------------------------------------------ small helpers
 
@@ -1059,18 +1060,20 @@ __device__ __forceinline__ void density_item(const SimConst &c, int blk)
     else density_item_v<false, THREADS, PAIRED>(c, blk, s_pend);
 }
 
-#if SPH_DENSITY_COOP
-// Alternative density pass, built only with -DSPH_DENSITY_COOP=G (G = 4, 8, 16 or 32) and
-// SPH_DENSITY_COOP_MINB: G cooperating lanes per particle (mass boundaries).  The lanes of
-// a group set up the particle's clipped rows of cells together, test the flattened
-// candidates G at a time (ascending slots, the order of the row walk), queue the
-// neighbours in shared memory and evaluate them G at a time, one neighbour per lane, each
-// lane summing its float-pair share; a shuffle tree of TwoSums adds the lanes' shares.
-// Same neighbours, same neighbour list (in the same order) as density_item_v; the density
-// sum, exact to ~1e-13 in any order, may round differently in its last bit.  Measured
-// against the one-thread-per-particle walk on the stirred coupled scene and rejected
-// (2.1x slower at best, G = 8): the group's set-up, compaction and queue round trips cost
-// more than the lanes it keeps busy.
+// Low-latency density pass (SPH_FLAG_LOW_LATENCY; mass boundaries): G cooperating lanes
+// per particle.  The lanes of a group set up the particle's clipped rows of cells together,
+// test the flattened candidates G at a time (ascending slots, the order of the row walk),
+// queue the neighbours in shared memory and evaluate them G at a time, one neighbour per
+// lane, each lane summing its float-pair share; a shuffle tree of TwoSums adds the lanes'
+// shares.  Same neighbours, same neighbour list (in the same order) and the same counts as
+// density_item_v; the density sum, exact to ~1e-13 in any order, may round differently in
+// its last bit.  A scene too small to fill the GPU waits for its slowest particles: a body
+// sampled at half spacing has ~226 neighbours, which one thread walks and evaluates in
+// series, and splitting them over G lanes shortens that chain (measured: the dam break's
+// density pass 129 -> 25 us at G = 32).  On a scene that fills the GPU the group's set-up,
+// compaction and queue round trips cost more than the lanes it keeps busy (the stirred
+// coupled scene: 2.1x slower at best, G = 8; the 250k stirring tank 234 -> 387 us at G =
+// 16), so the flag is for small interactive scenes.
 template <int G>
 __device__ __forceinline__ void density_coop_item(const SimConst &c, int blk)
 {
@@ -1220,7 +1223,6 @@ __device__ __forceinline__ void density_coop_item(const SimConst &c, int blk)
         report(c, bad);
     }
 }
-#endif
 
 #if SPH_DENSITY_BRICK
 // Alternative density pass, built only with -DSPH_DENSITY_BRICK=1 (and SPH_BRICK_X/Y/Z/CAP):

@@ -19,6 +19,15 @@
 #define SPH_FORCE_MINB 4
 #endif
 constexpr int kDensityWideMin = 300000;   // ~ 2 x 152 SMs x 2 blocks x 512 threads
+// Low-latency density pass (SPH_FLAG_LOW_LATENCY): G lanes per particle, 32 up to
+// kLowLatency32Max particles, else 16.  Measured (density pass, us) on the dam break (12k
+// particles) / a compact stirring tank (4.8k) / the coupled scene with 60k fluid (83k):
+// one thread 129 / 94 / 154; G = 4: 148 / 81 / 205; G = 8: 67 / 37 / 109; G = 16: 34 / 22
+// / 94; G = 32: 25 / 16 / 111 (4 resident blocks; 3 and 2 the same).
+#ifndef SPH_LOW_LATENCY_MINB
+#define SPH_LOW_LATENCY_MINB 4
+#endif
+constexpr int kLowLatency32Max = 20000;
 
 namespace sphgb {
 
@@ -32,12 +41,11 @@ __global__ void __launch_bounds__(SPH_DENSITY_THREADS, SPH_DENSITY_MINB) k_densi
     density_item<SPH_DENSITY_THREADS>(c, blockIdx.x);
 }
 __global__ void __launch_bounds__(kTile, 4) k_density_narrow(SimConst c) { density_item<kTile>(c, blockIdx.x); }
-#if SPH_DENSITY_COOP
-__global__ void __launch_bounds__(kTile, SPH_DENSITY_COOP_MINB) k_density_coop(SimConst c)
+template <int G>
+__global__ void __launch_bounds__(kTile, SPH_LOW_LATENCY_MINB) k_density_coop(SimConst c)
 {
-    density_coop_item<SPH_DENSITY_COOP>(c, blockIdx.x);
+    density_coop_item<G>(c, blockIdx.x);
 }
-#endif
 #if SPH_DENSITY_BRICK
 __global__ void __launch_bounds__(kBrickThreads, 2) k_density_brick(SimConst c)
 {
@@ -122,11 +130,12 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
                           sizeof(BrickShared), s>>>(c);
     else
 #endif
-#if SPH_DENSITY_COOP
-    if (c.n >= kDensityWideMin && !(c.flags & FLAG_VOLUME) && c.Rc < 2.5f)
-        k_density_coop<<<(unsigned)(((long long)c.n * SPH_DENSITY_COOP + kTile - 1) / kTile), kTile, 0, s>>>(c);
+    // the group's rows fit its 6 x 6 table while Rc < 2.5 (cells >= h give Rc ~ 2)
+    if ((c.flags & FLAG_LOW_LATENCY) && !(c.flags & FLAG_VOLUME) && c.Rc < 2.5f && c.n <= kLowLatency32Max)
+        k_density_coop<32><<<(unsigned)(((long long)c.n * 32 + kTile - 1) / kTile), kTile, 0, s>>>(c);
+    else if ((c.flags & FLAG_LOW_LATENCY) && !(c.flags & FLAG_VOLUME) && c.Rc < 2.5f)
+        k_density_coop<16><<<(unsigned)(((long long)c.n * 16 + kTile - 1) / kTile), kTile, 0, s>>>(c);
     else
-#endif
     if (c.n >= kDensityWideMin)
         k_density<<<blocks_for(c.n, SPH_DENSITY_THREADS), SPH_DENSITY_THREADS, 0, s>>>(c);
     else

@@ -22,6 +22,7 @@ CHECKED_LIB_PATH = os.path.join(_HERE, "libsph_gb300_checked.so")
 OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_CAPACITY, ERR_NONFINITE, ERR_DOMAIN, ERR_TIMEOUT, \
     ERR_STATE, ERR_BOUNDS = range(10)
 FLAG_CLAMP_PRESSURE, FLAG_RECORD, FLAG_NO_GRAPH, FLAG_TAIT, FLAG_VOLUME_BOUNDARY = 1, 2, 4, 8, 16
+FLAG_LOW_LATENCY = 32
 BODY_STATIC, BODY_RIGID, BODY_SOFT = 1, 2, 3
 
 # Every symbol the header declares (checked by the CPU test suite).

@@ -165,7 +165,7 @@ def _workload(name, fluid=None):
     if name == "stirring":
         return scenes.stirring_tank(seed=0, n_substeps=4096)
     if name == "dam_break":
-        return scenes.dam_break(seed=0, n_substeps=4096)
+        return scenes.dam_break(seed=0, n_substeps=4096, grab=True)   # the cube on a grab path
     raise ValueError(name)
 
 

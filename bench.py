@@ -778,8 +778,9 @@ def run_ours(args):
                 raise
             domain[0] += 1
         e2e_s += time.perf_counter() - t0
-    if (domain[0] or rec_domain[0]) and not args.fluid:
+    if (domain[0] or rec_domain[0]) and args.workload == "coupled" and not args.fluid:
         # a particle left the grid domain: the workload is not the one this line describes
+        # (the other workloads splash by design -- the dam break's jet -- and report the count)
         raise RuntimeError(f"{domain[0] + rec_domain[0]} out-of-domain reports during the run")
     e2e_s = max_over_ranks(e2e_s)
     e2e_value = job_rate(sc.n_fluid * args.steps, world, e2e_s)

@@ -77,15 +77,16 @@ enum {
                                           boundary particle's density */
     SPH_FLAG_LOW_LATENCY = 1u << 5     /* the density pass (Alg. 1's density loop) takes 32
                                           (scenes up to 20,000 particles) or 16
-                                          cooperating threads per particle instead of one:
+                                          cooperating threads per particle instead of one,
+                                          and the force pass 8:
                                           for scenes too small to fill the GPU, whose
                                           substep waits for the serial neighbour loop of
                                           their half-spacing body particles (~226
                                           neighbours each).  Same neighbours, neighbour
                                           counts and interaction lists; the densities'
-                                          float-pair sums are added in another order, so
-                                          the FP32 excess rho - rho0 may round to the
-                                          neighbouring value.  Slower on a
+                                          float-pair sums and the forces' FP32 sums are
+                                          added in another order, so they may round to
+                                          neighbouring values.  Slower on a
                                           scene that fills the GPU.  No effect with
                                           SPH_FLAG_VOLUME_BOUNDARY or inside a batch
                                           (sph_batch_*), which runs one thread per

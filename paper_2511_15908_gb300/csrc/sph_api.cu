@@ -69,6 +69,9 @@ Layout make_layout(const sph_params &p, const sph_capacity &cap)
     const size_t N = (size_t)std::max(cap.max_particles, 1);
     L.max_wblocks = (int)((N + kReduceChunk - 1) / kReduceChunk) + kMaxBodies;
     L.max_force_blocks = (int)((N + 255) / 256);
+    // the low-latency force pass writes a diagnostic row per block of 256 / G particles
+    if ((p.flags & SPH_FLAG_LOW_LATENCY) && !(p.flags & SPH_FLAG_VOLUME_BOUNDARY))
+        L.max_force_blocks = (int)((N * kLowLatencyForceG + 255) / 256);
     const int W = std::max(p.smooth_window, 1);
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t r = off; off = align256(off + bytes); return r; };
@@ -229,6 +232,8 @@ sph_status finalize(sph_handle *h)
     c.nb = (int)h->bodies.size();
     c.n_body_particles = n - c.nf;
     c.n_force_blocks = (n + 255) / 256;
+    if ((h->p.flags & SPH_FLAG_LOW_LATENCY) && !(h->p.flags & SPH_FLAG_VOLUME_BOUNDARY))
+        c.n_force_blocks = (int)(((long long)n * kLowLatencyForceG + 255) / 256);
     for (int b = 0; b < kMaxBodies; ++b) {
         c.body_end[b] = b < c.nb ? h->bodies[b].first + h->bodies[b].n : n;
         c.body_kind[b] = b < c.nb ? h->bodies[b].kind : 0;

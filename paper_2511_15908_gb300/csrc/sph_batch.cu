@@ -406,6 +406,7 @@ sph_status sph_batch_create(sph_handle *const *scenes, int32_t n_scenes, void *d
         // them give the same results (a batch fills the GPU; the low-latency pass is not
         // what it needs)
         table[s].flags &= ~FLAG_LOW_LATENCY;
+        table[s].n_force_blocks = (table[s].n + 255) / 256;
     }
     sph_batch *b = new sph_batch();
     b->n = n_scenes;

@@ -1703,6 +1703,196 @@ __device__ __forceinline__ void force_item(const SimConst &c, int blk)
     else force_item_v<false>(c, blk);
 }
 
+// Low-latency force pass (SPH_FLAG_LOW_LATENCY; mass boundaries): G cooperating lanes per
+// particle, for scenes too small to fill the GPU, whose force pass waits for the serial
+// partner loop of each fluid particle (~37 partners, two dependent loads each).  Lane l of a
+// group evaluates partners l, l + G, ... of the particle's list (or, past the list's
+// capacity, every G-th candidate of the row walk) with the pair terms of force_item_v; a
+// fixed shuffle tree adds the lanes' FP32 sums and, by TwoSums, their float-pair kernel-
+// gradient sums; lane 0 then does the springs, the integration, the writes and the
+// diagnostics.  The same forces up to the order of the FP32 sums.  The grid has G blocks
+// for each 256 particles, each writing its own diagnostic row (n_force_blocks is set to
+// match for flagged scenes).
+template <int G>
+__device__ __forceinline__ void force_coop_item(const SimConst &c, int blk)
+{
+    __shared__ double sd[8][8];
+    __shared__ unsigned s_done;
+    if (threadIdx.x == 0) s_done = 0u;
+    __syncthreads();
+    constexpr int kGroups = kTile / G;
+    const int l = threadIdx.x % G;
+    const int gbase = (threadIdx.x & 31) & ~(G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << gbase;
+    const int p = blk * kGroups + (int)threadIdx.x / G;
+    float dg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t bad = 0;
+    if (p < c.n) {                                   // group-uniform
+        const float4 xi = c.xA[p];
+        const float4 vi = c.vA[p];
+        const float2 pi = c.prho[p];
+        const int id = __float_as_int(vi.w);
+        const float mi = fabsf(xi.w);
+        int kind, excl_lo, excl_n;
+        pair_scope(c, id, kind, excl_lo, excl_n);
+        const bool skip = (kind == KIND_STATIC) && !(c.flags & FLAG_RECORD);
+        const bool near0 = near_origin_planes(c, xi);
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        PairGradSum Gs;
+        if (!skip) {
+            auto pair = [&](float4 xj, float4 vj, float2 pj, float dx, float dy, float dz, float r2,
+                            bool check_own) {
+                const int jd = __float_as_int(vj.w);
+                if (check_own && (unsigned)(jd - excl_lo) < (unsigned)excl_n) return;
+                float r2x, lx, ly, lz;
+                pair_offset(xi, xj, near0, dx, dy, dz, r2x, lx, ly, lz);
+                const PairQ pq = pair_q(c, dx, dy, dz, r2x);
+                float gl;
+                const float gq = gradq_pair(pq.qh, pq.ql, gl);
+                const float vx = -((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz);
+                const float mj = fabsf(xj.w);
+                const float visc = __fdividef(c.nu20 * vx, (pi.x + pj.x) * (r2 + c.eps_h2));
+                const float coef = mj * (visc - __fsub_rn(pj.y, pi.y)) * gq;
+                Gs.add(__fmul_rn(2.0f, mj), gq, gl, dx, dy, dz, lx, ly, lz);
+                ax -= coef * dx;
+                ay -= coef * dy;
+                az -= coef * dz;
+            };
+            const int nl = __ldg(c.nlist_n + p);
+            if (nl <= c.nl_cap) {
+                // entry k: component k % 4 of quad (k / 4) of the particle
+                const uint32_t *list = reinterpret_cast<const uint32_t *>(c.nlist4 + p);
+                const size_t lstride = 4 * (size_t)c.n;
+                for (int k = l; k < nl; k += G) {
+                    const int q = in_range(c, (int)__ldg(list + (size_t)(k >> 2) * lstride + (k & 3)), c.n);
+                    const float4 xj = __ldg(c.xA + q);
+                    float dx, dy, dz;
+                    const float r2 = dist2(xi, xj, dx, dy, dz);
+                    pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2, false);
+                }
+            } else {
+                // more partners than list slots: every G-th candidate of the row walk
+                int t = 0;
+                for_each_row(c, xi, bad, [&](int s0, int e0) {
+                    for (int q = s0; q < e0; ++q, ++t) {
+                        if (q == p || t % G != l) continue;
+                        const float4 xj = __ldg(c.xA + q);
+                        float dx, dy, dz;
+                        const float r2 = dist2(xi, xj, dx, dy, dz);
+                        if (r2 < c.R2) pair(xj, __ldg(c.vA + q), __ldg(c.prho + q), dx, dy, dz, r2, true);
+                    }
+                });
+            }
+        }
+        // the lanes' shares, added by a fixed shuffle tree (lane 0 of the group holds the sums)
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            ax = __fadd_rn(ax, __shfl_down_sync(gmask, ax, off, G));
+            ay = __fadd_rn(ay, __shfl_down_sync(gmask, ay, off, G));
+            az = __fadd_rn(az, __shfl_down_sync(gmask, az, off, G));
+            float e;
+            const float sx = __shfl_down_sync(gmask, Gs.Sx, off, G), lx = __shfl_down_sync(gmask, Gs.Lx, off, G);
+            const float sy = __shfl_down_sync(gmask, Gs.Sy, off, G), ly = __shfl_down_sync(gmask, Gs.Ly, off, G);
+            const float sz = __shfl_down_sync(gmask, Gs.Sz, off, G), lz = __shfl_down_sync(gmask, Gs.Lz, off, G);
+            Gs.Sx = two_sum(Gs.Sx, sx, e);
+            Gs.Lx = __fadd_rn(Gs.Lx, __fadd_rn(lx, e));
+            Gs.Sy = two_sum(Gs.Sy, sy, e);
+            Gs.Ly = __fadd_rn(Gs.Ly, __fadd_rn(ly, e));
+            Gs.Sz = two_sum(Gs.Sz, sz, e);
+            Gs.Lz = __fadd_rn(Gs.Lz, __fadd_rn(lz, e));
+            bad |= __shfl_down_sync(gmask, bad, off, G);
+        }
+        if (l == 0) {
+            if (!skip) {
+                ax = __fmaf_rn(pi.y, __fadd_rn(Gs.Sx, Gs.Lx), ax);
+                ay = __fmaf_rn(pi.y, __fadd_rn(Gs.Sy, Gs.Ly), ay);
+                az = __fmaf_rn(pi.y, __fadd_rn(Gs.Sz, Gs.Lz), az);
+                ax *= c.alpha_g;
+                ay *= c.alpha_g;
+                az *= c.alpha_g;
+            }
+            const float fx = mi * ax, fy = mi * ay, fz = mi * az;   // pair force on i
+            dg[0] = fx; dg[1] = fy; dg[2] = fz;
+            dg[3] = sqrtf(fx * fx + fy * fy + fz * fz);
+            if (kind == 0 || kind == KIND_SOFT) {
+                float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+                bool anchored = false;
+                if (kind == KIND_SOFT) {
+                    const int lp = in_range(c, id - c.nf, c.n_body_particles);
+                    anchored = c.locals[lp].w != 0.0f;
+                    for (int e = c.spring_row[lp]; e < c.spring_row[lp + 1]; ++e) {
+                        const float4 sp = c.spring_e[e];
+                        if (sp.z == 0.0f && sp.w == 0.0f) continue;   // cut spring
+                        const int q = in_range(c, c.slot_of_id[in_range(c, __float_as_int(sp.x), c.n)], c.n);
+                        const float4 xj = c.xA[q], vj = c.vA[q];
+                        float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z;
+                        const float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                        const float il = 1.0f / L;
+                        d0 *= il; d1 *= il; d2 *= il;
+                        const float vr = (vi.x - vj.x) * d0 + (vi.y - vj.y) * d1 + (vi.z - vj.z) * d2;
+                        const float f = -sp.z * (L - sp.y) - sp.w * vr;
+                        sx += f * d0; sy += f * d1; sz += f * d2;
+                    }
+                }
+                const float im = 1.0f / mi;
+                const float a0 = ax + sx * im + c.g[0];
+                const float a1 = ay + sy * im + c.g[1];
+                const float a2 = az + sz * im + c.g[2];
+                float4 vn = make_float4(vi.x + a0 * c.dt, vi.y + a1 * c.dt, vi.z + a2 * c.dt, vi.w);
+                float4 xn = make_float4(xi.x + vn.x * c.dt, xi.y + vn.y * c.dt, xi.z + vn.z * c.dt, xi.w);
+                if (anchored) {
+                    vn = make_float4(0.0f, 0.0f, 0.0f, vi.w);
+                    xn = xi;
+                }
+                if (!(isfinite(xn.x) && isfinite(xn.y) && isfinite(xn.z))) bad |= ST_NONFINITE;
+                c.xB[p] = xn;
+                c.vB[p] = vn;
+                dg[4] = mi * vn.x; dg[5] = mi * vn.y; dg[6] = mi * vn.z;
+                dg[7] = mi * sqrtf(vn.x * vn.x + vn.y * vn.y + vn.z * vn.z);
+                if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(a0, a1, a2, 0.0f);
+            } else {
+                c.xB[p] = xi;
+                c.vB[p] = vi;
+                const int lp = in_range(c, id - c.nf, c.n_body_particles);
+                c.fb[lp] = make_float4(fx, fy, fz, 0.0f);
+                c.xb[lp] = xi;
+                if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(ax, ay, az, 0.0f);
+            }
+        }
+    }
+    if (l == 0) report(c, bad);
+    // the block's diagnostic row, as in force_item_v (only lane 0 of a group holds values)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    {
+        const unsigned full = 0xffffffffu;
+        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+        float v4[4], v2[2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            v4[k] = (h16 ? dg[k + 4] : dg[k]) + __shfl_xor_sync(full, h16 ? dg[k] : dg[k + 4], 16);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            v2[k] = (h8 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(full, h8 ? v4[k] : v4[k + 2], 8);
+        float v1 = (h4 ? v2[1] : v2[0]) + __shfl_xor_sync(full, h4 ? v2[0] : v2[1], 4);
+        v1 += __shfl_xor_sync(full, v1, 2);
+        v1 += __shfl_xor_sync(full, v1, 1);
+        if ((lane & 3) == 0) sd[wid][(h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0)] = (double)v1;
+    }
+    unsigned last = 0;
+    if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last && lane < 8) {
+        __threadfence_block();
+        volatile double *v = &sd[0][0];
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
+        c.diag_part[(size_t)blk * 8 + lane] = t;
+    }
+}
+
 // ------------------------------------------------------------------ spring cutting
 
 struct Blade {

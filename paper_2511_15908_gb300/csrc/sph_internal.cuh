@@ -15,6 +15,12 @@ constexpr int kMaxBodies = 64;
 constexpr int kMaxCellRun = 1536;   // particles scanned per x-run of cells before the
                                     // status word reports SPH_ERR_CAPACITY
 constexpr int kMaxCell = 512;       // particles per cell for the deterministic rank
+// Lanes per particle of the low-latency force pass (SPH_FLAG_LOW_LATENCY): its grid has
+// this many blocks for each 256 particles, and as many diagnostic rows.
+#ifndef SPH_LOW_LATENCY_FORCE_G
+#define SPH_LOW_LATENCY_FORCE_G 8
+#endif
+constexpr int kLowLatencyForceG = SPH_LOW_LATENCY_FORCE_G;
 constexpr int kScanTile = 2048;     // cells per scan block (256 threads x 8)
 constexpr int kReduceChunk = 256;   // body particles per wrench-reduction block
 constexpr int kWrenchMinBlocks = 128; // the FP64 reduction is spread over at least this many

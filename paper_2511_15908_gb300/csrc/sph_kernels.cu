@@ -55,6 +55,11 @@ __global__ void __launch_bounds__(kBrickThreads, 2) k_density_brick(SimConst c)
 #endif
 __global__ void __launch_bounds__(kTile) k_boundary_volume(SimConst c) { boundary_volume_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force(SimConst c) { force_item(c, blockIdx.x); }
+template <int G>
+__global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force_coop(SimConst c)
+{
+    force_coop_item<G>(c, blockIdx.x);
+}
 __global__ void __launch_bounds__(kTile) k_wrench(SimConst c) { wrench_item(c, blockIdx.x); }
 __global__ void k_cycle_end(SimConst c) { cycle_end_item(c); }
 
@@ -141,7 +146,11 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     else
         k_density_narrow<<<nb, kTile, 0, s>>>(c);
     mark();
-    k_force<<<c.n_force_blocks, kTile, 0, s>>>(c);
+    // (a flagged scene's n_force_blocks counts blocks of 256 / G particles)
+    if ((c.flags & FLAG_LOW_LATENCY) && !(c.flags & FLAG_VOLUME))
+        k_force_coop<kLowLatencyForceG><<<c.n_force_blocks, kTile, 0, s>>>(c);
+    else
+        k_force<<<c.n_force_blocks, kTile, 0, s>>>(c);
     mark();
     k_wrench<<<c.n_wgrid, kTile, 0, s>>>(c);
     mark();

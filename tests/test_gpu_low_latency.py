@@ -1,13 +1,14 @@
-"""The low-latency density pass (SPH_FLAG_LOW_LATENCY: 32 or 16 threads per particle):
+"""The low-latency passes (SPH_FLAG_LOW_LATENCY: the density pass with 32 or 16 threads per
+particle, the force pass with 8):
 
 - one substep against the oracle with the same bars as the default pass (keys, order,
   cell_start and neighbour counts bit-exact, densities within 1e-5, every acceleration within
   1e-4 max(|a|, 0.1 g), wrenches within 1e-4), on scenes with every body kind, a grabbed
   half-spacing cube, cell edges from h to 2h and a neighbour list too short for most
   particles;
-- against the default pass: the same neighbour counts and sorted order, densities apart by at
-  most one rounding of the FP32 excess rho - rho0 and one of rho (the float-pair sums are
-  added in another order);
+- against the default passes: the same neighbour counts and sorted order, densities apart by
+  at most one rounding of the FP32 excess rho - rho0 and one of rho (the float-pair sums are
+  added in another order), trajectories that stay together over 20 substeps;
 - where the flag has no effect: volume boundaries (bit-identical to the unflagged scene) and
   inside a batch (every structure equals unflagged single-scene stepping bit for bit).
 """

@@ -1474,6 +1474,101 @@ __device__ __forceinline__ void boundary_volume_item(const SimConst &c, int blk)
 
 // -------------------------------------------------------------- force + integrate
 
+// The end of a force-pass particle: the pair force, its soft springs, the explicit Euler
+// step (Eq. euler) for a fluid or soft particle or the coupling force of a boundary one,
+// the writes and the particle's diagnostic values dg (pair force xyz, |f|, m v xyz, m|v|).
+__device__ __forceinline__ void force_tail(const SimConst &c, int p, float4 xi, float4 vi, int id, int kind,
+                                           float mi, float ax, float ay, float az, float (&dg)[8],
+                                           uint32_t &bad)
+{
+    float fx = mi * ax, fy = mi * ay, fz = mi * az;   // pair force on i
+    dg[0] = fx; dg[1] = fy; dg[2] = fz;
+    dg[3] = sqrtf(fx * fx + fy * fy + fz * fz);
+    if (kind == 0 || kind == KIND_SOFT) {
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        bool anchored = false;
+        if (kind == KIND_SOFT) {
+            int l = in_range(c, id - c.nf, c.n_body_particles);
+            anchored = c.locals[l].w != 0.0f;      // pinned soft particle (cloth anchor)
+            for (int e = c.spring_row[l]; e < c.spring_row[l + 1]; ++e) {
+                float4 sp = c.spring_e[e];
+                if (sp.z == 0.0f && sp.w == 0.0f) continue;   // cut spring
+                int q = in_range(c, c.slot_of_id[in_range(c, __float_as_int(sp.x), c.n)], c.n);
+                float4 xj = c.xA[q], vj = c.vA[q];
+                float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z;
+                float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                float il = 1.0f / L;
+                d0 *= il; d1 *= il; d2 *= il;
+                float vr = (vi.x - vj.x) * d0 + (vi.y - vj.y) * d1 + (vi.z - vj.z) * d2;
+                float f = -sp.z * (L - sp.y) - sp.w * vr;
+                sx += f * d0; sy += f * d1; sz += f * d2;
+            }
+        }
+        float im = 1.0f / mi;
+        float a0 = ax + sx * im + c.g[0];
+        float a1 = ay + sy * im + c.g[1];
+        float a2 = az + sz * im + c.g[2];
+        float4 vn = make_float4(vi.x + a0 * c.dt, vi.y + a1 * c.dt, vi.z + a2 * c.dt, vi.w);
+        float4 xn = make_float4(xi.x + vn.x * c.dt, xi.y + vn.y * c.dt, xi.z + vn.z * c.dt, xi.w);
+        if (anchored) {                        // an anchor stays where it is, at rest
+            vn = make_float4(0.0f, 0.0f, 0.0f, vi.w);
+            xn = xi;
+        }
+        if (!(isfinite(xn.x) && isfinite(xn.y) && isfinite(xn.z))) bad |= ST_NONFINITE;
+        c.xB[p] = xn;
+        c.vB[p] = vn;
+        dg[4] = mi * vn.x; dg[5] = mi * vn.y; dg[6] = mi * vn.z;
+        dg[7] = mi * sqrtf(vn.x * vn.x + vn.y * vn.y + vn.z * vn.z);
+        if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(a0, a1, a2, 0.0f);
+    } else {
+        c.xB[p] = xi;
+        c.vB[p] = vi;
+        int l = in_range(c, id - c.nf, c.n_body_particles);
+        c.fb[l] = make_float4(fx, fy, fz, 0.0f);
+        c.xb[l] = xi;
+        if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(ax, ay, az, 0.0f);
+    }
+}
+
+// The block's row of the momentum diagnostics (dg summed over its particles): FP32 within
+// the warp, FP64 above it; the last warp of the block to finish sums the per-warp partials
+// in a fixed order (no block barrier, so no warp waits for another).
+__device__ __forceinline__ void force_diag_row(const SimConst &c, int blk, const float (&dg)[8],
+                                               double (&sd)[8][8], unsigned &s_done)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    {
+        // the 8 warp sums by a halving exchange: after the xor-16, -8 and -4 steps each lane
+        // holds one component (bits 4, 3, 2 of the lane pick it), then xor-2 and -1 finish
+        const unsigned full = 0xffffffffu;
+        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+        float v4[4], v2[2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            v4[k] = (h16 ? dg[k + 4] : dg[k]) + __shfl_xor_sync(full, h16 ? dg[k] : dg[k + 4], 16);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            v2[k] = (h8 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(full, h8 ? v4[k] : v4[k + 2], 8);
+        float v1 = (h4 ? v2[1] : v2[0]) + __shfl_xor_sync(full, h4 ? v2[0] : v2[1], 4);
+        v1 += __shfl_xor_sync(full, v1, 2);
+        v1 += __shfl_xor_sync(full, v1, 1);
+        if ((lane & 3) == 0) sd[wid][(h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0)] = (double)v1;
+    }
+    unsigned last = 0;
+    if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last && lane < 8) {
+        __threadfence_block();
+        volatile double *v = &sd[0][0];
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
+        c.diag_part[(size_t)blk * 8 + lane] = t;
+    }
+}
+
 template <bool VOL>
 __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
 {
@@ -1613,88 +1708,10 @@ __device__ __forceinline__ void force_item_v(const SimConst &c, int blk)
             ay *= c.alpha_g;
             az *= c.alpha_g;
         }
-        float fx = mi * ax, fy = mi * ay, fz = mi * az;   // pair force on i
-        dg[0] = fx; dg[1] = fy; dg[2] = fz;
-        dg[3] = sqrtf(fx * fx + fy * fy + fz * fz);
-        if (kind == 0 || kind == KIND_SOFT) {
-            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-            bool anchored = false;
-            if (kind == KIND_SOFT) {
-                int l = in_range(c, id - c.nf, c.n_body_particles);
-                anchored = c.locals[l].w != 0.0f;      // pinned soft particle (cloth anchor)
-                for (int e = c.spring_row[l]; e < c.spring_row[l + 1]; ++e) {
-                    float4 sp = c.spring_e[e];
-                    if (sp.z == 0.0f && sp.w == 0.0f) continue;   // cut spring
-                    int q = in_range(c, c.slot_of_id[in_range(c, __float_as_int(sp.x), c.n)], c.n);
-                    float4 xj = c.xA[q], vj = c.vA[q];
-                    float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z;
-                    float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-                    float il = 1.0f / L;
-                    d0 *= il; d1 *= il; d2 *= il;
-                    float vr = (vi.x - vj.x) * d0 + (vi.y - vj.y) * d1 + (vi.z - vj.z) * d2;
-                    float f = -sp.z * (L - sp.y) - sp.w * vr;
-                    sx += f * d0; sy += f * d1; sz += f * d2;
-                }
-            }
-            float im = 1.0f / mi;
-            float a0 = ax + sx * im + c.g[0];
-            float a1 = ay + sy * im + c.g[1];
-            float a2 = az + sz * im + c.g[2];
-            float4 vn = make_float4(vi.x + a0 * c.dt, vi.y + a1 * c.dt, vi.z + a2 * c.dt, vi.w);
-            float4 xn = make_float4(xi.x + vn.x * c.dt, xi.y + vn.y * c.dt, xi.z + vn.z * c.dt, xi.w);
-            if (anchored) {                        // an anchor stays where it is, at rest
-                vn = make_float4(0.0f, 0.0f, 0.0f, vi.w);
-                xn = xi;
-            }
-            if (!(isfinite(xn.x) && isfinite(xn.y) && isfinite(xn.z))) bad |= ST_NONFINITE;
-            c.xB[p] = xn;
-            c.vB[p] = vn;
-            dg[4] = mi * vn.x; dg[5] = mi * vn.y; dg[6] = mi * vn.z;
-            dg[7] = mi * sqrtf(vn.x * vn.x + vn.y * vn.y + vn.z * vn.z);
-            if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(a0, a1, a2, 0.0f);
-        } else {
-            c.xB[p] = xi;
-            c.vB[p] = vi;
-            int l = in_range(c, id - c.nf, c.n_body_particles);
-            c.fb[l] = make_float4(fx, fy, fz, 0.0f);
-            c.xb[l] = xi;
-            if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(ax, ay, az, 0.0f);
-        }
+        force_tail(c, p, xi, vi, id, kind, mi, ax, ay, az, dg, bad);
     }
     report(c, bad);
-    // FP32 within the warp, FP64 above it; the last warp of the block to finish sums the
-    // per-warp partials in a fixed order (no block barrier, so no warp waits for another)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    {
-        // the 8 warp sums by a halving exchange: after the xor-16, -8 and -4 steps each lane
-        // holds one component (bits 4, 3, 2 of the lane pick it), then xor-2 and -1 finish
-        const unsigned full = 0xffffffffu;
-        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-        float v4[4], v2[2];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            v4[k] = (h16 ? dg[k + 4] : dg[k]) + __shfl_xor_sync(full, h16 ? dg[k] : dg[k + 4], 16);
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-            v2[k] = (h8 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(full, h8 ? v4[k] : v4[k + 2], 8);
-        float v1 = (h4 ? v2[1] : v2[0]) + __shfl_xor_sync(full, h4 ? v2[0] : v2[1], 4);
-        v1 += __shfl_xor_sync(full, v1, 2);
-        v1 += __shfl_xor_sync(full, v1, 1);
-        if ((lane & 3) == 0) sd[wid][(h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0)] = (double)v1;
-    }
-    unsigned last = 0;
-    if (lane == 0) {
-        __threadfence_block();
-        last = atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last && lane < 8) {
-        __threadfence_block();
-        volatile double *v = &sd[0][0];
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
-        c.diag_part[(size_t)blk * 8 + lane] = t;
-    }
+    force_diag_row(c, blk, dg, sd, s_done);
 }
 
 __device__ __forceinline__ void force_item(const SimConst &c, int blk)
@@ -1811,86 +1828,11 @@ __device__ __forceinline__ void force_coop_item(const SimConst &c, int blk)
                 ay *= c.alpha_g;
                 az *= c.alpha_g;
             }
-            const float fx = mi * ax, fy = mi * ay, fz = mi * az;   // pair force on i
-            dg[0] = fx; dg[1] = fy; dg[2] = fz;
-            dg[3] = sqrtf(fx * fx + fy * fy + fz * fz);
-            if (kind == 0 || kind == KIND_SOFT) {
-                float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-                bool anchored = false;
-                if (kind == KIND_SOFT) {
-                    const int lp = in_range(c, id - c.nf, c.n_body_particles);
-                    anchored = c.locals[lp].w != 0.0f;
-                    for (int e = c.spring_row[lp]; e < c.spring_row[lp + 1]; ++e) {
-                        const float4 sp = c.spring_e[e];
-                        if (sp.z == 0.0f && sp.w == 0.0f) continue;   // cut spring
-                        const int q = in_range(c, c.slot_of_id[in_range(c, __float_as_int(sp.x), c.n)], c.n);
-                        const float4 xj = c.xA[q], vj = c.vA[q];
-                        float d0 = xi.x - xj.x, d1 = xi.y - xj.y, d2 = xi.z - xj.z;
-                        const float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-                        const float il = 1.0f / L;
-                        d0 *= il; d1 *= il; d2 *= il;
-                        const float vr = (vi.x - vj.x) * d0 + (vi.y - vj.y) * d1 + (vi.z - vj.z) * d2;
-                        const float f = -sp.z * (L - sp.y) - sp.w * vr;
-                        sx += f * d0; sy += f * d1; sz += f * d2;
-                    }
-                }
-                const float im = 1.0f / mi;
-                const float a0 = ax + sx * im + c.g[0];
-                const float a1 = ay + sy * im + c.g[1];
-                const float a2 = az + sz * im + c.g[2];
-                float4 vn = make_float4(vi.x + a0 * c.dt, vi.y + a1 * c.dt, vi.z + a2 * c.dt, vi.w);
-                float4 xn = make_float4(xi.x + vn.x * c.dt, xi.y + vn.y * c.dt, xi.z + vn.z * c.dt, xi.w);
-                if (anchored) {
-                    vn = make_float4(0.0f, 0.0f, 0.0f, vi.w);
-                    xn = xi;
-                }
-                if (!(isfinite(xn.x) && isfinite(xn.y) && isfinite(xn.z))) bad |= ST_NONFINITE;
-                c.xB[p] = xn;
-                c.vB[p] = vn;
-                dg[4] = mi * vn.x; dg[5] = mi * vn.y; dg[6] = mi * vn.z;
-                dg[7] = mi * sqrtf(vn.x * vn.x + vn.y * vn.y + vn.z * vn.z);
-                if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(a0, a1, a2, 0.0f);
-            } else {
-                c.xB[p] = xi;
-                c.vB[p] = vi;
-                const int lp = in_range(c, id - c.nf, c.n_body_particles);
-                c.fb[lp] = make_float4(fx, fy, fz, 0.0f);
-                c.xb[lp] = xi;
-                if (c.flags & FLAG_RECORD) c.acc_dbg[p] = make_float4(ax, ay, az, 0.0f);
-            }
+            force_tail(c, p, xi, vi, id, kind, mi, ax, ay, az, dg, bad);
         }
     }
     if (l == 0) report(c, bad);
-    // the block's diagnostic row, as in force_item_v (only lane 0 of a group holds values)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    {
-        const unsigned full = 0xffffffffu;
-        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
-        float v4[4], v2[2];
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            v4[k] = (h16 ? dg[k + 4] : dg[k]) + __shfl_xor_sync(full, h16 ? dg[k] : dg[k + 4], 16);
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-            v2[k] = (h8 ? v4[k + 2] : v4[k]) + __shfl_xor_sync(full, h8 ? v4[k] : v4[k + 2], 8);
-        float v1 = (h4 ? v2[1] : v2[0]) + __shfl_xor_sync(full, h4 ? v2[0] : v2[1], 4);
-        v1 += __shfl_xor_sync(full, v1, 2);
-        v1 += __shfl_xor_sync(full, v1, 1);
-        if ((lane & 3) == 0) sd[wid][(h16 ? 4 : 0) + (h8 ? 2 : 0) + (h4 ? 1 : 0)] = (double)v1;
-    }
-    unsigned last = 0;
-    if (lane == 0) {
-        __threadfence_block();
-        last = atomicAdd(&s_done, 1u) == (blockDim.x >> 5) - 1;
-    }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (last && lane < 8) {
-        __threadfence_block();
-        volatile double *v = &sd[0][0];
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += v[w * 8 + lane];
-        c.diag_part[(size_t)blk * 8 + lane] = t;
-    }
+    force_diag_row(c, blk, dg, sd, s_done);   // only lane 0 of a group holds values
 }
 
 // ------------------------------------------------------------------ spring cutting

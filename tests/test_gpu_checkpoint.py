@@ -133,6 +133,35 @@ def test_haptic_cycle_equals_the_three_calls(sph):
         assert np.array_equal(u, w)
 
 
+@pytest.mark.parametrize("low_latency", [False, True])
+def test_one_substep_haptic_cycle_equals_the_three_calls(sph, low_latency):
+    # the haptic tick's form, one substep and the raw wrench, with both density and force
+    # passes: the wrenches, the state and the cycle log (read through the smoothed wrench)
+    # are the three calls' bit for bit
+    sc = _grabbed()
+    b = sc.grab_body
+    flags = sc.params["flags"] | (sph.FLAG_LOW_LATENCY if low_latency else 0)
+    outs = []
+    for fused in (False, True):
+        sim = sph.Simulation(sc, flags=flags)
+        sim.step(3)
+        ws = []
+        for i in range(8):
+            row = sc.trajectory[10 + i]
+            if fused:
+                ws.append(sim.haptic_cycle(sim.body_ids[b], row[:7], row[7:], 1).copy())
+            else:
+                sim.set_grab_pose(sim.body_ids[b], row[:7], row[7:])
+                sim.step(1)
+                ws.append(sim.grab_wrench(smoothed=False))
+        st = sim.state()
+        outs.append((np.array(ws), sim.grab_wrench(smoothed=True), st["x"], st["v"], sim.body(b),
+                     sim.info()[4]))
+        sim.close()
+    for u, w in zip(*outs):
+        assert np.array_equal(u, w)
+
+
 def test_readme_example_runs(sph):
     # the usage example of the README, verbatim apart from the assertions
     sc = scenes.dam_break(seed=0, grab=True)

@@ -75,19 +75,18 @@ enum {
                                           force; boundary particles exert no SPH force on
                                           each other; sph_get_state reports psi_b as a
                                           boundary particle's density */
-    SPH_FLAG_LOW_LATENCY = 1u << 5     /* the density pass (Alg. 1's density loop) takes 32
-                                          (scenes up to 20,000 particles) or 16
-                                          cooperating threads per particle instead of one,
-                                          and the force pass 8:
-                                          for scenes too small to fill the GPU, whose
-                                          substep waits for the serial neighbour loop of
-                                          their half-spacing body particles (~226
-                                          neighbours each).  Same neighbours, neighbour
-                                          counts and interaction lists; the densities'
-                                          float-pair sums and the forces' FP32 sums are
-                                          added in another order, so they may round to
-                                          neighbouring values.  Slower on a
-                                          scene that fills the GPU.  No effect with
+    SPH_FLAG_LOW_LATENCY = 1u << 5     /* for scenes too small to fill the GPU, whose
+                                          substep waits for the serial neighbour loops of
+                                          single threads (a body sampled at half spacing
+                                          has ~226 neighbours): the density pass (Alg. 1's
+                                          density loop) takes 32 cooperating threads per
+                                          particle (scenes up to 20,000 particles, else
+                                          16) and the force pass 8.  Same neighbours,
+                                          neighbour counts and interaction lists; the
+                                          densities' float-pair sums and the forces' FP32
+                                          sums are added in another order, so they may
+                                          round to neighbouring values.  Slower on a scene
+                                          that fills the GPU.  No effect with
                                           SPH_FLAG_VOLUME_BOUNDARY or inside a batch
                                           (sph_batch_*), which runs one thread per
                                           particle */
@@ -149,7 +148,10 @@ typedef struct {
 } sph_capacity;
 
 /* Bytes of device workspace a scene with these parameters and capacities needs
- * (0 if the arguments are invalid).  The grid size follows from domain and cell. */
+ * (0 if the arguments are invalid).  The grid size follows from domain and cell; with
+ * SPH_FLAG_LOW_LATENCY the force pass's diagnostic rows take 8 times their usual
+ * 256 bytes per 1,024 particles (so the flag is part of the parameters the size is
+ * computed for). */
 size_t sph_workspace_bytes(const sph_params *p, const sph_capacity *cap);
 
 /*

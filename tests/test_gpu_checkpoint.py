@@ -176,6 +176,10 @@ def test_readme_example_runs(sph):
     sim2.restore(ck)
     assert sim2.info()[4] == 60
     sim2.close()
+    fast = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_LOW_LATENCY)
+    fast.step(10)
+    assert np.all(np.isfinite(fast.state()["x"]))
+    fast.close()
 
 
 def test_released_body_is_a_free_body(sph):

@@ -4,8 +4,8 @@ particle, the force pass with 8):
 - one substep against the oracle with the same bars as the default pass (keys, order,
   cell_start and neighbour counts bit-exact, densities within 1e-5, every acceleration within
   1e-4 max(|a|, 0.1 g), wrenches within 1e-4), on scenes with every body kind, a grabbed
-  half-spacing cube, cell edges from h to 2h and a neighbour list too short for most
-  particles;
+  half-spacing cube, cell edges from h to 2h, a neighbour list too short for most
+  particles, the Tait equation of state and anchored, cut cloth;
 - against the default passes: the same neighbour counts and sorted order, densities apart by
   at most one rounding of the FP32 excess rho - rho0 and one of rho (the float-pair sums are
   added in another order), trajectories that stay together over 20 substeps;
@@ -135,3 +135,48 @@ def test_batch_runs_one_thread_per_particle(sph, bps):
     batch.close()
     for s in solo + flagged:
         s.close()
+
+
+def test_tait_eos_dam_break(sph):
+    # the Tait equation of state in the group density pass
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=3, grab=True, cube_pos=(0.4, 0.4, 0.2)),
+                                    seed=10, sigma=0.3)
+    sc.params = dict(sc.params, flags=sc.params["flags"] | scenes.FLAG_TAIT)
+    check_one_substep(sph, _flagged(sph, sc), mode=0)
+
+
+@pytest.mark.parametrize("anchors", ["corners", "edges"])
+def test_cloth_bath_with_anchors(sph, anchors):
+    # springs, anchors and the cloth's soft particles go through the shared tail of the
+    # force passes; one substep against the oracle
+    sc = scenes.with_velocity_noise(scenes.cloth_bath(seed=1, anchors=anchors), seed=21, sigma=0.2)
+    check_one_substep(sph, _flagged(sph, sc), mode=0)
+
+
+def test_cut_cloth_then_substep_matches_oracle(sph):
+    import oracle
+    from test_gpu_parity import _by_id, G, ACC_TOL
+    rng = np.random.default_rng(200)
+    sc = scenes.with_velocity_noise(scenes.cloth_bath(seed=0), seed=40, sigma=0.2)
+    sheet = sc.bodies[1]
+    lo, hi = sheet.xyz.min(0), sheet.xyz.max(0)
+    for _ in range(50):                          # a blade with no ambiguous spring
+        c = lo + rng.uniform(0.2, 0.8, 3) * (hi - lo)
+        blade = (c + rng.normal(0, 0.08, (3, 3))).astype(np.float32)
+        sysm = oracle.System(sc, mode=0)
+        n_orc, per_body = sysm.cut_springs(blade)
+        if n_orc > 3 and not any(near.any() for _, near in per_body):
+            break
+    else:
+        pytest.fail("no unambiguous blade found")
+    sim = sph.Simulation(sc, flags=sc.params["flags"] | sph.FLAG_RECORD | sph.FLAG_LOW_LATENCY)
+    assert sim.cut_springs(blade) == n_orc
+    sim.step(1)
+    st = sim.state(record=True)
+    ref = sysm.substep()
+    n = sc.n_total
+    acc_ref = _by_id(ref, "acc", n)
+    scale = np.maximum(np.linalg.norm(acc_ref, axis=1), 0.1 * G)
+    dif = np.linalg.norm(st["acc"].astype(np.float64) - acc_ref, axis=1)
+    assert np.all(dif <= ACC_TOL * scale), (dif / scale).max()
+    sim.close()

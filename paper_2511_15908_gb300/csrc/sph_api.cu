@@ -22,7 +22,7 @@ namespace {
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t xA, vA, xB, vB, prho, key, rank, perm, cnt, cell_start, tile_sum, slot_of_id, locals,
+    size_t xA, vA, xB, vB, prho, key, rank, perm, cnt, cell_start, tile_sum, tile_state, slot_of_id, locals,
         spring_row, spring_e, fb, xb, acc_dbg, nnbr, body, path, wrench, wrench_part, wblock,
         diag_part, diag_part2, nlist, nlist_n, cut, diag, wlog, cyc_log, status, ctr, total;
     int dims[3], ncell, n_scan_tiles, max_wblocks, max_force_blocks, nl_cap;
@@ -81,6 +81,7 @@ Layout make_layout(const sph_params &p, const sph_capacity &cap)
     L.cnt = take(4 * ((size_t)L.ncell + 1));
     L.cell_start = take(4 * ((size_t)L.ncell + 1));
     L.tile_sum = take(4 * (size_t)L.n_scan_tiles);
+    L.tile_state = take(8 * ((size_t)L.n_scan_tiles + 1));
     L.slot_of_id = take(4 * N);
     L.locals = take(16 * N);
     L.spring_row = take(4 * (N + 1));
@@ -399,6 +400,7 @@ sph_status sph_create(const sph_params *p, const sph_capacity *cap, void *d_work
     c.key = at<uint32_t>(h, L.key); c.rank = at<uint32_t>(h, L.rank); c.perm = at<uint32_t>(h, L.perm);
     c.cnt = at<uint32_t>(h, L.cnt); c.cell_start = at<uint32_t>(h, L.cell_start);
     c.tile_sum = at<uint32_t>(h, L.tile_sum);
+    c.tile_state = at<unsigned long long>(h, L.tile_state);
     c.slot_of_id = at<int>(h, L.slot_of_id);
     c.locals = at<float4>(h, L.locals);
     c.spring_row = at<int>(h, L.spring_row);

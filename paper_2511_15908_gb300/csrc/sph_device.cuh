@@ -250,6 +250,8 @@ __device__ __forceinline__ void hash_item(const SimConst &c, int blk)
 {
     int e = blk * kTile + threadIdx.x;
     if (e >= c.n) return;
+    // the single-pass scan's tile states and tile counter, ready for this substep's scan
+    for (int t = e; t <= c.n_scan_tiles; t += c.n) c.tile_state[t] = 0ull;
     float4 x = c.xB[e];
     if (x.w < 0.0f) {                       // boundary particle (negative mass tag)
         float4 v = c.vB[e];
@@ -354,6 +356,113 @@ __device__ __forceinline__ void scan_apply_item(const SimConst &c, int blk)
         for (int i = 0; i < 8; ++i) { st[i] = run; run += v[i]; }
         *reinterpret_cast<uint4 *>(c.cell_start + base) = make_uint4(st[0], st[1], st[2], st[3]);
         *reinterpret_cast<uint4 *>(c.cell_start + base + 4) = make_uint4(st[4], st[5], st[6], st[7]);
+        // counts ready for the next substep's hash
+        *reinterpret_cast<uint4 *>(c.cnt + base) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(c.cnt + base + 4) = make_uint4(0u, 0u, 0u, 0u);
+        if (base + 8 == c.ncell) c.cell_start[c.ncell] = run;
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        int ci = base + i;
+        if (ci < c.ncell) {
+            c.cell_start[ci] = run;
+            c.cnt[ci] = 0u;                 // ready for the next substep's count
+            run += v[i];
+            if (ci == c.ncell - 1) c.cell_start[c.ncell] = run;
+        }
+    }
+}
+
+// Single-pass exclusive scan of the cell counts (decoupled look-back): one launch instead of
+// the tile sums and the apply pass above, the counts read once.  A block takes the next tile
+// index in the order blocks start (so every earlier tile is running or done), sums its 2048
+// counts, publishes that aggregate, then warp 0 walks back over the earlier tiles 32 at a
+// time, adding aggregates up to the first tile that has published its inclusive prefix, and
+// publishes its own inclusive prefix; the cells then get their starts as in scan_apply_item.
+// A state word is (kind << 32 | value), kind 1 = aggregate, 2 = inclusive prefix, 0 = not
+// yet (the hash pass zeroes them).  Each wait is bounded: a wait that gives up latches
+// ST_TIMEOUT and counts the tile as a prefix of 0.  The same integer sums as the two-pass
+// scan, so the same cell_start.
+constexpr unsigned kScanSpin = 1u << 20;
+__device__ __forceinline__ void scan_lookback_item(const SimConst &c)
+{
+    __shared__ uint32_t ws[8];
+    __shared__ uint32_t s_pre;
+    __shared__ int s_tile;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0)
+        s_tile = (int)atomicAdd(reinterpret_cast<unsigned *>(c.tile_state + c.n_scan_tiles), 1u);
+    __syncthreads();
+    const int blk = s_tile;
+    const int base = blk * kScanTile + threadIdx.x * 8;
+    const bool full = base + 8 <= c.ncell &&
+                      (((uintptr_t)c.cnt | (uintptr_t)c.cell_start) & 15u) == 0;
+    uint32_t v[8], tot = 0;
+    if (full) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(c.cnt + base);
+        const uint4 b = *reinterpret_cast<const uint4 *>(c.cnt + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = (base + i < c.ncell) ? c.cnt[base + i] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) tot += v[i];
+    // inclusive warp scan of the thread totals, the warp totals in ws
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t agg = 0;
+        for (int w = 0; w < 8; ++w) agg += ws[w];
+        uint32_t excl = 0, bad = 0;
+        volatile unsigned long long *st = c.tile_state;
+        if (blk == 0) {
+            if (lane == 0) atomicExch(c.tile_state, (2ull << 32) | agg);
+        } else {
+            if (lane == 0) atomicExch(c.tile_state + blk, (1ull << 32) | agg);
+            for (int j = blk - 1;; j -= 32) {
+                const int jj = j - lane;
+                unsigned kind = 2u, val = 0u;        // before tile 0: a prefix of 0
+                if (jj >= 0) {
+                    unsigned long long w = st[jj];
+                    for (unsigned it = 0; (w >> 32) == 0ull && it < kScanSpin; ++it) w = st[jj];
+                    if ((w >> 32) == 0ull) {
+                        bad |= ST_TIMEOUT;
+                        w = 2ull << 32;
+                    }
+                    kind = (unsigned)(w >> 32);
+                    val = (unsigned)w;
+                }
+                // the nearest tile with an inclusive prefix ends the walk; the tiles after
+                // it contribute their aggregates
+                const unsigned pm = __ballot_sync(0xffffffffu, kind == 2u);
+                const int first = pm ? __ffs(pm) - 1 : 31;
+                excl += warp_sum(lane <= first ? val : 0u);
+                if (pm) break;
+            }
+            if (lane == 0) atomicExch(c.tile_state + blk, (2ull << 32) | (excl + agg));
+        }
+        if (lane == 0) s_pre = excl;
+        report(c, bad);
+    }
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += ws[w];
+    uint32_t run = s_pre + wpre + inc - tot;
+    if (full) {
+        uint32_t stv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { stv[i] = run; run += v[i]; }
+        *reinterpret_cast<uint4 *>(c.cell_start + base) = make_uint4(stv[0], stv[1], stv[2], stv[3]);
+        *reinterpret_cast<uint4 *>(c.cell_start + base + 4) = make_uint4(stv[4], stv[5], stv[6], stv[7]);
         // counts ready for the next substep's hash
         *reinterpret_cast<uint4 *>(c.cnt + base) = make_uint4(0u, 0u, 0u, 0u);
         *reinterpret_cast<uint4 *>(c.cnt + base + 4) = make_uint4(0u, 0u, 0u, 0u);

@@ -78,6 +78,9 @@ struct __align__(16) SimConst {
     float4 *xA, *vA, *xB, *vB;
     float2 *prho;              // (rho, p / rho^2) in sorted order
     uint32_t *key, *rank, *perm, *cnt, *cell_start, *tile_sum;
+    unsigned long long *tile_state;   // n_scan_tiles + 1 words of the single-pass scan: per
+                                      // tile (kind << 32 | value), then the tile counter;
+                                      // zeroed by the hash pass before every scan
     int *slot_of_id;           // id -> sorted slot (soft particles only)
     float4 *locals;            // per body particle (id - nf): body-frame offset
     int *spring_row;           // per body particle (id - nf), CSR row start (+1 entry)

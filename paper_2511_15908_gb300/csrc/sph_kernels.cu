@@ -34,6 +34,12 @@ namespace sphgb {
 __global__ void __launch_bounds__(kTile) k_hash(SimConst c) { hash_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_scan_tiles(SimConst c) { scan_tiles_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_scan_apply(SimConst c) { scan_apply_item(c, blockIdx.x); }
+__global__ void __launch_bounds__(kTile) k_scan_lookback(SimConst c) { scan_lookback_item(c); }
+// the substep's scan: single-pass (one launch; timed as the tile pass, the apply pass reads
+// ~0) unless built with SPH_SCAN_LOOKBACK=0
+#ifndef SPH_SCAN_LOOKBACK
+#define SPH_SCAN_LOOKBACK 1
+#endif
 __global__ void __launch_bounds__(kTile) k_scatter(SimConst c) { scatter_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(kTile) k_rank_gather(SimConst c) { rank_gather_item(c, blockIdx.x); }
 __global__ void __launch_bounds__(SPH_DENSITY_THREADS, SPH_DENSITY_MINB) k_density(SimConst c)
@@ -114,9 +120,14 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     mark();
     k_hash<<<nb, kTile, 0, s>>>(c);
     mark();
-    k_scan_tiles<<<c.n_scan_tiles, kTile, 0, s>>>(c);
-    mark();
-    k_scan_apply<<<c.n_scan_tiles, kTile, 0, s>>>(c);
+    if (SPH_SCAN_LOOKBACK) {
+        k_scan_lookback<<<c.n_scan_tiles, kTile, 0, s>>>(c);
+        mark();
+    } else {
+        k_scan_tiles<<<c.n_scan_tiles, kTile, 0, s>>>(c);
+        mark();
+        k_scan_apply<<<c.n_scan_tiles, kTile, 0, s>>>(c);
+    }
     mark();
     k_scatter<<<nb, kTile, 0, s>>>(c);
     mark();

@@ -373,12 +373,16 @@ sph_status sph_surrogate_targets(sph_mlp *m, const double *d_wrench, const doubl
 sph_status sph_get_info(sph_handle *h, int64_t out[5]);
 
 /*
- * Per-kernel timing hook (benchmarks).  With profiling on, every later substep records a
- * CUDA event before and after each of its 8 kernels (as event-record nodes inside the
- * captured graph, on the handle's stream).  sph_get_kernel_times synchronises and returns
- * the durations of the last substep in milliseconds, in launch order: hash, scan tiles,
- * scan apply, scatter, rank + gather, density, force + integrate, wrench reduction.
- * The events are created by sph_set_profiling(h, 1) (no device memory is allocated).
+ * Per-kernel timing hook (benchmarks).  With profiling on (on = 1), every later substep
+ * records a CUDA event before and after each of its 8 kernels (as event-record nodes inside
+ * the captured graph, on the handle's stream); with on = 2 only the two around the density
+ * pass, which costs the substep less (each event node adds a few microseconds).
+ * sph_get_kernel_times synchronises and returns the durations of the last substep in
+ * milliseconds, in launch order: hash, scan tiles (the single-pass scan), scan apply (~0
+ * with it), scatter, rank + gather, density, force + integrate, wrench reduction (0 for
+ * the kernels a level-2 substep does not time).  The events are created by the first
+ * sph_set_profiling(h, on > 0) (no device memory is allocated).  Errors: SPH_ERR_ARG for
+ * a level other than 0, 1, 2.
  */
 sph_status sph_set_profiling(sph_handle *h, int32_t on);
 sph_status sph_get_kernel_times(sph_handle *h, float out_ms[8]);

@@ -128,7 +128,9 @@ struct sph_handle {
     // graphs: 1 and 16 substeps, 1 substep followed by the update cycle's end (the last
     // launch of a call), and the profiling substep with event nodes
     cudaGraphExec_t exec1 = nullptr, exec16 = nullptr, exec1c = nullptr, exec_prof = nullptr;
-    bool profiling = false;
+    int profiling = 0;                      // 0 off, 1 every kernel, 2 the density pass only
+    int prof_graph = 0;                     // the level exec_prof was captured for
+    int prof_last = 0;                      // the level of the last profiled substep
     cudaEvent_t ev[kSubstepKernels + 1] = {};
     int64_t substeps = 0;
     std::string err;
@@ -280,14 +282,14 @@ sph_status finalize(sph_handle *h)
 }
 
 sph_status capture(sph_handle *h, int count, cudaGraphExec_t *out, bool prof = false,
-                   bool cycle_end = false)
+                   bool cycle_end = false, unsigned ev_mask = ~0u)
 {
     cudaGraph_t g = nullptr;
     SPH_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < count && le == cudaSuccess; ++i)
-        le = launch_substep(h->c, h->stream, prof ? h->ev : nullptr, prof);
-    if (le == cudaSuccess && cycle_end) le = launch_cycle_end(h->c, h->stream);
+        le = launch_substep(h->c, h->stream, prof ? h->ev : nullptr, prof, cycle_end && i == count - 1,
+                            ev_mask);
     cudaError_t ce = cudaStreamEndCapture(h->stream, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, le, "capture launch"); }
     if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
@@ -628,14 +630,21 @@ sph_status sph_step(sph_handle *h, int32_t n_substeps)
     int left = n_substeps;
     bool cycle_done = false;
     if (h->profiling) {
+        const unsigned mask = h->profiling == 2 ? kDensityEvents : ~0u;
+        if (graphs && h->exec_prof && h->prof_graph != h->profiling) {
+            cudaGraphExecDestroy(h->exec_prof);
+            h->exec_prof = nullptr;
+        }
         if (graphs && !h->exec_prof) {
-            st = capture(h, 1, &h->exec_prof, true);
+            st = capture(h, 1, &h->exec_prof, true, false, mask);
             if (st != SPH_OK) return st;
+            h->prof_graph = h->profiling;
         }
         for (; left > 0; --left) {
             if (graphs) SPH_CUDA(h, cudaGraphLaunch(h->exec_prof, h->stream));
-            else SPH_CUDA(h, launch_substep(h->c, h->stream, h->ev, false));
+            else SPH_CUDA(h, launch_substep(h->c, h->stream, h->ev, false, false, mask));
         }
+        h->prof_last = h->profiling;
     } else if (graphs) {
         if (!h->exec1) {
             st = capture(h, 1, &h->exec1);
@@ -986,7 +995,8 @@ sph_status sph_set_profiling(sph_handle *h, int32_t on)
     if (!h) return SPH_ERR_ARG;
     if (on && !h->ev[0])
         for (int i = 0; i <= kSubstepKernels; ++i) SPH_CUDA(h, cudaEventCreate(&h->ev[i]));
-    h->profiling = on != 0;
+    if (on < 0 || on > 2) return fail(h, SPH_ERR_ARG, "profiling level 0, 1 or 2");
+    h->profiling = on;
     return SPH_OK;
 }
 
@@ -995,8 +1005,12 @@ sph_status sph_get_kernel_times(sph_handle *h, float out_ms[8])
     if (!h || !out_ms) return SPH_ERR_ARG;
     if (!h->ev[0]) return fail(h, SPH_ERR_STATE, "profiling was never enabled");
     SPH_CUDA(h, cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < kSubstepKernels; ++i)
+    for (int i = 0; i < kSubstepKernels; ++i) {
+        out_ms[i] = 0.0f;
+        // level 2 records the density pass's two events only (kernel 5)
+        if (h->prof_last == 2 && i != 5) continue;
         SPH_CUDA(h, cudaEventElapsedTime(&out_ms[i], h->ev[i], h->ev[i + 1]));
+    }
     return read_status(h);
 }
 

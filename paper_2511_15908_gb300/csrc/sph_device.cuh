@@ -2076,7 +2076,8 @@ constexpr int kWrenchThreads = kTile;
 // FP64 and a slice of the force pass's FP64 diagnostic partials; the last block to finish
 // forms the per-body wrenches and diagnostics in a fixed order and updates rigid bodies.
 // GB300 runs FP64 at a small fraction of FP32, so this work is spread over many SMs.
-__device__ __forceinline__ void wrench_item(const SimConst &c, int blk)
+// true in the block that took the last ticket (and ran the sums and the rigid update)
+__device__ __forceinline__ bool wrench_item(const SimConst &c, int blk)
 {
     __shared__ double sw[kWrenchThreads / 32][6];
     __shared__ double sdg[kWrenchThreads / 32][8];
@@ -2143,7 +2144,7 @@ __device__ __forceinline__ void wrench_item(const SimConst &c, int blk)
     __syncthreads();
     if (threadIdx.x == 0) s_last = (atomicAdd(c.ctr + 1, 1u) == (unsigned)G - 1);
     __syncthreads();
-    if (!s_last) return;
+    if (!s_last) return false;
     __threadfence();
     // ---- last block: fixed-order sums
     // Every column is summed by 32 threads (rows strided by 32) and a fixed shuffle tree,
@@ -2189,6 +2190,7 @@ __device__ __forceinline__ void wrench_item(const SimConst &c, int blk)
         c.ctr[0] = step + 1u;
         __threadfence();
     }
+    return true;
 }
 
 // ---------------------------------------------------------------- per-call kernels

@@ -110,8 +110,13 @@ struct __align__(16) SimConst {
 constexpr int kSubstepKernels = 8;
 // ev (nullable): kSubstepKernels + 1 events recorded around the kernels; external = record
 // them as graph nodes when the stream is being captured.
+// cycle_end: the update cycle's end (launch_cycle_end's work) folded into the wrench pass;
+// ev_mask: which of the kSubstepKernels + 1 events are recorded (bit k: event k)
 cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev = nullptr,
-                           bool external = false);
+                           bool external = false, bool cycle_end = false,
+                           unsigned ev_mask = ~0u);
+// the events around the density pass alone (events 5 and 6)
+constexpr unsigned kDensityEvents = (1u << 5) | (1u << 6);
 // spring cutting against a blade triangle (sorts the current state first, like the next
 // substep would); count (device) += springs cut
 cudaError_t launch_cut(const SimConst &c, cudaStream_t s, const float tri[9], unsigned *count);

@@ -67,6 +67,12 @@ __global__ void __launch_bounds__(kTile, SPH_FORCE_MINB) k_force_coop(SimConst c
     force_coop_item<G>(c, blockIdx.x);
 }
 __global__ void __launch_bounds__(kTile) k_wrench(SimConst c) { wrench_item(c, blockIdx.x); }
+// the last substep of an update cycle: the cycle's end (the rolling-average log) in the
+// block that finished the wrench, after its sums (the same values k_cycle_end would read)
+__global__ void __launch_bounds__(kTile) k_wrench_cycle(SimConst c)
+{
+    if (wrench_item(c, blockIdx.x) && threadIdx.x == 0) cycle_end_item(c);
+}
 __global__ void k_cycle_end(SimConst c) { cycle_end_item(c); }
 
 __global__ void k_set_grab(SimConst c, int body, int grab, float pv0, float pv1, float pv2,
@@ -109,12 +115,13 @@ __global__ void k_sorted_keys(SimConst c, uint32_t *keys, int *ids)
 
 static inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
-cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, bool external)
+cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, bool external,
+                           bool cycle_end, unsigned ev_mask)
 {
     const int nb = blocks_for(c.n, 256);
     int k = 0;
     auto mark = [&]() {
-        if (ev) cudaEventRecordWithFlags(ev[k], s, external ? cudaEventRecordExternal : 0);
+        if (ev && (ev_mask >> k & 1u)) cudaEventRecordWithFlags(ev[k], s, external ? cudaEventRecordExternal : 0);
         ++k;
     };
     mark();
@@ -163,7 +170,8 @@ cudaError_t launch_substep(const SimConst &c, cudaStream_t s, cudaEvent_t *ev, b
     else
         k_force<<<c.n_force_blocks, kTile, 0, s>>>(c);
     mark();
-    k_wrench<<<c.n_wgrid, kTile, 0, s>>>(c);
+    if (cycle_end) k_wrench_cycle<<<c.n_wgrid, kTile, 0, s>>>(c);
+    else k_wrench<<<c.n_wgrid, kTile, 0, s>>>(c);
     mark();
     return cudaGetLastError();
 }

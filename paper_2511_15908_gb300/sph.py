@@ -459,7 +459,9 @@ class Simulation:
         self.stream.synchronize()
         return d.cpu().numpy()
 
-    def set_profiling(self, on: bool = True):
+    def set_profiling(self, on=True):
+        """on: False / 0 off, True / 1 events around every kernel, 2 around the density
+        pass only."""
         self._check(self.L.sph_set_profiling(self.h, int(on)))
 
     def kernel_times(self) -> np.ndarray:

@@ -286,6 +286,36 @@ def test_sort_is_stable_over_substeps_and_deterministic(sph):
         assert np.array_equal(a, b), "two runs of the same scene differ"
 
 
+def test_profiling_levels_time_the_kernels_and_change_nothing(sph):
+    # level 1: events around every kernel; level 2: around the density pass only; the
+    # state is the unprofiled run's bit for bit
+    sc = scenes.with_velocity_noise(scenes.dam_break(seed=4), seed=4, sigma=0.2)
+    states = []
+    for level in (0, 1, 2):
+        sim = sph.Simulation(sc)
+        if level:
+            sim.set_profiling(level)
+        sim.step(3)
+        if level:
+            t = sim.kernel_times()
+            k = sph.KERNELS.index("density")
+            assert t[k] > 0
+            if level == 1:
+                assert np.all(t >= 0) and (t > 0).sum() >= 6
+            else:
+                assert np.all(np.delete(t, k) == 0)
+        st = sim.state()
+        states.append((st["x"], st["v"], sim.body(1)))
+        sim.close()
+    for other in states[1:]:
+        for u, w in zip(states[0], other):
+            assert np.array_equal(u, w)
+    sim = sph.Simulation(sc)
+    with pytest.raises(sph.SphError):
+        sim.set_profiling(3)
+    sim.close()
+
+
 def test_graph_replay_equals_direct_launches(sph):
     sc = scenes.dam_break(seed=2)
     out = []
